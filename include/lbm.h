@@ -1,0 +1,263 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) total-Lagrangian vectorial lattice
+ * Boltzmann library for finite-strain hyperelasticity on embedded curved
+ * domains (arXiv 2606.20646).
+ *
+ * The calls follow the paper's statement of the problem: a reference body
+ * given by a level set (Sec. 3.1, Eq. level-set-domain) on a Cartesian
+ * lattice, a hyperelastic material (Sec. 4.1, Eq. validation-nh-energy),
+ * boundary data on Dirichlet and nominal-traction parts of the surface
+ * (Sec. 2.1, Eqs. physical-dirichlet, vD-from-uD, nominal-traction-general),
+ * initial fields (Eq. initial-data-general), and the one-step update of
+ * Algorithm 1 (Sec. 3.6), returning the fields v, F and u.
+ *
+ * Conventions shared by every call
+ *   - Lattice nodes are cell centred: X_i = origin + (i + 1/2) dx.
+ *   - Box fields are structure-of-arrays planes of doubles, one plane per
+ *     component, each plane nx*ny*nz values with x fastest (node index
+ *     x + nx*(y + ny*z)); inactive nodes are written as 0 and ignored on input.
+ *     v: D planes; F: D*D planes, F row-major (F_11, F_12, .., F_DD) as in
+ *     Eq. (state-general-d); u: D planes; dU0: D*(D+D*D) planes, plane
+ *     A*(D+D*D) + k holding d U0_k / d X_A.
+ *   - Pointers to fields may be device pointers, or host pointers when the
+ *     handle was created with host staging (lbm_options.host_staging = 1);
+ *     the library tells them apart with cudaPointerGetAttributes.
+ *   - All device work is enqueued on the CUDA stream given to lbm_create and
+ *     is asynchronous unless stated otherwise.  Device-side failures (Newton
+ *     non-convergence, J <= 0, non-finite values) are latched in a device
+ *     status word and reported by lbm_sync.
+ *   - The library never allocates device memory.  The caller allocates the
+ *     geometry storage before lbm_create and the solver storage after it,
+ *     keeps both alive until lbm_destroy, and frees them afterwards.  The
+ *     handle itself owns only host memory.
+ *   - Every int-returning call returns LBM_OK (0) or a negative lbm_error;
+ *     lbm_error_string gives its text.  No call throws or aborts.
+ */
+#ifndef LBM_B300_H
+#define LBM_B300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (negative returns) -------------------------------------- */
+enum lbm_error {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument or descriptor                           */
+    LBM_ERR_DOMAIN = -2,   /* empty body, or the body reaches a non-periodic box face  */
+    LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                               */
+    LBM_ERR_STORAGE = -4,  /* storage missing, too small or misaligned (256 B)         */
+    LBM_ERR_STATE = -5,    /* call out of order (e.g. lbm_step before lbm_set_initial) */
+    LBM_ERR_DEVICE = -6,   /* lbm_sync found a non-zero device status word             */
+    LBM_ERR_CAPACITY = -7  /* a fixed capacity (LSQ stencil) was exceeded              */
+};
+
+/* ---- device status bits returned by lbm_sync ------------------------------ */
+enum lbm_device_status {
+    LBM_DEV_NONFINITE = 1, /* a recovered state component was not finite             */
+    LBM_DEV_JACOBIAN = 2,  /* J = det F <= 0 at an active node (Eq. positive-jacobian) */
+    LBM_DEV_NEWTON = 4,    /* traction inversion failed (Eqs. neumann-newton-2d/3d)   */
+    LBM_DEV_LSQ = 8,       /* no least-squares fit at a Neumann link                   */
+    LBM_DEV_CAPACITY = 16  /* LSQ stencil larger than LBM_LSQ_CAPACITY                */
+};
+
+enum lbm_precision { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1 };
+
+/* level-set primitives; local coordinates xi = rot^T (X - center), rot row-major 3x3
+ *   SPHERE        phi = |X - center| - axes[0]                (circle in 2D)
+ *   ELLIPSOID     phi = sum_a (xi_a / axes[a])^2 - 1          (ellipse in 2D)
+ *   SUPERELLIPSE  phi = |xi_1/axes[0]|^p + |xi_2/axes[1]|^p - 1  (2D only)
+ *   CYLINDER      phi = |(X_1, X_2) - (c_1, c_2)| - axes[0]   (axis X_3)
+ *   HALFSPACE     phi = axes . (X - center), axes a unit outward normal
+ * complement != 0 negates phi.  The body is {X : max_s phi_s(X) <= 0}. */
+enum lbm_shape_kind {
+    LBM_SHAPE_SPHERE = 0,
+    LBM_SHAPE_ELLIPSOID = 1,
+    LBM_SHAPE_SUPERELLIPSE = 2,
+    LBM_SHAPE_CYLINDER = 3,
+    LBM_SHAPE_HALFSPACE = 4
+};
+
+enum lbm_bc_kind { LBM_BC_DIRICHLET = 0, LBM_BC_NEUMANN = 1 };
+
+/* boundary profiles, s(t) the ramp:
+ *   Dirichlet (prescribed displacement; the lattice imposes v_D = d u_D / dt):
+ *     ZERO          u_D = 0
+ *     AFFINE        u_D = s(t) A (X - center)
+ *     RADIAL        u_D = amp s(t) (X - center)/|X - center|
+ *     TWIST_STRETCH u_D = ((R(s(t) amp) - I) (X_1 - c_1, X_2 - c_2), s(t) vec[2])  (3D)
+ *   Neumann (nominal traction T = P N):
+ *     CONST         T = s(t) vec
+ *     RADIAL        T = amp s(t) (X - center)/|X - center|                        */
+enum lbm_profile {
+    LBM_PROFILE_ZERO = 0,
+    LBM_PROFILE_AFFINE = 1,
+    LBM_PROFILE_RADIAL = 2,
+    LBM_PROFILE_TWIST_STRETCH = 3,
+    LBM_PROFILE_CONST = 4
+};
+
+/* ramps: ONE s=1; LINEAR t/T then 1; SIN2 sin^2(pi t/(2T)) then 1 (Eq. sine2-ramp);
+ * COS (1 - cos(pi t/T))/2 then 1 (Eq. tube-cosine-ramp); TIME s = t */
+enum lbm_ramp { LBM_RAMP_ONE = 0, LBM_RAMP_LINEAR = 1, LBM_RAMP_SIN2 = 2, LBM_RAMP_COS = 3, LBM_RAMP_TIME = 4 };
+
+/* initialisation: EQUILIBRIUM f = f^eq(U0); CHARACTERISTIC adds the second-order
+ * correction of Eqs. (init-general-d, Ut-general-init) */
+enum lbm_init { LBM_INIT_EQUILIBRIUM = 0, LBM_INIT_CHARACTERISTIC = 1 };
+
+#define LBM_MAX_SHAPES 16
+#define LBM_MAX_BCS 16
+#define LBM_LSQ_CAPACITY 160 /* max active nodes within 3 dx of a boundary point */
+
+typedef struct lbm_grid {
+    int dim;         /* 2 (D2Q4x6) or 3 (D3Q6x12)                               */
+    int n[3];        /* nodes per axis; n[2] ignored in 2D                      */
+    int periodic[3]; /* non-zero: periodic axis (no cut links across it)        */
+    int reserved;
+    double dx;       /* lattice spacing                                          */
+    double origin[3];
+} lbm_grid;
+
+typedef struct lbm_shape {
+    int kind;        /* enum lbm_shape_kind                                     */
+    int complement;  /* non-zero: use -phi                                      */
+    int boundary_id; /* id carried by cut links whose X_b lies on this shape    */
+    int reserved;
+    double center[3];
+    double axes[3];
+    double rot[9];
+    double p;        /* superellipse exponent                                   */
+} lbm_shape;
+
+typedef struct lbm_levelset {
+    int nshapes; /* 0: every box node active (periodic boxes) */
+    const lbm_shape *shapes;
+} lbm_levelset;
+
+typedef struct lbm_material {
+    double mu;     /* shear modulus                  */
+    double lambda; /* Lame's first parameter          */
+} lbm_material;
+
+typedef struct lbm_bc {
+    int boundary_id;
+    int kind;    /* enum lbm_bc_kind */
+    int profile; /* enum lbm_profile */
+    int ramp;    /* enum lbm_ramp    */
+    double t_ramp;
+    double center[3];
+    double A[9]; /* row-major 3x3 */
+    double vec[3];
+    double amp;
+} lbm_bc;
+
+typedef struct lbm_options {
+    int precision;    /* enum lbm_precision: population storage and collision arithmetic */
+    int proj_every;   /* compatibility projection cadence in steps (0: never)            */
+    int proj_iters;   /* damped-Jacobi sweeps per projection solve                        */
+    int host_staging; /* non-zero: reserve a staging area so field calls accept host memory */
+    double c;         /* lattice speed dx/dt                                              */
+    double omega;     /* BGK relaxation, 0 < omega <= 2                                   */
+    double gamma;     /* velocity damping: B = (b - gamma v, 0)                           */
+    double theta_F;   /* F repair weight, 0 < theta_F <= 1 (Eq. projection-F-repair-weight) */
+    double proj_beta; /* Jacobi damping, 0 < beta <= 1                                    */
+    double body_force[3];
+} lbm_options;
+
+typedef struct lbm_info {
+    long long n_box, n_active, n_cut, n_neumann, n_dirichlet, n_segments;
+    long long step;          /* steps taken since lbm_set_initial */
+    double t, dt;
+    size_t geometry_bytes, storage_bytes;
+    long long launches;      /* kernels launched by lbm_step since creation */
+    long long lsq_entries;   /* total LSQ stencil entries over Neumann links */
+} lbm_info;
+
+typedef struct lbm_kernel_time {
+    double stream_collide_ms; /* fused gather + closure + collision kernel       */
+    double cutlink_ms;        /* per-link boundary source kernel                  */
+    double projection_ms;     /* projection, repair and reset kernels             */
+    long long stream_collide_launches, cutlink_launches, projection_launches;
+} lbm_kernel_time;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of caller-provided device memory lbm_create needs for the geometry
+ * pass (active mask, cut-link bits, link offsets, segment list).  Depends only
+ * on the grid.  Returns LBM_ERR_ARG for an invalid grid. */
+int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes);
+
+/* Validates the descriptors, then runs the FP64 geometry pass on the GPU in
+ * geometry_storage (>= lbm_geometry_bytes, 256-byte aligned): active nodes
+ * phi(X) <= 0 (Eq. level-set-domain) and cut links (Sec. 3.1, the sets I and
+ * C of Sec. 3.6).  Synchronises the stream once to read the counts.  The
+ * descriptors are copied; the arrays they point to may be freed on return.
+ * Errors: LBM_ERR_ARG (bad descriptor, omega outside (0,2], dx<=0, c<=0,
+ * missing BC for a boundary id is reported later by lbm_bind_storage),
+ * LBM_ERR_DOMAIN (no active node, or the body reaches a non-periodic box
+ * face), LBM_ERR_STORAGE, LBM_ERR_CUDA. */
+int lbm_create(const lbm_grid *grid, const lbm_levelset *levelset, const lbm_material *material,
+               const lbm_bc *bcs, int nbc, const lbm_options *options, void *geometry_storage,
+               size_t geometry_bytes, void *cuda_stream, lbm_handle **out);
+
+/* Bytes of solver storage (populations x2, u*, u^n, cut-link records, LSQ
+ * weights, projection scratch, optional host staging). */
+int lbm_storage_bytes(const lbm_handle *h, size_t *bytes);
+
+/* Binds the solver storage (>= lbm_storage_bytes, 256-byte aligned) and builds
+ * the per-link geometry in FP64 on the GPU: eta by bisection of phi
+ * (Eq. cut-link-point), boundary normal (Eq. level-set-normal), boundary id,
+ * tangent frame and LSQ tangent-derivative weights (Eq. tangent-derivative-2d,
+ * Eq. tangent-image-3d-lsq).  Errors: LBM_ERR_STORAGE, LBM_ERR_ARG (a boundary
+ * id with no BC), LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
+int lbm_bind_storage(lbm_handle *h, void *storage, size_t bytes);
+
+/* Initial state (Eq. initial-data-general): v0 (D planes), F0 (D*D planes),
+ * u0 (D planes), all required; dU0 (D*(D+D*D) planes) optional.  mode
+ * LBM_INIT_EQUILIBRIUM sets f = f^eq(U0); LBM_INIT_CHARACTERISTIC applies
+ * Eq. (init-general-d) with d_t U0 from Eq. (Ut-general-init), using dU0 when
+ * given and second-order central (one-sided at the body) differences
+ * otherwise.  Sets u*^0 = u0 - dt/2 v0 and the step counter to 0. */
+int lbm_set_initial(lbm_handle *h, int mode, const double *v0, const double *F0, const double *u0,
+                    const double *dU0);
+
+/* Advances nsteps steps of Algorithm 1 (collide, stream, cut-link closure,
+ * and, when Neumann links exist, the compatibility projection every
+ * proj_every steps).  Enqueued; returns after launching. */
+int lbm_step(lbm_handle *h, int nsteps);
+
+/* Writes v, F (from U^num, Eq. state-recovery-general) and u = u* + dt/2 v
+ * (Eq. u-recovery-general) at the current time.  Any pointer may be NULL. */
+int lbm_fields(lbm_handle *h, double *v, double *F, double *u);
+
+/* Synchronises the stream and reads (then clears) the device status word.
+ * Returns LBM_ERR_DEVICE if it was non-zero, with the bits in *device_status. */
+int lbm_sync(lbm_handle *h, int *device_status);
+
+int lbm_get_info(const lbm_handle *h, lbm_info *info);
+
+/* Per-kernel CUDA-event timing of lbm_step's launches (enable != 0 starts and
+ * clears the accumulators); lbm_kernel_times synchronises and reports them. */
+int lbm_enable_timing(lbm_handle *h, int enable);
+int lbm_kernel_times(lbm_handle *h, lbm_kernel_time *out);
+
+/* Cut-link geometry, for verification: copies n_cut entries into host arrays
+ * (any may be NULL): node index, outgoing direction q (0:+x 1:-x 2:+y 3:-y
+ * 4:+z 5:-z), eta, X_b (3 per link), N_b (3 per link), boundary id, LSQ
+ * stencil size.  Synchronises the stream. */
+int lbm_copy_links(lbm_handle *h, long long *node, int *q, double *eta, double *Xb, double *Nb, int *bid,
+                   int *ns);
+
+/* Active mask (1 byte per box node), for verification.  Synchronises. */
+int lbm_copy_active(lbm_handle *h, unsigned char *mask);
+
+void lbm_destroy(lbm_handle *h);
+const char *lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_B300_H */

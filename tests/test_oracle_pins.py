@@ -1,0 +1,452 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/paper_values.json), closed forms, exact solutions,
+invariants, or brute force.  No GPU is used.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import radial_bvp as rb
+from paper_2606_20646_b300 import inputs as I
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def energy(D, mu, lam, F):
+    """Neo-Hookean strain energy, Eq. (validation-nh-energy)."""
+    J = np.linalg.det(F)
+    return 0.5 * mu * (np.sum(F * F) - D) - (mu + 0.5 * lam) * math.log(J) + 0.25 * lam * (J * J - 1.0)
+
+
+def rand_F(rng, D, s=0.3):
+    while True:
+        F = np.eye(D) + s * rng.standard_normal((D, D))
+        if np.linalg.det(F) > 0.2:
+            return F
+
+
+# --------------------------------------------------------------------------- constitutive law
+
+def test_piola_reproduces_printed_cauchy_stress():
+    g = GOLD["affine_annulus"]
+    F = np.eye(2) + np.array(g["A"])
+    P, J = oracle.piola(2, g["mu"], g["lambda"], F)
+    assert abs(J - g["J_star"]) < 1e-12
+    sigma = g["stress_scale_MPa"] * P @ F.T / J          # Eq. (cauchy-recovery-general)
+    assert np.allclose(sigma, np.array(g["sigma_MPa"]), atol=5e-5)
+
+
+def test_ellipsoid_printed_F_and_J():
+    g = GOLD["ellipsoid"]
+    F = np.eye(3) + g["T"] * np.array(g["A"])
+    assert np.allclose(F, np.array(g["F_T"]), atol=5e-5)
+    _, J = oracle.piola(3, 1.0, 2.0 / 3.0, F)
+    assert abs(J - g["J_T"]) < 5e-6
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_piola_is_gradient_of_energy(D):
+    rng = np.random.default_rng(1 + D)
+    mu, lam = 1.3, 2.7
+    for _ in range(5):
+        F = rand_F(rng, D)
+        P, _ = oracle.piola(D, mu, lam, F)
+        G = np.zeros((D, D))
+        h = 1e-6
+        for i in range(D):
+            for A in range(D):
+                E = np.zeros((D, D))
+                E[i, A] = h
+                G[i, A] = (energy(D, mu, lam, F + E) - energy(D, mu, lam, F - E)) / (2 * h)
+        assert np.allclose(P, G, atol=1e-8)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_piola_reference_state_and_objectivity(D):
+    rng = np.random.default_rng(7)
+    P0, J0 = oracle.piola(D, 1.0, 5.0, np.eye(D))
+    assert np.abs(P0).max() < 1e-15 and J0 == 1.0
+    F = rand_F(rng, D)
+    Rq, _ = np.linalg.qr(rng.standard_normal((D, D)))
+    if np.linalg.det(Rq) < 0:
+        Rq[:, 0] *= -1
+    P, _ = oracle.piola(D, 1.0, 5.0, F)
+    PR, _ = oracle.piola(D, 1.0, 5.0, Rq @ F)           # frame indifference P(RF) = R P(F)
+    assert np.allclose(PR, Rq @ P, atol=1e-12)
+    PI, _ = oracle.piola(D, 1.0, 5.0, F @ Rq)           # isotropy P(FR) = P(F) R
+    assert np.allclose(PI, P @ Rq, atol=1e-12)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_tangent_is_derivative_of_stress(D):
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        F = rand_F(rng, D)
+        Z = rng.standard_normal((D, D))
+        dP = oracle.dpiola(D, 0.8, 3.0, F, Z)
+        h = 1e-6
+        fd = (oracle.piola(D, 0.8, 3.0, F + h * Z)[0] - oracle.piola(D, 0.8, 3.0, F - h * Z)[0]) / (2 * h)
+        assert np.allclose(dP, fd, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- lattice algebra
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_equilibrium_moments_and_pair_identities(D):
+    """Eqs. (moment-constraints-general), (pair-sum-general), (pair-identities-general)."""
+    rng = np.random.default_rng(3)
+    c, mu, lam = 7.0, 1.1, 2.3
+    K = D + D * D
+    v = rng.standard_normal(D) * 0.1
+    F = rand_F(rng, D)
+    U = np.concatenate([v, F.reshape(-1)])
+    feq = oracle.feq(D, c, mu, lam, U)
+    P, _ = oracle.piola(D, mu, lam, F)
+    Phi = np.zeros((D, K))
+    for A in range(D):
+        Phi[A, :D] = -P[:, A]
+        for i in range(D):
+            Phi[A, D + i * D + A] = -v[i]
+    e = np.zeros((2 * D, D))
+    for q in range(2 * D):
+        e[q, q // 2] = 1.0 if q % 2 == 0 else -1.0
+    assert np.allclose(feq.sum(0), U, atol=1e-14)
+    for A in range(D):
+        assert np.allclose(c * (e[:, A:A + 1] * feq).sum(0), Phi[A], atol=1e-13)
+        assert np.allclose(feq[2 * A] + feq[2 * A + 1], U / D, atol=1e-14)
+        assert np.allclose(feq[2 * A + 1] - feq[2 * A], -Phi[A] / c, atol=1e-14)  # d = -e_A
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_single_node_collision_brute_force(D):
+    """Recovery with implicit damping (Eq. state-recovery-general) and BGK with
+    source weights 1/(4D) (Eqs. collision-general-d, source-weights-general),
+    expanded by hand component by component."""
+    rng = np.random.default_rng(5 + D)
+    K, Q = D + D * D, 2 * D
+    c, omega, dt, gamma, mu, lam = 10.0, 1.7, 0.003, 4.0, 1.0, 2.0
+    b = np.array([0.3, -0.2, 0.1])[:D]
+    F0 = rand_F(rng, D, 0.1)
+    U0 = np.concatenate([0.05 * rng.standard_normal(D), F0.reshape(-1)])
+    f = oracle.feq(D, c, mu, lam, U0) + 1e-3 * rng.standard_normal((Q, K))
+    out, U = oracle.collide_node(D, c, omega, dt, gamma, np.r_[b, np.zeros(3 - D)], mu, lam, f)
+    S = f.sum(0)
+    v = (S[:D] + 0.5 * dt * b) / (1.0 + 0.5 * dt * gamma)
+    Uh = np.concatenate([v, S[D:]])
+    assert np.allclose(U, Uh, atol=1e-15)
+    feq = oracle.feq(D, c, mu, lam, Uh)
+    B = np.zeros(K)
+    B[:D] = b - gamma * v
+    expect = np.empty_like(f)
+    for q in range(Q):
+        for k in range(K):
+            expect[q, k] = f[q, k] + omega * (feq[q, k] - f[q, k]) + dt * (2 - omega) * B[k] / (4 * D)
+    assert np.allclose(out, expect, atol=1e-15)
+    # the collision shifts the momentum by dt*B and leaves the F moment unchanged
+    assert np.allclose(out.sum(0)[:D] - S[:D], dt * B[:D], atol=1e-14)
+    assert np.allclose(out.sum(0)[D:], S[D:], atol=1e-14)
+
+
+# --------------------------------------------------------------------------- bulk dynamics
+
+def test_shear_wave_second_order_convergence():
+    """Exact finite-amplitude shear wave (derived from Sec. 2.2 and Eq. validation-nh-energy)."""
+    errs = []
+    for n in (32, 64):
+        p = I.shear_wave_2d(n)
+        o = oracle.Oracle(p).set_initial()
+        o.step(p.steps)
+        v, F, u = o.fields()
+        v2, F21 = I.shear_wave_exact(p, p.steps * p.dt)
+        errs.append(np.linalg.norm(v[1] - v2) / np.linalg.norm(v2))
+        assert np.abs(v[0]).max() < 1e-12 and np.abs(F[1]).max() < 1e-12      # no v_1, F_12 produced
+        assert np.linalg.norm(F[2] - F21) / np.linalg.norm(F21) < 4e-2
+    assert errs[0] < 3.5e-2 and errs[1] < 9e-3
+    order = math.log(errs[0] / errs[1], 2)
+    assert 1.9 < order < 2.1
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_homogeneous_state_is_fixed_point(D):
+    rng = np.random.default_rng(21)
+    p = I.random_periodic(D, 8 if D == 3 else 12, seed=2, omega=1.6)
+    F = rand_F(rng, D, 0.2)
+    p.v0[:] = 0.0
+    for k in range(D * D):
+        p.F0[k] = F.reshape(-1)[k]
+    o = oracle.Oracle(p).set_initial()
+    f0 = o.populations()
+    o.step(7)
+    assert np.abs(o.populations() - f0).max() < 1e-15
+    v, Fo, _ = o.fields()
+    assert np.abs(v).max() < 1e-15
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_momentum_balance_on_periodic_box(D):
+    """sum_m v_m is conserved without forcing and grows by dt*b per step with a body force."""
+    for b in ((0.0, 0.0, 0.0), (0.5, -0.3, 0.2)):
+        p = I.random_periodic(D, 8 if D == 3 else 16, seed=4, body_force=b, omega=1.5)
+        o = oracle.Oracle(p).set_initial()
+        v0, _, _ = o.fields()
+        n = 9
+        o.step(n)
+        v1, _, _ = o.fields()
+        N = p.n_box
+        drift = v1.reshape(D, -1).sum(1) - v0.reshape(D, -1).sum(1)
+        assert np.allclose(drift, n * p.dt * np.array(b[:D]) * N, atol=1e-11)
+
+
+# --------------------------------------------------------------------------- geometry
+
+@pytest.mark.parametrize("name,builder,N", [
+    ("affine_annulus", I.affine_annulus_2d, 384),
+    ("radial_annulus", I.radial_traction_annulus_2d, 196),
+    ("superellipse", I.superellipse_shell_2d, 384)])
+def test_active_and_cut_counts_match_paper_2d(name, builder, N):
+    """Tables tab:2d-curved-summary: exact active-node and cut-link counts."""
+    key = "active_cut_N%d" % N
+    o = oracle.Oracle(builder(N))
+    c = o.counts()
+    assert [c["n_active"], c["n_cut"]] == GOLD[name][key]
+
+
+def test_active_and_cut_counts_match_paper_sphere_200():
+    """Table tab:3d-curved-summary prints 1.57e6 / 1.39e5 for the 200^3 spherical shell."""
+    p = I.sphere_shell_paper_3d(200)
+    p.bcs = [I.BC(0, "dirichlet", "zero"), I.BC(1, "dirichlet", "zero")]   # geometry only, no LSQ build
+    c = oracle.Oracle(p).counts()
+    a, l = GOLD["spherical_shell"]["active_cut_N200_rounded"]
+    assert round(c["n_active"], -4) == a and round(c["n_cut"], -3) == l
+
+
+def test_eta_and_normal_match_circle():
+    """Eq. (cut-link-point) and Eq. (level-set-normal) on a circle: closed-form root and normal."""
+    p = I.affine_annulus_2d(96)
+    o = oracle.Oracle(p)
+    L = o.links()
+    X = p.coords()
+    for l in range(0, len(L["node"]), 7):
+        m = L["node"][l]
+        iy, ix = divmod(m, p.n[0])
+        Xm = np.array([X[0][iy, ix], X[1][iy, ix]]) - 0.5
+        e = np.zeros(2)
+        e[L["q"][l] // 2] = 1.0 if L["q"][l] % 2 == 0 else -1.0
+        R = 0.42 if np.linalg.norm(Xm + p.dx * e) > 0.3 else 0.18
+        # |Xm + s dx e| = R, smallest s in (0,1)
+        bq, cq = 2 * (Xm @ e) * p.dx, Xm @ Xm - R * R
+        roots = np.roots([p.dx * p.dx, bq, cq]).real
+        s = min(r for r in roots if 0 < r < 1 + 1e-12)
+        assert abs(L["eta"][l] - s) < 1e-12          # phi resolves eta to ~ eps / (dx |dphi/dX|)
+        nb = (Xm + s * p.dx * e) / R * (1 if R == 0.42 else -1)
+        assert np.allclose(L["Nb"][l, :2], nb, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- Neumann building blocks
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_lsq_tangent_derivative_exact_on_quadratics(D):
+    """Eqs. (quadratic-lsq-2d), (tangent-derivative-2d): exact on any quadratic field."""
+    rng = np.random.default_rng(9)
+    dx = 0.05
+    for _ in range(5):
+        pts = rng.uniform(-2.5, 2.5, size=(40, D))
+        pts = pts[np.linalg.norm(pts, axis=1) <= 3.0][:25 if D == 2 else 35]
+        N = rng.standard_normal(D)
+        N /= np.linalg.norm(N)
+        t = np.array([-N[1], N[0]]) if D == 2 else np.cross(N, [1.0, 0, 0])
+        t /= np.linalg.norm(t)
+        w, r = oracle.lsq_weights(D, pts, [t], dx)
+        assert r == 0
+        a, g, H = rng.standard_normal(), rng.standard_normal(D), rng.standard_normal((D, D))
+        H = H + H.T
+        u = a + (pts * dx) @ g + 0.5 * np.einsum("ni,ij,nj->n", pts * dx, H, pts * dx)
+        assert abs(w[0] @ u - g @ t) < 1e-9
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_newton_traction_inversion(D):
+    """Eqs. (Fb-decomp-2d/3d), (neumann-newton-2d/3d): residual at the tolerance, det F_b > 0,
+    and the recovered F_b reproduces a known state."""
+    rng = np.random.default_rng(13)
+    mu, lam = 1.0, 5.0
+    for _ in range(6):
+        Ftrue = rand_F(rng, D, 0.25)
+        N = rng.standard_normal(D)
+        N /= np.linalg.norm(N)
+        if D == 2:
+            ts = [np.array([-N[1], N[0]])]
+        else:
+            t1 = np.cross(N, [0, 0, 1.0] if abs(N[2]) < 0.9 else [1.0, 0, 0])
+            t1 /= np.linalg.norm(t1)
+            ts = [t1, np.cross(N, t1)]
+        g = [Ftrue @ t for t in ts]
+        P, _ = oracle.piola(D, mu, lam, Ftrue)
+        T = P @ N
+        h, it = oracle.newton(D, mu, lam, N, g, ts, T, N.copy())
+        assert it >= 0
+        Fb = np.outer(h, N) + sum(np.outer(gg, t) for gg, t in zip(g, ts))
+        assert np.linalg.det(Fb) > 0
+        Pb, _ = oracle.piola(D, mu, lam, Fb)
+        assert np.abs(Pb @ N - T).max() < 1e-12
+        assert np.allclose(Fb, Ftrue, atol=1e-10)
+
+
+def test_newton_axis_case_matches_appendix():
+    """Appendix A, Eq. (appendix-axis-newton): for N = -e_1 the normal column of F^b solves
+    sign(N_1) P_{i1}(F^b) = T_i with the tangential columns held."""
+    mu, lam = 1.0, 2.0 / 3.0
+    N = np.array([-1.0, 0.0, 0.0])
+    ts = [np.array([0, 1.0, 0]), np.array([0, 0, 1.0])]
+    g = [np.array([0.05, 1.1, 0.02]), np.array([-0.03, 0.01, 0.95])]
+    T = np.array([0.4, -0.1, 0.2])
+    h, it = oracle.newton(3, mu, lam, N, g, ts, T, N.copy())
+    assert it >= 0
+    Fb = np.column_stack([-h, g[0], g[1]])              # h = F_b N = -F_b[:,0]
+    P, _ = oracle.piola(3, mu, lam, Fb)
+    assert np.allclose(-P[:, 0], T, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- compatibility projection
+
+def test_projection_is_identity_on_compatible_affine_fields():
+    """u linear with F = I + grad u already satisfies every edge relation
+    (Eq. projection-edge-relation): u^c = u and F^c = F (Eq. projection-compatible-F)."""
+    p = I.radial_traction_annulus_2d(48)
+    p.bcs = [I.BC(0, "neumann", "const"), I.BC(1, "neumann", "const")]     # gauge-only solve
+    o = oracle.Oracle(p)
+    G = np.array([[0.1, -0.05], [0.07, 0.12]])
+    X, Y = p.coords()
+    u = np.stack([G[0, 0] * X + G[0, 1] * Y, G[1, 0] * X + G[1, 1] * Y])
+    F = np.stack([np.full(X.shape, (np.eye(2) + G).reshape(-1)[k]) for k in range(4)])
+    act = o.active_mask()
+    uc, Fc = o.project(F, u * act)
+    assert np.abs((uc - u) * act).max() < 1e-13
+    assert np.abs((Fc - F) * act).max() < 1e-12
+
+
+def test_projection_reduces_incompatibility():
+    """The damped-Jacobi solve lowers the edge-relation residual of a perturbed field."""
+    p = I.radial_traction_annulus_2d(48)
+    p.bcs = [I.BC(0, "neumann", "const"), I.BC(1, "neumann", "const")]
+    o = oracle.Oracle(p)
+    act = o.active_mask()
+    rng = np.random.default_rng(2)
+    X, Y = p.coords()
+    F = np.stack([np.full(X.shape, v) for v in (1.1, 0.05, -0.02, 0.95)])
+    u = np.stack([0.1 * X + 0.05 * Y, -0.02 * X - 0.05 * Y]) + 1e-3 * rng.standard_normal((2,) + X.shape)
+    u *= act
+
+    def residual(uu):
+        r = 0.0
+        for A, (dxs) in enumerate(((0, 1), (1, 0))):
+            sl_a = (slice(None), slice(0, -1)) if A == 0 else (slice(0, -1), slice(None))
+            sl_b = (slice(None), slice(1, None)) if A == 0 else (slice(1, None), slice(None))
+            both = act[sl_a] & act[sl_b]
+            for i in range(2):
+                G = 0.5 * ((F[2 * i + A][sl_a] - (i == A)) + (F[2 * i + A][sl_b] - (i == A)))
+                r += (((uu[i][sl_b] - uu[i][sl_a] - G * p.dx) * both) ** 2).sum()
+        return r
+
+    uc, _ = o.project(F, u)
+    assert residual(uc) < 0.2 * residual(u)
+
+
+# --------------------------------------------------------------------------- closures end to end
+
+def test_affine_dirichlet_annulus_is_exact():
+    """Sec. 4.2: the curved Dirichlet reconstruction keeps the exact affine finite-strain mode;
+    errors at round-off, well below the printed N=384 values."""
+    g = GOLD["affine_annulus"]
+    p = I.affine_annulus_2d(64)
+    o = oracle.Oracle(p).set_initial()
+    o.step(p.steps)
+    v, F, u = o.fields()
+    act = o.active_mask()
+    A, T = p.meta["A"], p.meta["T"]
+    X, Y = p.coords()
+    t = p.steps * p.dt
+    ue = np.stack([(A[0, 0] * (X - .5) + A[0, 1] * (Y - .5)) * t / T, (A[1, 0] * (X - .5) + A[1, 1] * (Y - .5)) * t / T])
+    Fe = (np.eye(2) + A * t / T).reshape(-1)
+    Eu = np.sqrt((((u - ue) ** 2) * act).sum() / ((ue ** 2) * act).sum())
+    EF = np.sqrt(sum((((F[k] - Fe[k]) ** 2) * act).sum() for k in range(4)) /
+                 (act.sum() * ((Fe - np.eye(2).reshape(-1)) ** 2).sum()))
+    assert Eu < 1e-12 and EF < 1e-12
+    assert Eu < g["E_u_N384"] and EF < g["E_FmI_N384"]
+
+
+def test_affine_dirichlet_ellipsoid_is_exact():
+    """Sec. 5.1 at a coarse lattice: rotated ellipsoid, affine Dirichlet data, omega = 1.8."""
+    p = I.ellipsoid_3d(32)
+    o = oracle.Oracle(p).set_initial()
+    o.step(p.steps)
+    v, F, u = o.fields()
+    act = o.active_mask()
+    A = p.meta["A"]
+    X = p.coords()
+    t = p.steps * p.dt
+    d = [X[j] - 0.5 for j in range(3)]
+    ve = np.stack([sum(A[i, j] * d[j] for j in range(3)) for i in range(3)])
+    assert np.sqrt((((v - ve) ** 2) * act).sum() / ((ve ** 2) * act).sum()) < 1e-12
+    assert np.sqrt((((u - t * ve) ** 2) * act).sum() / ((t * ve) ** 2 * act).sum()) < 1e-12
+    Fe = (np.eye(3) + t * A).reshape(-1)
+    assert max(np.abs((F[k] - Fe[k]) * act).max() for k in range(9)) < 1e-12
+
+
+def test_radial_bvp_reproduces_printed_spherical_shell():
+    g = GOLD["spherical_shell"]
+    r = rb.solve(3, 1.0, 2.0 / 3.0, g["R_i"], g["R_o"], ("r", g["r_Ri"]), ("P", 0.0))
+    assert abs(r["r_o"] - g["r_Ro"]) < 5e-6
+    assert abs(r["Pr_i"] - g["Pr_Ri"]) < 5e-6
+    for key, arr in (("lambda_r_range", r["lr"]), ("lambda_t_range", r["lt"]), ("J_range", r["J"])):
+        lo, hi = g[key]
+        assert abs(arr.min() - lo) < 6e-4 and abs(arr.max() - hi) < 6e-4
+
+
+def test_radial_bvp_annulus_matches_printed_displacement():
+    g = GOLD["radial_annulus"]
+    r = rb.solve(2, 1.0, 2.0 / 3.0, 0.18, 0.42, ("r", 0.18), ("P", 1.0))
+    assert abs(10.0 * (r["r_o"] - 0.42) - g["max_u_cm_FEM"]) < 3e-3     # cm, L0 = 10 cm
+
+
+def test_radial_traction_annulus_converges_to_bvp():
+    """Sec. 4.3 protocol (sin^2 ramp, damping, projection every 20 steps) on a coarse lattice:
+    the Neumann closure + projection relaxes to the nonlinear radial BVP."""
+    g = GOLD["radial_annulus"]
+    r = rb.solve(2, 1.0, 2.0 / 3.0, 0.18, 0.42, ("r", 0.18), ("P", 1.0))
+    p = I.radial_traction_annulus_2d(48)
+    o = oracle.Oracle(p).set_initial()
+    o.step(p.steps)
+    assert o.counts()["status"] == 0
+    v, F, u = o.fields()
+    act = o.active_mask()
+    ue = rb.displacement_field(r, p.coords(), (0.5, 0.5))
+    Eu = np.sqrt((((u - ue) ** 2) * act).sum() / ((ue ** 2) * act).sum())
+    assert Eu < 4e-3
+    J = (F[0] * F[3] - F[1] * F[2])[act]
+    lo, hi = g["J_range_LBM"]
+    assert lo - 0.02 < J.min() and J.max() < hi + 0.01
+    umax = np.sqrt((u ** 2).sum(0)).max()
+    assert abs(10 * umax - g["max_u_cm_LBM"]) < 0.01
+
+
+@pytest.mark.slow
+def test_spherical_shell_converges_to_bvp_3d():
+    """Sec. 5.2 protocol on a 32^3 lattice (both surfaces Neumann, mean gauge)."""
+    g = GOLD["spherical_shell"]
+    r = rb.solve(3, 1.0, 2.0 / 3.0, g["R_i"], g["R_o"], ("r", g["r_Ri"]), ("P", 0.0))
+    p = I.sphere_shell_paper_3d(32)
+    o = oracle.Oracle(p).set_initial()
+    o.step(p.steps)
+    assert o.counts()["status"] == 0
+    v, F, u = o.fields()
+    act = o.active_mask()
+    ue = rb.displacement_field(r, p.coords(), (0.5, 0.5, 0.5))
+    Eu = np.sqrt((((u - ue) ** 2) * act).sum() / ((ue ** 2) * act).sum())
+    assert Eu < 3e-2
