@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Throughput of the full total-Lagrangian vectorial LBM step on one B300.
+
+Workload (default): the 3D D3Q6x12 FP32 thick spherical shell on a 256^3 box
+(R_i = 0.4, R_o = 0.9 of the half-width, mu = 1, lambda = 5, internal nominal
+pressure with the sin^2 ramp, outer surface traction-free, c = 10, omega = 1.8,
+gamma = 10, compatibility projection every 20 steps): 5,841,344 active nodes,
+299,448 Neumann cut links.  A step is one pass of Algorithm 1 over the whole body:
+fused pull gather + cut-link closure + recovery + collision, per-link boundary
+sources (LSQ + Newton), and on every 20th step the two projection solves with the
+population repair.  Timed steps include their share of projection steps (K is a
+multiple of 20 by default).
+
+Printed: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded 64^3 copy of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and HBM GB/s (% of peak), FP32 vs FP64 at stated L2 error; adjoint/forward time"
+UNIT = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="box nodes per axis of the shell workload")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bytes_per_node(D, real_size):
+    """Algorithmic HBM bytes per active node of the fused collide-stream kernel: every
+    population component read once and written once, u* read and written, one flag byte."""
+    K, Q = D + D * D, 2 * D
+    return 2 * Q * K * real_size + 2 * D * real_size + 1
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n=64, steps=None, warmup=0, budget_s=15.0):
+    """FP64 oracle on an n^3 copy of the shell workload (single host thread)."""
+    import oracle
+    from paper_2606_20646_b300 import inputs as I
+    p = I.shell_3d(n)
+    o = oracle.Oracle(p).set_initial()
+    if warmup:
+        o.step(warmup)
+    nact = o.counts()["n_active"]
+    if steps is None:
+        t0 = time.perf_counter()
+        o.step(5)
+        dt = time.perf_counter() - t0
+        steps = max(5, int(budget_s / max(dt / 5, 1e-6)))
+        steps = (steps // 20) * 20 or 5
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return nact * steps / el / 1e6, steps, el, nact
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    t0 = time.time()
+    mlups, steps, el, nact = oracle_sample(n=64, steps=args.steps, warmup=args.warmup)
+    sample = (f"FP64 C oracle (lbm_oracle.c, 1 host thread) on the 64^3 copy of the shell workload "
+              f"({nact} active nodes), {args.warmup} untimed + {steps} timed steps incl. projection steps")
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"shell_3d_{args.n} (64^3 copy on the host)"},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.time() - t0, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2606_20646_b300 import build as b
+    b.build()
+    from paper_2606_20646_b300 import inputs as I
+    from paper_2606_20646_b300 import lbm
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peak, peak_kind = measured_peaks()
+    K, W = args.steps, args.warmup
+    p = I.shell_3d(args.n)
+
+    def timed(sim, steps, with_timing):
+        stream = sim.stream
+        torch.cuda.synchronize()
+        barrier(world)
+        if with_timing:
+            sim.enable_timing(True)
+        l0 = sim.info()["launches"]
+        clk = Clocks(torch.cuda.current_device()) if with_timing else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        clocks = clk.stop() if clk else None
+        launches = sim.info()["launches"] - l0
+        kt = sim.kernel_times() if with_timing else None
+        return ms, launches, kt, clocks
+
+    # ---- main measurement: FP32, populations resident in HBM --------------------------------
+    sim = lbm.Simulation(p, precision="fp32", device=dev)
+    sim.set_initial()
+    sim.step(W)
+    ms, launches, kt, clocks = timed(sim, K, True)
+    st = sim.sync(raise_on_status=False)
+    info = sim.info()
+    nact = info["n_active"]
+    ms = max_over_ranks(ms, world)
+    value = world * nact * K / (ms / 1e3) / 1e6
+    avg_sc = kt["stream_collide_ms"] / max(kt["stream_collide_launches"], 1)
+    bpn = bytes_per_node(3, 4)
+    achieved = nact * bpn / (avg_sc / 1e3) / 1e9
+    share = {"stream_collide": kt["stream_collide_ms"] / ms, "cutlink": kt["cutlink_ms"] / ms,
+             "projection": kt["projection_ms"] / ms}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_stream_collide<float,3,1>", "bytes_per_launch": nact * bpn,
+                "avg_launch_ms": round(avg_sc, 4), "peak_kind": peak_kind}
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- FP64 form on the same workload --------------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        sim = lbm.Simulation(p, precision="fp64", device=dev)
+        sim.set_initial()
+        sim.step(W)
+        K64 = max(20, K // 2)
+        ms64, _, kt64, _ = timed(sim, K64, True)
+        avg64 = kt64["stream_collide_ms"] / max(kt64["stream_collide_launches"], 1)
+        fp64 = {"value": round(nact * K64 / (ms64 / 1e3) / 1e6, 2), "steps": K64,
+                "stream_collide_GBps": round(nact * bytes_per_node(3, 8) / (avg64 / 1e3) / 1e9, 1),
+                "device_status": sim.sync(raise_on_status=False)}
+        del sim
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        sim = lbm.Simulation(p, precision="fp32", device=dev, host_staging=True)
+        hv = torch.from_numpy(p.v0).pin_memory()
+        hF = torch.from_numpy(p.F0).pin_memory()
+        hu = torch.from_numpy(p.u0).pin_memory()
+        outs = tuple(torch.empty(t.shape, dtype=torch.float64).pin_memory() for t in (hv, hF, hu))
+        sim.set_initial(hv, hF, hu)
+        sim.step(W)
+        sim.fields(out=outs)
+        sim.sync(raise_on_status=False)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        sim.set_initial(hv, hF, hu)
+        sim.step(K)
+        sim.fields(out=outs)
+        sim.sync(raise_on_status=False)
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        h2d = sum(t.numel() * 8 for t in (hv, hF, hu))
+        d2h = sum(t.numel() * 8 for t in outs)
+        e2e = {"value": round(world * nact * K / el / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": h2d // K, "d2h_bytes_per_step": d2h // K,
+               "note": "timed: upload of v0, F0, u0 from pinned host memory, K steps, download of v, F, u"}
+        del sim
+        torch.cuda.empty_cache()
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ---------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, steps, el, nact64 = oracle_sample(n=64, budget_s=15.0)
+        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 C oracle, 1 host thread, 64^3 copy of the shell ({nact64} active nodes), "
+                         f"{steps} steps incl. projection steps, {el:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"shell_3d_{args.n}: D3Q6x12 FP32 thick spherical shell, {args.n}^3 box, "
+                                       "R_i=0.4 R_o=0.9, mu=1 lambda=5, internal pressure sin^2 ramp, "
+                                       "projection every 20 steps",
+                           "n_active": nact, "n_cut_links": info["n_cut"], "lsq_entries": info["lsq_entries"],
+                           "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
+                "cpu_baseline": cpu, "device_status": st}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,450 @@
+// Host runtime and C ABI (include/lbm.h) of the sm_103a total-Lagrangian vectorial LBM.
+//
+// The handle owns host metadata only; all device memory is caller-provided.  Every
+// operation is enqueued on the stream given to lbm_create.  Kernels live in
+// lbm_kernels.cuh; this file validates descriptors, carves caller storage, and
+// schedules one update of Algorithm 1 per step:
+//   regular step     K3 fused gather/closure/collision  ->  K4 boundary sources
+//   projection step  gather+moments -> projection solve -> repair+collision
+//                    -> projection solve -> displacement reset -> K4
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_ops.cuh"
+
+static const PrecOps &ops(const lbm_handle *h) { return h->real_size == 8 ? ops_fp64() : ops_fp32(); }
+
+// =============================================================================================
+// storage layouts
+// =============================================================================================
+
+static void carve_geometry(lbm_handle *h, char *base, size_t *bytes) {
+    Carver c{base};
+    const long long np = h->box.npad;
+    h->flags = c.take<uint8_t>(np + 64);
+    h->lstart = c.take<int>(np);
+    h->cnt = c.take<int>(np);
+    h->segflag = c.take<int>(h->nsegmax + 1);
+    h->segidx = c.take<int>(h->nsegmax + 1);
+    h->seg = c.take<int2>(h->nsegmax + 1);
+    h->scan_scratch = c.take<int>(scan_scratch_ints(std::max<long long>(np, h->nsegmax)));
+    h->counters = c.take<unsigned long long>(8);
+    h->dshapes = c.take<ShapeD>(kMaxShapes);
+    h->dbcs = c.take<BCD>(kMaxBCs);
+    h->status = c.take<int>(8);
+    *bytes = c.off;
+}
+
+static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
+    Carver c{base};
+    const long long np = h->box.npad, nc = std::max<long long>(h->n_cut, 1);
+    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
+    h->fA = c.take<char>((size_t)Q * K * np * rs);
+    h->fB = c.take<char>((size_t)Q * K * np * rs);
+    h->ustar = c.take<char>((size_t)D * np * rs);
+    h->un = c.take<char>((size_t)D * np * rs);
+    h->dmask = c.take<uint8_t>(np);
+    h->l_node = c.take<int>(nc);
+    h->l_q = c.take<int>(nc);
+    h->l_bc = c.take<int>(nc);
+    h->l_ns = c.take<int>(nc);
+    h->l_eta = c.take<double>(nc);
+    h->l_Xb = c.take<double>(3 * nc);
+    h->l_Nb = c.take<double>(3 * nc);
+    h->l_tan = c.take<double>(6 * nc);
+    h->l_h = c.take<char>((size_t)3 * nc * rs);
+    h->l_rec = c.take<char>((size_t)(K + 2) * nc * rs);
+    if (h->has_neumann_bc) {
+        h->l_sidx = c.take<int>((size_t)kLsqCap * nc);
+        h->l_w = c.take<char>((size_t)2 * kLsqCap * nc * rs);
+        h->u0 = c.take<double>((size_t)D * np);
+        h->u1 = c.take<double>((size_t)D * np);
+        h->dA = c.take<char>((size_t)D * np * rs);
+        h->dB = c.take<char>((size_t)D * np * rs);
+        h->resid = c.take<char>((size_t)D * np * rs);
+        h->vst = c.take<char>((size_t)D * np * rs);
+        h->Gst = c.take<char>((size_t)D * D * np * rs);
+        h->partial = c.take<double>((size_t)D * (grid_for(h->nseg, 4) + 1));
+        h->mean = c.take<double>(4);
+    } else {
+        h->l_sidx = nullptr;
+        h->l_w = nullptr;
+        h->u0 = h->u1 = h->partial = h->mean = nullptr;
+        h->dA = h->dB = h->resid = h->vst = h->Gst = nullptr;
+    }
+    h->staging = h->opt.host_staging ? c.take<double>((size_t)(2 * D + D * D + D * K) * h->box.nbox) : nullptr;
+    *bytes = c.off;
+}
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+
+extern "C" {
+
+const char *lbm_error_string(int code) {
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument or descriptor";
+    case LBM_ERR_DOMAIN: return "empty body, or the body reaches a non-periodic box face";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_STORAGE: return "storage missing, too small or misaligned";
+    case LBM_ERR_STATE: return "call out of order";
+    case LBM_ERR_DEVICE: return "device status word is non-zero";
+    case LBM_ERR_CAPACITY: return "LSQ stencil capacity exceeded";
+    default: return "unknown error";
+    }
+}
+
+static int validate_grid(const lbm_grid *g) {
+    if (!g || (g->dim != 2 && g->dim != 3) || !(g->dx > 0.0) || !std::isfinite(g->dx)) return LBM_ERR_ARG;
+    for (int a = 0; a < g->dim; ++a)
+        if (g->n[a] < 1) return LBM_ERR_ARG;
+    long long nz = g->dim == 3 ? g->n[2] : 1;
+    long long nbox = (long long)g->n[0] * g->n[1] * nz;
+    if (nbox >= (1LL << 31) - 64) return LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes) {
+    if (!bytes || validate_grid(grid)) return LBM_ERR_ARG;
+    lbm_handle tmp;
+    tmp.grid = *grid;
+    long long nz = grid->dim == 3 ? grid->n[2] : 1;
+    tmp.box.nbox = (long long)grid->n[0] * grid->n[1] * nz;
+    tmp.box.npad = (tmp.box.nbox + 31) / 32 * 32;
+    tmp.segs_per_row = (grid->n[0] + 31) / 32;
+    tmp.nsegmax = (long long)tmp.segs_per_row * grid->n[1] * nz;
+    carve_geometry(&tmp, nullptr, bytes);
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material *mat, const lbm_bc *bcs, int nbc,
+               const lbm_options *opt, void *geometry_storage, size_t geometry_bytes, void *cuda_stream,
+               lbm_handle **out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (validate_grid(grid) || !ls || !mat || !opt || nbc < 0 || nbc > kMaxBCs || (nbc > 0 && !bcs))
+        return LBM_ERR_ARG;
+    if (ls->nshapes < 0 || ls->nshapes > kMaxShapes || (ls->nshapes > 0 && !ls->shapes)) return LBM_ERR_ARG;
+    if (!(mat->mu > 0.0) || !(mat->lambda > -mat->mu)) return LBM_ERR_ARG;
+    if (opt->precision != LBM_PREC_FP64 && opt->precision != LBM_PREC_FP32) return LBM_ERR_ARG;
+    if (!(opt->c > 0.0) || !(opt->omega > 0.0 && opt->omega <= 2.0) || !(opt->gamma >= 0.0)) return LBM_ERR_ARG;
+    if (opt->proj_every < 0 || opt->proj_iters < 0 || !(opt->theta_F > 0.0 && opt->theta_F <= 1.0) ||
+        !(opt->proj_beta > 0.0 && opt->proj_beta <= 1.0))
+        return LBM_ERR_ARG;
+    for (int s = 0; s < ls->nshapes; ++s) {
+        const lbm_shape &sh = ls->shapes[s];
+        if (sh.kind < 0 || sh.kind > LBM_SHAPE_HALFSPACE) return LBM_ERR_ARG;
+        if (sh.kind == LBM_SHAPE_SUPERELLIPSE && (grid->dim != 2 || !(sh.p >= 1.0))) return LBM_ERR_ARG;
+    }
+    for (int b = 0; b < nbc; ++b) {
+        const lbm_bc &bc = bcs[b];
+        if (bc.kind != LBM_BC_DIRICHLET && bc.kind != LBM_BC_NEUMANN) return LBM_ERR_ARG;
+        if (bc.ramp < 0 || bc.ramp > LBM_RAMP_TIME) return LBM_ERR_ARG;
+        if ((bc.ramp == LBM_RAMP_LINEAR || bc.ramp == LBM_RAMP_SIN2 || bc.ramp == LBM_RAMP_COS) && !(bc.t_ramp > 0.0))
+            return LBM_ERR_ARG;
+        if (bc.kind == LBM_BC_DIRICHLET && !(bc.profile >= LBM_PROFILE_ZERO && bc.profile <= LBM_PROFILE_TWIST_STRETCH))
+            return LBM_ERR_ARG;
+        if (bc.kind == LBM_BC_NEUMANN && !(bc.profile == LBM_PROFILE_ZERO || bc.profile == LBM_PROFILE_RADIAL ||
+                                           bc.profile == LBM_PROFILE_CONST))
+            return LBM_ERR_ARG;
+    }
+    size_t need = 0;
+    lbm_geometry_bytes(grid, &need);
+    if (!geometry_storage || geometry_bytes < need || (reinterpret_cast<uintptr_t>(geometry_storage) % kAlign))
+        return LBM_ERR_STORAGE;
+
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_ARG;
+    h->grid = *grid;
+    if (grid->dim == 2) {
+        h->grid.n[2] = 1;
+        h->grid.periodic[2] = 1;
+        h->grid.origin[2] = 0.0;
+    }
+    h->opt = *opt;
+    h->mat = *mat;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->D = grid->dim;
+    h->K = h->D + h->D * h->D;
+    h->Q = 2 * h->D;
+    h->real_size = opt->precision == LBM_PREC_FP64 ? 8 : 4;
+    h->nshapes = ls->nshapes;
+    for (int s = 0; s < ls->nshapes; ++s) {
+        const lbm_shape &sh = ls->shapes[s];
+        ShapeD &d = h->shapes[s];
+        d.kind = sh.kind;
+        d.complement = sh.complement != 0;
+        d.bid = sh.boundary_id;
+        for (int a = 0; a < 3; ++a) { d.c[a] = sh.center[a]; d.a[a] = sh.axes[a]; }
+        for (int a = 0; a < 9; ++a) d.Q[a] = sh.rot[a];
+        d.p = sh.p;
+    }
+    h->nbc = nbc;
+    for (int b = 0; b < nbc; ++b) {
+        const lbm_bc &bc = bcs[b];
+        BCD &d = h->bcs[b];
+        d.bid = bc.boundary_id;
+        d.kind = bc.kind;
+        d.profile = bc.profile;
+        d.ramp = bc.ramp;
+        d.t_ramp = bc.t_ramp;
+        for (int a = 0; a < 3; ++a) { d.center[a] = bc.center[a]; d.vec[a] = bc.vec[a]; }
+        for (int a = 0; a < 9; ++a) d.A[a] = bc.A[a];
+        d.amp = bc.amp;
+        if (bc.kind == LBM_BC_NEUMANN) h->has_neumann_bc = true;
+    }
+    Box &bx = h->box;
+    bx.D = h->D;
+    bx.nx = h->grid.n[0];
+    bx.ny = h->grid.n[1];
+    bx.nz = h->grid.n[2];
+    for (int a = 0; a < 3; ++a) { bx.per[a] = h->grid.periodic[a] != 0; bx.origin[a] = h->grid.origin[a]; }
+    bx.dx = h->grid.dx;
+    bx.nbox = (long long)bx.nx * bx.ny * bx.nz;
+    bx.npad = (bx.nbox + 31) / 32 * 32;
+    h->segs_per_row = (bx.nx + 31) / 32;
+    h->nsegmax = (long long)h->segs_per_row * bx.ny * bx.nz;
+    h->geo = static_cast<char *>(geometry_storage);
+    carve_geometry(h, h->geo, &h->geo_bytes);
+
+    auto fail = [&](int rc) { delete h; return rc; };
+    cudaStream_t st = h->stream;
+    if (cudaMemsetAsync(h->geo, 0, h->geo_bytes, st) != cudaSuccess) return fail(LBM_ERR_CUDA);
+    if (cudaMemcpyAsync(h->dshapes, h->shapes, sizeof(h->shapes), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(h->dbcs, h->bcs, sizeof(h->bcs), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    k_mask<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, h->dshapes, h->nshapes, h->flags);
+    k_cutbits<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, h->dshapes, h->nshapes, h->flags, h->cnt, h->counters,
+                                                       h->status);
+    if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
+    if (scan(h->cnt, h->lstart, bx.nbox, h->scan_scratch, st)) return fail(LBM_ERR_CUDA);
+    k_seg_flags<<<grid_for(h->nsegmax, 256), 256, 0, st>>>(bx, h->flags, h->segs_per_row, h->nsegmax, h->segflag);
+    if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
+    if (scan(h->segflag, h->segidx, h->nsegmax, h->scan_scratch, st)) return fail(LBM_ERR_CUDA);
+    k_seg_write<<<grid_for(h->nsegmax, 256), 256, 0, st>>>(bx, h->segflag, h->segidx, h->segs_per_row, h->nsegmax,
+                                                            h->seg);
+    if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
+    int last[4] = {0, 0, 0, 0}, stv = 0;
+    unsigned long long nact = 0;
+    if (cudaMemcpyAsync(&last[0], h->lstart + (bx.nbox - 1), sizeof(int), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&last[1], h->cnt + (bx.nbox - 1), sizeof(int), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&last[2], h->segidx + (h->nsegmax - 1), sizeof(int), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&last[3], h->segflag + (h->nsegmax - 1), sizeof(int), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&nact, h->counters, sizeof(nact), cudaMemcpyDeviceToHost, st) ||
+        cudaMemcpyAsync(&stv, h->status, sizeof(int), cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        return fail(LBM_ERR_CUDA);
+    h->n_cut = (long long)last[0] + last[1];
+    h->nseg = (long long)last[2] + last[3];
+    h->n_active = (long long)nact;
+    if (h->n_active == 0 || (stv & kStDomain)) return fail(LBM_ERR_DOMAIN);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_storage_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_ERR_ARG;
+    lbm_handle tmp = *h;
+    tmp.events.clear();
+    carve_solver(&tmp, nullptr, bytes);
+    return LBM_OK;
+}
+
+int lbm_bind_storage(lbm_handle *h, void *storage, size_t bytes) {
+    if (!h) return LBM_ERR_ARG;
+    size_t need = 0;
+    lbm_storage_bytes(h, &need);
+    if (!storage || bytes < need || (reinterpret_cast<uintptr_t>(storage) % kAlign)) return LBM_ERR_STORAGE;
+    h->sto = static_cast<char *>(storage);
+    carve_solver(h, h->sto, &h->sto_bytes);
+    cudaStream_t st = h->stream;
+    // zero everything except the large LSQ tables, which are written before use
+    CK(cudaMemsetAsync(h->sto, 0, h->sto_bytes, st));
+    int rc = ops(h).link_build(h);
+    if (rc) return rc;
+    int stv = 0;
+    CK(cudaMemcpyAsync(&stv, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> bc(h->n_cut), ns(h->n_cut);
+    if (h->n_cut) {
+        CK(cudaMemcpyAsync(bc.data(), h->l_bc, h->n_cut * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ns.data(), h->l_ns, h->n_cut * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (stv & kStNoBC) return LBM_ERR_ARG;
+    if (stv & kStCapacity) return LBM_ERR_CAPACITY;
+    h->n_neu = h->n_dir = h->lsq_entries = 0;
+    for (long long l = 0; l < h->n_cut; ++l) {
+        if (h->bcs[bc[l]].kind == LBM_BC_NEUMANN) { h->n_neu++; h->lsq_entries += ns[l]; }
+        else h->n_dir++;
+    }
+    h->bound = true;
+    h->initialized = false;
+    return LBM_OK;
+}
+
+int lbm_set_initial(lbm_handle *h, int mode, const double *v0, const double *F0, const double *u0, const double *dU0) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->bound) return LBM_ERR_STATE;
+    if (!v0 || !F0 || !u0 || (mode != LBM_INIT_EQUILIBRIUM && mode != LBM_INIT_CHARACTERISTIC)) return LBM_ERR_ARG;
+    const int D = h->D, K = h->K;
+    const long long N = h->box.nbox;
+    const double *pv = v0, *pF = F0, *pu = u0, *pd = dU0;
+    if (!is_device_ptr(v0) || !is_device_ptr(F0) || !is_device_ptr(u0) || (dU0 && !is_device_ptr(dU0))) {
+        if (!h->staging) return LBM_ERR_ARG;
+        double *s = h->staging;
+        auto stage = [&](const double *src, double *dst, size_t n) {
+            return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h->stream);
+        };
+        pv = s;
+        pF = s + (size_t)D * N;
+        pu = s + (size_t)(D + D * D) * N;
+        pd = dU0 ? s + (size_t)(2 * D + D * D) * N : nullptr;
+        CK(stage(v0, const_cast<double *>(pv), (size_t)D * N));
+        CK(stage(F0, const_cast<double *>(pF), (size_t)D * D * N));
+        CK(stage(u0, const_cast<double *>(pu), (size_t)D * N));
+        if (dU0) CK(stage(dU0, const_cast<double *>(pd), (size_t)D * K * N));
+    }
+    int rc = ops(h).init(h, mode, pv, pF, pu, pd);
+    if (rc) return rc;
+    h->phase = 0;
+    h->step = 0;
+    h->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    if (!h->initialized) return LBM_ERR_STATE;
+    return ops(h).step(h, nsteps);
+}
+
+int lbm_fields(lbm_handle *h, double *v, double *F, double *u) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->initialized) return LBM_ERR_STATE;
+    const int D = h->D;
+    const long long N = h->box.nbox;
+    double *ptr[3] = {v, F, u};
+    const size_t cnt[3] = {(size_t)D * N, (size_t)D * D * N, (size_t)D * N};
+    double *dev[3] = {nullptr, nullptr, nullptr};
+    bool host[3] = {false, false, false};
+    size_t off = 0;
+    for (int j = 0; j < 3; ++j) {
+        if (!ptr[j]) { off += cnt[j]; continue; }
+        if (is_device_ptr(ptr[j])) {
+            dev[j] = ptr[j];
+        } else {
+            if (!h->staging) return LBM_ERR_ARG;
+            dev[j] = h->staging + off;
+            host[j] = true;
+        }
+        off += cnt[j];
+        CK(cudaMemsetAsync(dev[j], 0, cnt[j] * sizeof(double), h->stream));
+    }
+    int rc = ops(h).fields(h, dev[0], dev[1], dev[2]);
+    if (rc) return rc;
+    for (int j = 0; j < 3; ++j)
+        if (host[j]) CK(cudaMemcpyAsync(ptr[j], dev[j], cnt[j] * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h, int *device_status) {
+    if (!h) return LBM_ERR_ARG;
+    int stv = 0;
+    CK(cudaMemcpyAsync(&stv, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (device_status) *device_status = stv & 31;
+    if (stv & 31) {
+        CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return LBM_ERR_DEVICE;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_info(const lbm_handle *h, lbm_info *info) {
+    if (!h || !info) return LBM_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_box = h->box.nbox;
+    info->n_active = h->n_active;
+    info->n_cut = h->n_cut;
+    info->n_neumann = h->n_neu;
+    info->n_dirichlet = h->n_dir;
+    info->n_segments = h->nseg;
+    info->step = h->step;
+    info->dt = h->grid.dx / h->opt.c;
+    info->t = h->step * info->dt;
+    info->geometry_bytes = h->geo_bytes;
+    size_t sb = 0;
+    lbm_storage_bytes(h, &sb);
+    info->storage_bytes = sb;
+    info->launches = h->launches;
+    info->lsq_entries = h->lsq_entries;
+    return LBM_OK;
+}
+
+int lbm_enable_timing(lbm_handle *h, int enable) {
+    if (!h) return LBM_ERR_ARG;
+    timing_fold(h);
+    h->timing = enable != 0;
+    for (int i = 0; i < 3; ++i) { h->acc_ms[i] = 0.0; h->acc_n[i] = 0; }
+    return LBM_OK;
+}
+
+int lbm_kernel_times(lbm_handle *h, lbm_kernel_time *out) {
+    if (!h || !out) return LBM_ERR_ARG;
+    timing_fold(h);
+    out->stream_collide_ms = h->acc_ms[0];
+    out->cutlink_ms = h->acc_ms[1];
+    out->projection_ms = h->acc_ms[2];
+    out->stream_collide_launches = h->acc_n[0];
+    out->cutlink_launches = h->acc_n[1];
+    out->projection_launches = h->acc_n[2];
+    return LBM_OK;
+}
+
+int lbm_copy_links(lbm_handle *h, long long *node, int *q, double *eta, double *Xb, double *Nb, int *bid, int *ns) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->bound) return LBM_ERR_STATE;
+    const long long n = h->n_cut;
+    if (n == 0) return LBM_OK;
+    std::vector<int> nd(n), bc(n);
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(nd.data(), h->l_node, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(bc.data(), h->l_bc, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (q) CK(cudaMemcpyAsync(q, h->l_q, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (eta) CK(cudaMemcpyAsync(eta, h->l_eta, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (Xb) CK(cudaMemcpyAsync(Xb, h->l_Xb, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (Nb) CK(cudaMemcpyAsync(Nb, h->l_Nb, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (ns) CK(cudaMemcpyAsync(ns, h->l_ns, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (long long l = 0; l < n; ++l) {
+        if (node) node[l] = nd[l];
+        if (bid) bid[l] = h->bcs[bc[l]].bid;
+    }
+    return LBM_OK;
+}
+
+int lbm_copy_active(lbm_handle *h, unsigned char *mask) {
+    if (!h || !mask) return LBM_ERR_ARG;
+    const long long N = h->box.nbox;
+    std::vector<uint8_t> fl(N);
+    CK(cudaMemcpyAsync(fl.data(), h->flags, N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < N; ++i) mask[i] = (fl[i] & kActive) ? 1 : 0;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    timing_fold(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+// Device-side building blocks of the sm_103a total-Lagrangian vectorial LBM:
+// descriptors, level-set primitives (FP64), boundary data, the neo-Hookean
+// stress and small dense algebra.  Used by the kernels in lbm_kernels.cuh.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tlv {
+
+constexpr int kMaxShapes = 16;
+constexpr int kMaxBCs = 16;
+constexpr int kLsqCap = 160;      // LSQ stencil capacity per link (active nodes within 3 dx)
+constexpr double kLsqRho2 = 9.0;  // squared stencil radius in lattice units
+
+// flags byte per box node
+constexpr uint8_t kActive = 1u << 6;   // phi(X) <= 0
+constexpr uint8_t kNeedU = 1u << 7;    // u^n is read by some Neumann LSQ stencil
+constexpr uint8_t kCutMask = 0x3f;     // bit q: link (m, q) is cut (neighbour m + e_q inactive)
+
+// device status bits (mirrors lbm_device_status of the C ABI)
+constexpr int kStNonfinite = 1, kStJacobian = 2, kStNewton = 4, kStLsq = 8, kStCapacity = 16, kStDomain = 32,
+              kStNoBC = 64;
+
+struct ShapeD {
+    int kind, complement, bid, pad;
+    double c[3], a[3], Q[9], p;
+};
+
+struct BCD {
+    int bid, kind, profile, ramp;
+    double t_ramp, center[3], A[9], vec[3], amp;
+};
+
+// ---------------------------------------------------------------------------------------------
+// level set: phi = max over shapes (Sec. 3.1, Eq. level-set-domain)
+// ---------------------------------------------------------------------------------------------
+
+__device__ inline double shape_phi(const ShapeD &s, int D, const double X[3], double g[3]) {
+    const double d0 = X[0] - s.c[0], d1 = X[1] - s.c[1], d2 = (D == 3) ? X[2] - s.c[2] : 0.0;
+    double v;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    switch (s.kind) {
+    case 0: {  // sphere / circle
+        double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        v = r - s.a[0];
+        if (r > 0.0) { gx = d0 / r; gy = d1 / r; gz = d2 / r; }
+        break;
+    }
+    case 1: {  // ellipsoid, xi = Q^T d
+        double xi[3], gl[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a) xi[a] = s.Q[0 * 3 + a] * d0 + s.Q[1 * 3 + a] * d1 + s.Q[2 * 3 + a] * d2;
+        v = -1.0;
+        for (int a = 0; a < D; ++a) {
+            double r = xi[a] / s.a[a];
+            v += r * r;
+            gl[a] = 2.0 * xi[a] / (s.a[a] * s.a[a]);
+        }
+        gx = s.Q[0] * gl[0] + s.Q[1] * gl[1] + s.Q[2] * gl[2];
+        gy = s.Q[3] * gl[0] + s.Q[4] * gl[1] + s.Q[5] * gl[2];
+        gz = s.Q[6] * gl[0] + s.Q[7] * gl[1] + s.Q[8] * gl[2];
+        break;
+    }
+    case 2: {  // superellipse (2D)
+        double xi0 = s.Q[0] * d0 + s.Q[3] * d1, xi1 = s.Q[1] * d0 + s.Q[4] * d1;
+        double r0 = fabs(xi0 / s.a[0]), r1 = fabs(xi1 / s.a[1]);
+        v = pow(r0, s.p) + pow(r1, s.p) - 1.0;
+        double s0 = xi0 > 0.0 ? 1.0 : (xi0 < 0.0 ? -1.0 : 0.0);
+        double s1 = xi1 > 0.0 ? 1.0 : (xi1 < 0.0 ? -1.0 : 0.0);
+        double g0 = s.p * pow(r0, s.p - 1.0) * s0 / s.a[0], g1 = s.p * pow(r1, s.p - 1.0) * s1 / s.a[1];
+        gx = s.Q[0] * g0 + s.Q[1] * g1;
+        gy = s.Q[3] * g0 + s.Q[4] * g1;
+        break;
+    }
+    case 3: {  // cylinder about X_3
+        double r = sqrt(d0 * d0 + d1 * d1);
+        v = r - s.a[0];
+        if (r > 0.0) { gx = d0 / r; gy = d1 / r; }
+        break;
+    }
+    case 4:  // half-space with outward normal a
+        v = s.a[0] * d0 + s.a[1] * d1 + ((D == 3) ? s.a[2] * d2 : 0.0);
+        gx = s.a[0]; gy = s.a[1]; gz = s.a[2];
+        break;
+    default:
+        v = 1.0;
+    }
+    if (D == 2) gz = 0.0;
+    if (s.complement) { v = -v; gx = -gx; gy = -gy; gz = -gz; }
+    if (g) { g[0] = gx; g[1] = gy; g[2] = gz; }
+    return v;
+}
+
+__device__ inline double levelset(const ShapeD *__restrict__ shapes, int ns, int D, const double X[3], int *which) {
+    if (ns == 0) { if (which) *which = -1; return -1.0; }
+    double best = 0.0;
+    int w = -1;
+    for (int s = 0; s < ns; ++s) {
+        double v = shape_phi(shapes[s], D, X, nullptr);
+        if (w < 0 || v > best) { best = v; w = s; }
+    }
+    if (which) *which = w;
+    return best;
+}
+
+// ---------------------------------------------------------------------------------------------
+// boundary data: ramps s(t), Dirichlet displacement/velocity, nominal traction
+// ---------------------------------------------------------------------------------------------
+
+__device__ inline void ramp_eval(int kind, double T, double t, double &s, double &sd) {
+    const double pi = 3.14159265358979323846;
+    switch (kind) {
+    case 1: if (t < T) { s = t / T; sd = 1.0 / T; } else { s = 1.0; sd = 0.0; } return;
+    case 2: if (t < T) { double a = sin(pi * t / (2.0 * T)); s = a * a; sd = pi / (2.0 * T) * sin(pi * t / T); }
+            else { s = 1.0; sd = 0.0; } return;
+    case 3: if (t < T) { s = 0.5 * (1.0 - cos(pi * t / T)); sd = pi / (2.0 * T) * sin(pi * t / T); }
+            else { s = 1.0; sd = 0.0; } return;
+    case 4: s = t; sd = 1.0; return;
+    default: s = 1.0; sd = 0.0;
+    }
+}
+
+// velocity (want_u = false) or displacement (want_u = true) of a Dirichlet profile at X, t
+__device__ inline void dirichlet_eval(const BCD &bc, int D, const double X[3], double t, bool want_u, double out[3]) {
+    double s, sd;
+    ramp_eval(bc.ramp, bc.t_ramp, t, s, sd);
+    const double a = want_u ? s : sd;
+    out[0] = out[1] = out[2] = 0.0;
+    const double d[3] = {X[0] - bc.center[0], X[1] - bc.center[1], (D == 3) ? X[2] - bc.center[2] : 0.0};
+    switch (bc.profile) {
+    case 1:
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) out[i] += a * bc.A[i * 3 + j] * d[j];
+        break;
+    case 2: {
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int i = 0; i < D; ++i) out[i] = bc.amp * a * d[i] / r;
+        break;
+    }
+    case 3: {
+        double al = s * bc.amp;
+        if (want_u) {
+            out[0] = (cos(al) - 1.0) * d[0] - sin(al) * d[1];
+            out[1] = sin(al) * d[0] + (cos(al) - 1.0) * d[1];
+            if (D == 3) out[2] = s * bc.vec[2];
+        } else {
+            double ald = sd * bc.amp;
+            out[0] = ald * (-sin(al) * d[0] - cos(al) * d[1]);
+            out[1] = ald * (cos(al) * d[0] - sin(al) * d[1]);
+            if (D == 3) out[2] = sd * bc.vec[2];
+        }
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+__device__ inline void traction_eval(const BCD &bc, int D, const double X[3], double t, double T[3]) {
+    double s, sd;
+    ramp_eval(bc.ramp, bc.t_ramp, t, s, sd);
+    T[0] = T[1] = T[2] = 0.0;
+    if (bc.profile == 2) {
+        const double d[3] = {X[0] - bc.center[0], X[1] - bc.center[1], (D == 3) ? X[2] - bc.center[2] : 0.0};
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int i = 0; i < D; ++i) T[i] = bc.amp * s * d[i] / r;
+    } else if (bc.profile == 4) {
+        for (int i = 0; i < D; ++i) T[i] = s * bc.vec[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// constitutive law: compressible neo-Hookean (Sec. 4.1, Eq. validation-nh-energy)
+//   P = mu F + (lam/2 (J^2 - 1) - mu) F^{-T}
+// ---------------------------------------------------------------------------------------------
+
+template <typename real, int D> __device__ __forceinline__ real det(const real F[D * D]) {
+    if constexpr (D == 2) {
+        return F[0] * F[3] - F[1] * F[2];
+    } else {
+        return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+               F[2] * (F[3] * F[7] - F[4] * F[6]);
+    }
+}
+
+// cofactor matrix cof(F) = J F^{-T}
+template <typename real, int D> __device__ __forceinline__ void cofactor(const real F[D * D], real C[D * D]) {
+    if constexpr (D == 2) {
+        C[0] = F[3]; C[1] = -F[2]; C[2] = -F[1]; C[3] = F[0];
+    } else {
+        C[0] = F[4] * F[8] - F[5] * F[7];
+        C[1] = F[5] * F[6] - F[3] * F[8];
+        C[2] = F[3] * F[7] - F[4] * F[6];
+        C[3] = F[2] * F[7] - F[1] * F[8];
+        C[4] = F[0] * F[8] - F[2] * F[6];
+        C[5] = F[1] * F[6] - F[0] * F[7];
+        C[6] = F[1] * F[5] - F[2] * F[4];
+        C[7] = F[2] * F[3] - F[0] * F[5];
+        C[8] = F[0] * F[4] - F[1] * F[3];
+    }
+}
+
+// first Piola stress; returns J
+template <typename real, int D>
+__device__ __forceinline__ real piola(const real F[D * D], real mu, real lam, real P[D * D]) {
+    real C[D * D];
+    cofactor<real, D>(F, C);
+    const real J = det<real, D>(F);
+    const real s = real(0.5) * lam * (J * J - real(1)) - mu;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) P[k] = mu * F[k] + s * (C[k] / J);  // F^{-T} = cof(F) / J
+    return J;
+}
+
+// dense D x D solve by Cramer's rule (D = 2, 3); returns false if singular
+template <typename real, int D> __device__ __forceinline__ bool solve_small(const real A[D * D], const real b[D], real x[D]) {
+    const real J = det<real, D>(A);
+    if (!(J != real(0)) || !isfinite(J)) return false;
+    real C[D * D];
+    cofactor<real, D>(A, C);  // A^{-1} = C^T / J
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        real acc = 0;
+        #pragma unroll
+        for (int j = 0; j < D; ++j) acc += C[j * D + i] * b[j];
+        x[i] = acc / J;
+    }
+    return true;
+}
+
+}  // namespace tlv

@@ -1,0 +1,365 @@
+// Host-side orchestration shared by the precision-specific translation units: the handle,
+// storage carving helpers, and Impl<real, D> which launches the kernels of one update.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace tlv;
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T> T *take(size_t count) {
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off = align_up(off + count * sizeof(T));
+        return p;
+    }
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+struct lbm_handle {
+    lbm_grid grid{};
+    lbm_options opt{};
+    lbm_material mat{};
+    int nshapes = 0, nbc = 0;
+    ShapeD shapes[kMaxShapes]{};
+    BCD bcs[kMaxBCs]{};
+    bool has_neumann_bc = false;
+    cudaStream_t stream = nullptr;
+    int D = 0, K = 0, Q = 0;
+    int real_size = 8;
+    Box box{};
+    int segs_per_row = 0;
+    long long nsegmax = 0;
+    // geometry storage
+    char *geo = nullptr;
+    size_t geo_bytes = 0;
+    uint8_t *flags = nullptr;
+    int *lstart = nullptr, *cnt = nullptr, *scan_scratch = nullptr, *segflag = nullptr, *segidx = nullptr;
+    int2 *seg = nullptr;
+    unsigned long long *counters = nullptr;
+    ShapeD *dshapes = nullptr;
+    BCD *dbcs = nullptr;
+    int *status = nullptr;
+    long long n_active = 0, n_cut = 0, nseg = 0;
+    // solver storage
+    char *sto = nullptr;
+    size_t sto_bytes = 0;
+    bool bound = false;
+    void *fA = nullptr, *fB = nullptr, *ustar = nullptr, *un = nullptr, *vst = nullptr, *Gst = nullptr;
+    uint8_t *dmask = nullptr;
+    int *l_node = nullptr, *l_q = nullptr, *l_bc = nullptr, *l_ns = nullptr, *l_sidx = nullptr;
+    double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
+    void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr;
+    double *u0 = nullptr, *u1 = nullptr, *partial = nullptr, *mean = nullptr, *staging = nullptr;
+    void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
+    long long n_neu = 0, n_dir = 0, lsq_entries = 0;
+    // state
+    bool initialized = false;
+    int phase = 0;  // 0: fA holds pre-collision f^0; 1: fA holds post-collision f*^{n-1}
+    long long step = 0;
+    long long launches = 0;
+    // timing
+    bool timing = false;
+    std::vector<EventPair> events;
+    double acc_ms[3] = {0, 0, 0};
+    long long acc_n[3] = {0, 0, 0};
+};
+
+// =============================================================================================
+// helpers
+// =============================================================================================
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return LBM_ERR_CUDA;        \
+    } while (0)
+
+#define CKL()                                              \
+    do {                                                   \
+        cudaError_t e_ = cudaGetLastError();               \
+        if (e_ != cudaSuccess) return LBM_ERR_CUDA;        \
+    } while (0)
+
+inline bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+inline unsigned grid_for(long long n, int per_block) { return (unsigned)((n + per_block - 1) / per_block); }
+
+inline size_t scan_scratch_ints(long long n) {
+    size_t s = 0;
+    while (n > 1) {
+        long long nb = (n + 1023) / 1024;
+        s += 2 * (size_t)nb + 32;
+        n = nb;
+    }
+    return s + 64;
+}
+
+// exclusive scan of n ints (in -> out) using scratch; returns LBM_OK or LBM_ERR_CUDA
+inline int scan(const int *in, int *out, long long n, int *scratch, cudaStream_t st) {
+    long long nb = (n + 1023) / 1024;
+    int *bsum = scratch, *boff = scratch + nb + 16;
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in, out, bsum, n);
+    CKL();
+    if (nb > 1) {
+        int rc = scan(bsum, boff, nb, boff + nb + 16, st);
+        if (rc) return rc;
+        k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, boff, n);
+        CKL();
+    }
+    return LBM_OK;
+}
+
+inline void timing_begin(lbm_handle *h, EventPair &ep, int cls) {
+    ep.cls = cls;
+    cudaEventCreate(&ep.a);
+    cudaEventCreate(&ep.b);
+    cudaEventRecord(ep.a, h->stream);
+}
+
+inline void timing_end(lbm_handle *h, EventPair &ep) {
+    cudaEventRecord(ep.b, h->stream);
+    h->events.push_back(ep);
+}
+
+inline void timing_fold(lbm_handle *h) {
+    for (auto &ep : h->events) {
+        cudaEventSynchronize(ep.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ep.a, ep.b);
+        h->acc_ms[ep.cls] += ms;
+        h->acc_n[ep.cls] += 1;
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    h->events.clear();
+}
+
+// =============================================================================================
+// precision- and dimension-specialised operations
+// =============================================================================================
+
+template <typename real, int D> struct Impl {
+    static constexpr int K = D + D * D, Q = 2 * D, LREC = K + 2;
+
+    static LinkGeom<real> links(lbm_handle *h) {
+        LinkGeom<real> L;
+        L.node = h->l_node;
+        L.q = h->l_q;
+        L.bc = h->l_bc;
+        L.eta = h->l_eta;
+        L.Xb = h->l_Xb;
+        L.Nb = h->l_Nb;
+        L.tan = h->l_tan;
+        L.h = static_cast<real *>(h->l_h);
+        L.ns = h->l_ns;
+        L.sidx = h->l_sidx;
+        L.w = static_cast<real *>(h->l_w);
+        L.rec = static_cast<real *>(h->l_rec);
+        L.ncut = h->n_cut;
+        return L;
+    }
+
+    static StepArgs<real> step_args(lbm_handle *h) {
+        StepArgs<real> a;
+        a.b = h->box;
+        a.seg = h->seg;
+        a.nseg = (int)h->nseg;
+        a.flags = h->flags;
+        a.lstart = h->lstart;
+        a.fsrc = static_cast<const real *>(h->fA);
+        a.fdst = static_cast<real *>(h->fB);
+        a.ustar = static_cast<real *>(h->ustar);
+        a.un = static_cast<real *>(h->un);
+        a.lrec = static_cast<const real *>(h->l_rec);
+        a.vst = static_cast<real *>(h->vst);
+        a.Gst = static_cast<real *>(h->Gst);
+        a.u0 = h->u0;
+        const double dt = h->grid.dx / h->opt.c;
+        a.dt = (real)dt;
+        a.c = (real)h->opt.c;
+        a.omega = (real)h->opt.omega;
+        a.gamma = (real)h->opt.gamma;
+        a.mu = (real)h->mat.mu;
+        a.lam = (real)h->mat.lambda;
+        for (int i = 0; i < 3; ++i) a.bf[i] = (real)h->opt.body_force[i];
+        a.status = h->status;
+        return a;
+    }
+
+    static ProjArgs<real> proj_args(lbm_handle *h, double t, const double *warm) {
+        ProjArgs<real> p;
+        p.b = h->box;
+        p.seg = h->seg;
+        p.nseg = (int)h->nseg;
+        p.flags = h->flags;
+        p.dmask = h->dmask;
+        p.lstart = h->lstart;
+        p.L = links(h);
+        p.bcs = h->dbcs;
+        p.Gst = static_cast<const real *>(h->Gst);
+        p.u0 = warm;
+        p.resid = static_cast<real *>(h->resid);
+        p.t = t;
+        p.beta = h->opt.proj_beta;
+        return p;
+    }
+
+    static int link_build(lbm_handle *h) {
+        if (h->nseg == 0) return LBM_OK;
+        k_link_build<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
+            h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, h->dshapes, h->nshapes, h->dbcs, h->nbc,
+            links(h), h->status);
+        CKL();
+        return LBM_OK;
+    }
+
+    static int init(lbm_handle *h, int mode, const double *v0, const double *F0, const double *u0, const double *dU0) {
+        const double dt = h->grid.dx / h->opt.c;
+        k_init<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
+            h->box, h->seg, (int)h->nseg, h->flags, v0, F0, u0, dU0, mode == LBM_INIT_CHARACTERISTIC, h->opt.c, dt,
+            h->mat.mu, h->mat.lambda, h->opt.gamma, h->opt.body_force[0], h->opt.body_force[1], h->opt.body_force[2],
+            static_cast<real *>(h->fA), static_cast<real *>(h->ustar));
+        CKL();
+        return LBM_OK;
+    }
+
+    static int cutlinks(lbm_handle *h, double t) {
+        if (h->n_cut == 0) return LBM_OK;
+        CutArgs<real> a;
+        a.L = links(h);
+        a.bcs = h->dbcs;
+        a.un = static_cast<const real *>(h->un);
+        a.npad = h->box.npad;
+        a.t = t;
+        a.dt = h->grid.dx / h->opt.c;
+        a.c = h->opt.c;
+        a.mu = h->mat.mu;
+        a.lam = h->mat.lambda;
+        a.D = D;
+        a.status = h->status;
+        EventPair ep;
+        if (h->timing) timing_begin(h, ep, 1);
+        k_cutlinks<real, D><<<grid_for(h->n_cut, 128), 128, 0, h->stream>>>(a);
+        if (h->timing) timing_end(h, ep);
+        h->launches++;
+        CKL();
+        return LBM_OK;
+    }
+
+    // one projection solve from the warm start `warm` (FP64): FP64 residual, proj_iters damped-Jacobi
+    // sweeps on the correction d (population precision), gauge shift into h->mean (zero when Dirichlet
+    // anchors exist).  Returns the final correction buffer in *d.
+    static int solve(lbm_handle *h, double t, const double *warm, real **d) {
+        ProjArgs<real> p = proj_args(h, t, warm);
+        const unsigned g = grid_for(h->nseg, 4);
+        k_proj_residual<real, D><<<g, 128, 0, h->stream>>>(p);
+        h->launches++;
+        CKL();
+        real *A = static_cast<real *>(h->dA), *B = static_cast<real *>(h->dB);
+        const real *src = nullptr;
+        real *dst = A;
+        for (int it = 0; it < h->opt.proj_iters; ++it) {
+            k_jacobi<real, D><<<g, 128, 0, h->stream>>>(p, src, dst);
+            h->launches++;
+            src = dst;
+            dst = (dst == A) ? B : A;
+        }
+        CKL();
+        if (!src) {  // no sweeps: zero correction
+            CK(cudaMemsetAsync(A, 0, (size_t)D * h->box.npad * sizeof(real), h->stream));
+            src = A;
+        }
+        if (h->n_dir == 0) {
+            k_reduce_partial<real, D><<<g, 128, 0, h->stream>>>(p, src, h->partial);
+            k_reduce_final<D><<<1, 256, 0, h->stream>>>(h->partial, (int)g, 1.0 / (double)h->n_active, h->mean);
+            h->launches += 2;
+            CKL();
+        } else {
+            CK(cudaMemsetAsync(h->mean, 0, D * sizeof(double), h->stream));
+        }
+        *d = const_cast<real *>(src);
+        return LBM_OK;
+    }
+
+    static int step(lbm_handle *h, int nsteps) {
+        const double dt = h->grid.dx / h->opt.c;
+        for (int n = 0; n < nsteps; ++n) {
+            const double t = h->step * dt;
+            StepArgs<real> a = step_args(h);
+            const bool proj = h->n_neu > 0 && h->opt.proj_every > 0 && (h->step % h->opt.proj_every) == 0;
+            const unsigned g = grid_for(h->nseg, 4);
+            if (!proj) {
+                EventPair ep;
+                if (h->timing) timing_begin(h, ep, 0);
+                if (h->phase == 0) k_stream_collide<real, D, 0><<<g, 128, 0, h->stream>>>(a);
+                else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                if (h->timing) timing_end(h, ep);
+                h->launches++;
+                CKL();
+            } else {
+                EventPair ep;
+                if (h->timing) timing_begin(h, ep, 2);
+                if (h->phase == 0) k_gather_moments<real, D, 0><<<g, 128, 0, h->stream>>>(a);
+                else k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                h->launches++;
+                CKL();
+                real *d = nullptr;
+                int rc = solve(h, t, h->u0, &d);
+                if (rc) return rc;
+                k_repair_collide<real, D><<<g, 128, 0, h->stream>>>(a, h->u0, d, h->mean, h->opt.theta_F, h->u1);
+                h->launches++;
+                CKL();
+                rc = solve(h, t, h->u1, &d);
+                if (rc) return rc;
+                k_proj_reset<real, D><<<g, 128, 0, h->stream>>>(a, h->u1, d, h->mean);
+                h->launches++;
+                CKL();
+                if (h->timing) timing_end(h, ep);
+            }
+            int rc = cutlinks(h, t);
+            if (rc) return rc;
+            std::swap(h->fA, h->fB);
+            h->phase = 1;
+            h->step++;
+        }
+        return LBM_OK;
+    }
+
+    static int fields(lbm_handle *h, double *v, double *F, double *u) {
+        StepArgs<real> a = step_args(h);
+        const unsigned g = grid_for(h->nseg, 4);
+        if (h->phase == 0) k_fields<real, D, 0><<<g, 128, 0, h->stream>>>(a, v, F, u);
+        else k_fields<real, D, 1><<<g, 128, 0, h->stream>>>(a, v, F, u);
+        CKL();
+        return LBM_OK;
+    }
+};
+

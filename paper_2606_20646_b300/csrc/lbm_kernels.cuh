@@ -1,0 +1,1227 @@
+// sm_103a kernels of the total-Lagrangian vectorial LBM on embedded curved domains.
+//
+// Storage (device, caller-owned):
+//   populations  f~ = f - f^eq(0, I): one plane per (q, k), plane (q*K + k) of npad
+//                entries, node index x + nx*(y + ny*z).  Only the F-diagonal rows are
+//                shifted (by 1/(2D)), so F - I is summed without cancellation.
+//   flags        one byte per node: bit q = link (m, q) cut, kActive, kNeedU.
+//   links        cut links sorted by (node, q); record = [eta, kind, S~_0..S~_{K-1}].
+// The stored population state between steps is post-collision f*^{n-1}; the next
+// step's pull gather performs the streaming (Eq. streaming-general-d) and the cut-link
+// reconstruction (Eqs. bfl-eta-ge-half, bfl-eta-lt-half) before recovering U^num.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace tlv {
+
+// FP32 populations are stored shifted by f^eq(0, I); FP64 populations are stored raw and their
+// arithmetic follows the FP64 oracle operation for operation (its translation unit is built
+// without FMA contraction), so the FP64 form reproduces the oracle to rounding.
+template <typename real> constexpr bool kShifted = sizeof(real) == 4;
+
+template <typename real, int D> __device__ __forceinline__ real div2D(real x) {
+    if constexpr (kShifted<real>) return x * (real(1) / real(2 * D));
+    else return x / real(2 * D);
+}
+
+struct Box {
+    int D, nx, ny, nz;
+    int per[3];
+    int pad;
+    long long nbox, npad;
+    double dx, origin[3];
+};
+
+__device__ __forceinline__ void node_xyz(const Box &b, int node, int &x, int &y, int &z) {
+    x = node % b.nx;
+    int r = node / b.nx;
+    y = r % b.ny;
+    z = r / b.ny;
+}
+
+// neighbour m + e_q with periodic wrap (callers only use it for in-box or periodic neighbours)
+__device__ __forceinline__ int nbr(const Box &b, int node, int x, int y, int z, int q) {
+    const int A = q >> 1, s = (q & 1) ? -1 : 1;
+    if (A == 0) {
+        int xn = x + s;
+        xn = xn < 0 ? xn + b.nx : (xn >= b.nx ? xn - b.nx : xn);
+        return node + (xn - x);
+    } else if (A == 1) {
+        int yn = y + s;
+        yn = yn < 0 ? yn + b.ny : (yn >= b.ny ? yn - b.ny : yn);
+        return node + (yn - y) * b.nx;
+    } else {
+        int zn = z + s;
+        zn = zn < 0 ? zn + b.nz : (zn >= b.nz ? zn - b.nz : zn);
+        return node + (zn - z) * b.nx * b.ny;
+    }
+}
+
+__device__ __forceinline__ void node_X(const Box &b, int x, int y, int z, double X[3]) {
+    X[0] = b.origin[0] + (x + 0.5) * b.dx;
+    X[1] = b.origin[1] + (y + 0.5) * b.dx;
+    X[2] = (b.D == 3) ? b.origin[2] + (z + 0.5) * b.dx : 0.0;
+}
+
+__device__ __forceinline__ void set_status(int *st, int bits) {
+    if (bits) atomicOr(st, bits);
+}
+
+// =============================================================================================
+// geometry pass (FP64)
+// =============================================================================================
+
+static __global__ void k_mask(Box b, const ShapeD *__restrict__ shapes, int nshapes, uint8_t *flags) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= b.nbox) return;
+    int x, y, z;
+    node_xyz(b, (int)i, x, y, z);
+    double X[3];
+    node_X(b, x, y, z, X);
+    flags[i] = (levelset(shapes, nshapes, b.D, X, nullptr) <= 0.0) ? kActive : 0;
+}
+
+// cut bits (link (m,q) cut iff m + e_q is outside the body or outside a non-periodic box)
+static __global__ void k_cutbits(Box b, const ShapeD *__restrict__ shapes, int nshapes, uint8_t *flags, int *cnt,
+                          unsigned long long *n_active, int *status) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool act = false;
+    if (i < b.nbox) {
+        int node = (int)i;
+        uint8_t fl = flags[node];
+        act = fl & kActive;
+        int c = 0;
+        if (act) {
+            int x, y, z;
+            node_xyz(b, node, x, y, z);
+            uint8_t bits = 0;
+            for (int q = 0; q < 2 * b.D; ++q) {
+                const int A = q >> 1, s = (q & 1) ? -1 : 1;
+                const int co = (A == 0 ? x : (A == 1 ? y : z)) + s;
+                const int n = (A == 0 ? b.nx : (A == 1 ? b.ny : b.nz));
+                if ((co < 0 || co >= n) && !b.per[A]) {
+                    double X[3];
+                    node_X(b, x, y, z, X);
+                    X[A] += s * b.dx;
+                    if (!(levelset(shapes, nshapes, b.D, X, nullptr) > 0.0)) set_status(status, kStDomain);
+                    bits |= (1u << q);
+                } else if (!(flags[nbr(b, node, x, y, z, q)] & kActive)) {
+                    bits |= (1u << q);
+                }
+            }
+            // only this thread writes this byte; neighbours read bit 6, which is unchanged
+            flags[node] = fl | bits;
+            c = __popc(bits);
+        }
+        cnt[node] = c;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(n_active, (unsigned long long)__popc(mask));
+}
+
+// exclusive scan, 1024 elements per block; block totals to bsum
+static __global__ void k_scan_block(const int *__restrict__ in, int *out, int *bsum, long long n) {
+    __shared__ int wsum[32];
+    long long i = blockIdx.x * 1024LL + threadIdx.x;
+    int v = (i < n) ? in[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int s = wsum[lane];
+        int si = s;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        wsum[lane] = si - s;
+        if (lane == 31) bsum[blockIdx.x] = si;
+    }
+    __syncthreads();
+    if (i < n) out[i] = incl - v + wsum[w];
+}
+
+static __global__ void k_scan_add(int *out, const int *__restrict__ boff, long long n) {
+    long long i = blockIdx.x * 1024LL + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+// one flag per 32-node x-segment of a row: does it hold an active node?
+static __global__ void k_seg_flags(Box b, const uint8_t *__restrict__ flags, int segs_per_row, long long nsegmax, int *segflag) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= nsegmax) return;
+    int row = (int)(s / segs_per_row), j = (int)(s % segs_per_row);
+    int x0 = 32 * j, x1 = min(x0 + 32, b.nx);
+    const uint8_t *r = flags + (long long)row * b.nx;
+    int any = 0;
+    for (int x = x0; x < x1; ++x) any |= (r[x] & kActive) ? 1 : 0;
+    segflag[s] = any;
+}
+
+static __global__ void k_seg_write(Box b, const int *__restrict__ segflag, const int *__restrict__ segidx, int segs_per_row,
+                            long long nsegmax, int2 *seg) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= nsegmax || !segflag[s]) return;
+    int row = (int)(s / segs_per_row), j = (int)(s % segs_per_row);
+    seg[segidx[s]] = make_int2(row * b.nx + 32 * j, row);
+}
+
+// ---------------------------------------------------------------------------------------------
+// per-link geometry (bind): eta, X_b, N_b, boundary id / BC, tangents, LSQ weights
+// ---------------------------------------------------------------------------------------------
+
+template <typename real> struct LinkGeom {
+    int *node;          // [ncut]
+    int *q;             // [ncut] outgoing direction
+    int *bc;            // [ncut]
+    double *eta;        // [ncut]
+    double *Xb;         // [3*ncut]
+    double *Nb;         // [3*ncut]
+    double *tan;        // [6*ncut] t_1, t_2
+    real *h;            // [3*ncut] Newton state (normal image)
+    int *ns;            // [ncut]
+    int *sidx;          // [kLsqCap*ncut], entry j of link l at j*ncut + l
+    real *w;            // [2*kLsqCap*ncut], tangent a, entry j at (a*kLsqCap + j)*ncut + l
+    real *rec;          // [ncut*LREC]
+    long long ncut;
+};
+
+__device__ inline int lsq_basis(int D, bool linear, const double *xi, double *ph) {
+    int nb = 0;
+    ph[nb++] = 1.0;
+    for (int a = 0; a < D; ++a) ph[nb++] = xi[a];
+    if (linear) return nb;
+    if (D == 2) {
+        ph[nb++] = 0.5 * xi[0] * xi[0];
+        ph[nb++] = xi[0] * xi[1];
+        ph[nb++] = 0.5 * xi[1] * xi[1];
+    } else {
+        ph[nb++] = 0.5 * xi[0] * xi[0];
+        ph[nb++] = 0.5 * xi[1] * xi[1];
+        ph[nb++] = 0.5 * xi[2] * xi[2];
+        ph[nb++] = xi[0] * xi[1];
+        ph[nb++] = xi[0] * xi[2];
+        ph[nb++] = xi[1] * xi[2];
+    }
+    return nb;
+}
+
+// visit the active nodes within 3 dx of X_b in (z, y, x) offset order; fn(k, xi)
+template <typename Fn>
+__device__ inline void for_stencil(const Box &b, const uint8_t *__restrict__ flags, int x, int y, int z,
+                                   const double Xb[3], Fn fn) {
+    const int R = 4;
+    const int zlo = (b.D == 3) ? -R : 0, zhi = (b.D == 3) ? R : 0;
+    for (int dz = zlo; dz <= zhi; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dxo = -R; dxo <= R; ++dxo) {
+                int cx = x + dxo, cy = y + dy, cz = z + dz;
+                if (cx < 0 || cx >= b.nx || cy < 0 || cy >= b.ny) continue;
+                if (b.D == 3 && (cz < 0 || cz >= b.nz)) continue;
+                int k = cx + b.nx * (cy + b.ny * cz);
+                if (!(flags[k] & kActive)) continue;
+                double Xk[3], xi[3], r2 = 0.0;
+                node_X(b, cx, cy, cz, Xk);
+                for (int a = 0; a < b.D; ++a) {
+                    xi[a] = (Xk[a] - Xb[a]) / b.dx;
+                    r2 += xi[a] * xi[a];
+                }
+                if (r2 > kLsqRho2 + 1e-9) continue;
+                fn(k, xi, r2);
+            }
+}
+
+template <typename real, int D>
+__global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint8_t *flags, uint8_t *dmask,
+                             const int *__restrict__ lstart, const ShapeD *__restrict__ shapes, int nshapes,
+                             const BCD *__restrict__ bcs, int nbc, LinkGeom<real> L, int *status) {
+    constexpr int K = D + D * D, LREC = K + 2;
+    int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (sgi >= nseg) return;
+    int2 sg = seg[sgi];
+    int x0 = sg.x - sg.y * b.nx, x = x0 + (threadIdx.x & 31);
+    if (x >= b.nx) return;
+    int node = sg.x + (threadIdx.x & 31);
+    uint8_t fl = flags[node];
+    if (!(fl & kActive)) return;
+    unsigned cut = fl & kCutMask;
+    if (!cut) return;
+    int y = sg.y % b.ny, z = sg.y / b.ny;
+    double Xm[3];
+    node_X(b, x, y, z, Xm);
+    int l = lstart[node];
+    uint8_t dm = 0;
+    for (int q = 0; q < 2 * D; ++q) {
+        if (!((cut >> q) & 1)) continue;
+        const int A = q >> 1;
+        const double s = (q & 1) ? -1.0 : 1.0;
+        // eta by bisection of phi on the link (Eq. cut-link-point)
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double mid = 0.5 * (lo + hi), Xt[3] = {Xm[0], Xm[1], Xm[2]};
+            Xt[A] = Xm[A] + mid * b.dx * s;
+            if (levelset(shapes, nshapes, D, Xt, nullptr) <= 0.0) lo = mid; else hi = mid;
+        }
+        const double eta = 0.5 * (lo + hi);
+        double Xb[3] = {Xm[0], Xm[1], Xm[2]};
+        Xb[A] = Xm[A] + eta * b.dx * s;
+        int which;
+        levelset(shapes, nshapes, D, Xb, &which);
+        double g[3];
+        shape_phi(shapes[which], D, Xb, g);
+        double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};  // Eq. (level-set-normal)
+        int bid = shapes[which].bid, bci = -1;
+        for (int j = 0; j < nbc; ++j)
+            if (bcs[j].bid == bid) { bci = j; break; }
+        int kind = 0;
+        if (bci < 0) {
+            set_status(status, kStNoBC);  // reported by lbm_bind_storage; treated as Dirichlet here
+            bci = 0;
+        } else {
+            kind = bcs[bci].kind;
+        }
+        if (kind == 1 && L.sidx == nullptr) {  // Neumann link but no LSQ tables (cannot happen by construction)
+            set_status(status, kStNoBC);
+            kind = 0;
+        }
+        // tangent frame
+        double t[2][3] = {{0, 0, 0}, {0, 0, 0}};
+        if (D == 2) {
+            t[0][0] = -N[1]; t[0][1] = N[0];
+        } else {
+            int a = 0;
+            for (int k = 1; k < 3; ++k)
+                if (fabs(N[k]) < fabs(N[a])) a = k;
+            double e[3] = {0, 0, 0};
+            e[a] = 1.0;
+            double c[3] = {e[1] * N[2] - e[2] * N[1], e[2] * N[0] - e[0] * N[2], e[0] * N[1] - e[1] * N[0]};
+            double nc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+            for (int k = 0; k < 3; ++k) t[0][k] = c[k] / nc;
+            t[1][0] = N[1] * t[0][2] - N[2] * t[0][1];
+            t[1][1] = N[2] * t[0][0] - N[0] * t[0][2];
+            t[1][2] = N[0] * t[0][1] - N[1] * t[0][0];
+        }
+        L.node[l] = node;
+        L.q[l] = q;
+        L.bc[l] = bci;
+        L.eta[l] = eta;
+        for (int a = 0; a < 3; ++a) {
+            L.Xb[3 * l + a] = Xb[a];
+            L.Nb[3 * l + a] = N[a];
+            L.tan[6 * l + a] = t[0][a];
+            L.tan[6 * l + 3 + a] = t[1][a];
+            L.h[3 * l + a] = (real)N[a];
+        }
+        real *rec = L.rec + (long long)l * LREC;
+        rec[0] = (real)eta;
+        rec[1] = (real)kind;
+        for (int k = 0; k < K; ++k) rec[2 + k] = 0;
+        int ns = 0;
+        if (kind == 0) {
+            dm |= (uint8_t)(1u << q);
+        } else {
+            // weighted quadratic LSQ (Eqs. quadratic-lsq-2d, tangent-derivative-2d); linear fallback
+            int mode = -1;
+            double zs[2][10];
+            for (int linear = 0; linear <= 1 && mode < 0; ++linear) {
+                double M[55];  // packed lower triangle
+                for (int r = 0; r < 55; ++r) M[r] = 0.0;
+                int nb = 0, cntn = 0;
+                for_stencil(b, flags, x, y, z, Xb, [&](int k, const double *xi, double r2) {
+                    double ph[10];
+                    nb = lsq_basis(D, linear, xi, ph);
+                    double wt = exp(-r2);
+                    for (int r = 0; r < nb; ++r)
+                        for (int c = 0; c <= r; ++c) M[r * (r + 1) / 2 + c] += wt * ph[r] * ph[c];
+                    ++cntn;
+                });
+                double ph0[10], xi0[3] = {0, 0, 0};
+                nb = lsq_basis(D, linear, xi0, ph0);
+                if (cntn < nb) continue;
+                double maxd = 0.0;
+                for (int r = 0; r < nb; ++r) maxd = fmax(maxd, M[r * (r + 1) / 2 + r]);
+                double Lc[55];
+                bool ok = true;
+                for (int c = 0; c < nb && ok; ++c) {
+                    double d = M[c * (c + 1) / 2 + c];
+                    for (int k = 0; k < c; ++k) d -= Lc[c * (c + 1) / 2 + k] * Lc[c * (c + 1) / 2 + k];
+                    if (!(d > 1e-10 * maxd)) { ok = false; break; }
+                    Lc[c * (c + 1) / 2 + c] = sqrt(d);
+                    for (int r = c + 1; r < nb; ++r) {
+                        double v = M[r * (r + 1) / 2 + c];
+                        for (int k = 0; k < c; ++k) v -= Lc[r * (r + 1) / 2 + k] * Lc[c * (c + 1) / 2 + k];
+                        Lc[r * (r + 1) / 2 + c] = v / Lc[c * (c + 1) / 2 + c];
+                    }
+                }
+                if (!ok) continue;
+                for (int al = 0; al < D - 1; ++al) {
+                    double yv[10];
+                    double *zz = zs[al];
+                    for (int r = 0; r < nb; ++r) zz[r] = 0.0;
+                    for (int a = 0; a < D; ++a) zz[1 + a] = t[al][a];
+                    for (int r = 0; r < nb; ++r) {
+                        double v = zz[r];
+                        for (int k = 0; k < r; ++k) v -= Lc[r * (r + 1) / 2 + k] * yv[k];
+                        yv[r] = v / Lc[r * (r + 1) / 2 + r];
+                    }
+                    for (int r = nb - 1; r >= 0; --r) {
+                        double v = yv[r];
+                        for (int k = r + 1; k < nb; ++k) v -= Lc[k * (k + 1) / 2 + r] * zz[k];
+                        zz[r] = v / Lc[r * (r + 1) / 2 + r];
+                    }
+                }
+                mode = linear;
+            }
+            if (mode < 0) {
+                set_status(status, kStLsq);
+            } else {
+                const bool linear = mode == 1;
+                for_stencil(b, flags, x, y, z, Xb, [&](int k, const double *xi, double r2) {
+                    if (ns < kLsqCap) {
+                        double ph[10];
+                        int nb = lsq_basis(D, linear, xi, ph);
+                        L.sidx[(long long)ns * L.ncut + l] = k;
+                        for (int al = 0; al < D - 1; ++al) {
+                            double sacc = 0.0;
+                            for (int r = 0; r < nb; ++r) sacc += ph[r] * zs[al][r];
+                            L.w[((long long)al * kLsqCap + ns) * L.ncut + l] = (real)(exp(-r2) * sacc / b.dx);
+                        }
+                        unsigned *word = reinterpret_cast<unsigned *>(flags + (k & ~3));
+                        atomicOr(word, (unsigned)kNeedU << (8 * (k & 3)));
+                    }
+                    ++ns;
+                });
+                if (ns > kLsqCap) { set_status(status, kStCapacity); ns = kLsqCap; }
+            }
+        }
+        L.ns[l] = ns;
+        ++l;
+    }
+    dmask[node] = dm;
+}
+
+// =============================================================================================
+// initial state (Eqs. init-general-d, Ut-general-init; u* from Eq. u-recovery-general)
+// =============================================================================================
+
+// C_{iAkB} Z_{kB} for the neo-Hookean law, FP64
+template <int D> __device__ inline void dpiola64(const double *F, const double *Z, double mu, double lam, double *dP) {
+    double C[D * D];
+    cofactor<double, D>(F, C);
+    const double J = det<double, D>(F);
+    double Fit[D * D];
+    for (int k = 0; k < D * D; ++k) Fit[k] = C[k] / J;
+    double tr = 0.0;
+    for (int k = 0; k < D * D; ++k) tr += Fit[k] * Z[k];
+    const double s = 0.5 * lam * (J * J - 1.0) - mu;
+    for (int i = 0; i < D; ++i)
+        for (int A = 0; A < D; ++A) {
+            double m = 0.0;
+            for (int B = 0; B < D; ++B)
+                for (int j = 0; j < D; ++j) m += Fit[i * D + B] * Z[j * D + B] * Fit[j * D + A];
+            dP[i * D + A] = mu * Z[i * D + A] + lam * J * J * tr * Fit[i * D + A] - s * m;
+        }
+}
+
+template <typename real, int D>
+__global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint8_t *__restrict__ flags,
+                       const double *__restrict__ v0, const double *__restrict__ F0, const double *__restrict__ u0,
+                       const double *__restrict__ dU0, int characteristic, double c, double dt, double mu, double lam,
+                       double gamma, double b0, double b1, double b2, real *f, real *ustar) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (sgi >= nseg) return;
+    int2 sg = seg[sgi];
+    int x = sg.x - sg.y * b.nx + (threadIdx.x & 31);
+    if (x >= b.nx) return;
+    int node = sg.x + (threadIdx.x & 31);
+    uint8_t fl = flags[node];
+    if (!(fl & kActive)) return;
+    const long long N = b.nbox, P = b.npad;
+    int y = sg.y % b.ny, z = sg.y / b.ny;
+    double U0[K];
+    for (int i = 0; i < D; ++i) U0[i] = v0[i * N + node];
+    for (int k = 0; k < D * D; ++k) U0[D + k] = F0[k * N + node];
+    double Pm[D * D];
+    piola<double, D>(U0 + D, mu, lam, Pm);
+    const double shift = (sizeof(real) == 4) ? 1.0 : 0.0;  // FP32 stores f - f^eq(0, I)
+    const double bf[3] = {b0, b1, b2};
+    double dU[D * K], Ut[K];
+    if (characteristic) {
+        const unsigned cut = fl & kCutMask;
+        for (int A = 0; A < D; ++A) {
+            const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
+            const int lp = ap ? nbr(b, node, x, y, z, 2 * A) : node, lm = am ? nbr(b, node, x, y, z, 2 * A + 1) : node;
+            for (int k = 0; k < K; ++k) {
+                if (dU0) { dU[A * K + k] = dU0[(A * K + k) * N + node]; continue; }
+                const double *src = (k < D) ? v0 + k * N : F0 + (k - D) * N;
+                double vm = src[node], vp = src[lp], vn = src[lm];
+                if (ap && am) dU[A * K + k] = (vp - vn) / (2.0 * b.dx);
+                else if (ap) dU[A * K + k] = (vp - vm) / b.dx;
+                else if (am) dU[A * K + k] = (vm - vn) / b.dx;
+                else dU[A * K + k] = 0.0;
+            }
+        }
+        // d_t U0 = B0 - Phi_A'(U0) d_A U0, with (Phi_A' Z)^{v_i} = -C_iAkB Z_F,kB, (Phi_A' Z)^{F_iB} = -d_AB Z_v_i
+        for (int k = 0; k < K; ++k) Ut[k] = 0.0;
+        for (int i = 0; i < D; ++i) Ut[i] = bf[i] - gamma * U0[i];
+        for (int A = 0; A < D; ++A) {
+            double dP[D * D];
+            dpiola64<D>(U0 + D, dU + A * K + D, mu, lam, dP);
+            for (int i = 0; i < D; ++i) Ut[i] += dP[i * D + A];
+            for (int i = 0; i < D; ++i) Ut[D + i * D + A] += dU[A * K + i];
+        }
+    }
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const double s = (q & 1) ? -1.0 : 1.0;
+        double fq[K];
+        for (int i = 0; i < D; ++i) fq[i] = (U0[i] - s * (D / c) * Pm[i * D + A]) / (2.0 * D);
+        for (int i = 0; i < D; ++i)
+            for (int B = 0; B < D; ++B)
+                fq[D + i * D + B] = (A == B) ? ((U0[D + i * D + B] - (i == B ? shift : 0.0)) - s * (D / c) * U0[i]) / (2.0 * D)
+                                             : (U0[D + i * D + B] - (i == B ? shift : 0.0)) / (2.0 * D);
+        if (characteristic) {
+            double Zq[K];
+            for (int k = 0; k < K; ++k) Zq[k] = Ut[k] + c * s * dU[A * K + k];
+            double dP[D * D];
+            dpiola64<D>(U0 + D, Zq + D, mu, lam, dP);
+            for (int i = 0; i < D; ++i) fq[i] -= 0.5 * dt * (Zq[i] - s * (D / c) * dP[i * D + A]) / (2.0 * D);
+            for (int i = 0; i < D; ++i)
+                for (int B = 0; B < D; ++B)
+                    fq[D + i * D + B] -= 0.5 * dt * (Zq[D + i * D + B] - s * (D / c) * (A == B ? Zq[i] : 0.0)) / (2.0 * D);
+        }
+        for (int k = 0; k < K; ++k) f[(long long)(q * K + k) * P + node] = (real)fq[k];
+    }
+    for (int i = 0; i < D; ++i) ustar[i * P + node] = (real)(u0[i * N + node] - 0.5 * dt * v0[i * N + node]);
+}
+
+// =============================================================================================
+// gather: pull streaming + cut-link reconstruction
+// =============================================================================================
+
+template <typename real> struct StepArgs {
+    Box b;
+    const int2 *seg;
+    int nseg;
+    const uint8_t *flags;
+    const int *lstart;
+    const real *fsrc;
+    real *fdst;
+    real *ustar;
+    real *un;
+    const real *lrec;
+    real *vst, *Gst;   // projection steps: v^n and G^n = F^n - I (D and D*D planes)
+    double *u0;        // projection steps: u^n in FP64
+    real dt, c, omega, gamma, mu, lam, bf[3];
+    int *status;
+};
+
+// MODE 0: state is pre-collision f^0 (first step, no streaming); MODE 1: state is f*^{n-1}
+template <typename real, int D, int MODE>
+__device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x, int y, int z, unsigned cut,
+                                       real (&f)[2 * D * (D + D * D)]) {
+    constexpr int K = D + D * D, Q = 2 * D, LREC = K + 2;
+    const long long P = a.b.npad;
+    const real *__restrict__ fs = a.fsrc;
+    if constexpr (MODE == 0) {
+        #pragma unroll
+        for (int q = 0; q < Q; ++q)
+            #pragma unroll
+            for (int k = 0; k < K; ++k) f[q * K + k] = __ldg(fs + (long long)(q * K + k) * P + node);
+        return;
+    } else {
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (!((cut >> (q ^ 1)) & 1)) {  // source m - e_q = m + e_{q^1} is active
+            const int src = nbr(a.b, node, x, y, z, q ^ 1);
+            #pragma unroll
+            for (int k = 0; k < K; ++k) f[q * K + k] = __ldg(fs + (long long)(q * K + k) * P + src);
+        }
+    }
+    if (cut) {
+        const real *rec0 = a.lrec + (long long)__ldg(a.lstart + node) * LREC;
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int qo = q ^ 1;  // outgoing direction of the cut link; q is the missing incoming one
+            if ((cut >> qo) & 1) {
+                const real *rec = rec0 + __popc(cut & ((1u << qo) - 1u)) * LREC;
+                const real eta = rec[0];
+                const bool neu = rec[1] != real(0);
+                const bool up = !((cut >> q) & 1);  // m^- = m - e_{qo} = m + e_q active
+                #pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const real Dk = ((k < D) == neu) ? real(1) : real(-1);  // D_N = diag(I,-I), D_D = diag(-I,I)
+                    const real S = rec[2 + k];
+                    const real fo = __ldg(fs + (long long)(qo * K + k) * P + node);  // f*_{-d}(X_f)
+                    const real fi = __ldg(fs + (long long)(q * K + k) * P + node);   // f*_{d}(X_f)
+                    real r;
+                    if (eta >= real(0.5)) {
+                        r = (Dk * fo + S) / (real(2) * eta) + (real(1) - real(1) / (real(2) * eta)) * fi;
+                    } else {
+                        const real fu = up ? f[qo * K + k] : fo;  // f*_{-d}(X_f - dx e)
+                        r = Dk * (real(2) * eta * fo + (real(1) - real(2) * eta) * fu) + S;
+                    }
+                    f[q * K + k] = r;
+                }
+            }
+        }
+    }
+    }
+}
+
+// moments with half-step source and implicit damping (Eq. state-recovery-general, B = (b - gamma v, 0))
+template <typename real, int D>
+__device__ __forceinline__ void recover(const StepArgs<real> &a, const real (&f)[2 * D * (D + D * D)], real v[D],
+                                        real G[D * D], real F[D * D]) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        real s = f[k];
+        #pragma unroll
+        for (int q = 1; q < Q; ++q) s += f[q * K + k];
+        if (k < D) {
+            v[k] = (s + real(0.5) * a.dt * a.bf[k]) / (real(1) + real(0.5) * a.dt * a.gamma);
+        } else {
+            const real one = (((k - D) / D) == ((k - D) % D)) ? real(1) : real(0);
+            if constexpr (kShifted<real>) { G[k - D] = s; F[k - D] = s + one; }
+            else { F[k - D] = s; G[k - D] = s - one; }
+        }
+    }
+}
+
+// BGK collision with source (Eq. collision-general-d) in shifted variables; writes f*
+// equilibrium f^eq_q (Eq. feq-general-d) in the storage variables: v rows (v - s (D/c) P_iA)/(2D),
+// F rows (X_iB - s (D/c) delta_AB v_i)/(2D), X = F - I (shifted storage) or F (raw storage)
+template <typename real, int D>
+__device__ __forceinline__ void equilibrium(const real v[D], const real X[D * D], const real Pk[D * D], real Dc,
+                                            real (&feq)[2 * D * (D + D * D)]) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const real s = (q & 1) ? real(-1) : real(1);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) feq[q * K + i] = div2D<real, D>(v[i] - s * Dc * Pk[i * D + A]);
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            #pragma unroll
+            for (int Bc = 0; Bc < D; ++Bc)
+                feq[q * K + D + i * D + Bc] =
+                    (A == Bc) ? div2D<real, D>(X[i * D + Bc] - s * Dc * v[i]) : div2D<real, D>(X[i * D + Bc]);
+    }
+}
+
+template <typename real, int D>
+__device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node, real (&f)[2 * D * (D + D * D)],
+                                              const real v[D], const real G[D * D], const real F[D * D],
+                                              const real Pk[D * D]) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    const long long P = a.b.npad;
+    const real Dc = real(D) / a.c;
+    const real wq = real(1) / real(4 * D);
+    const real src = a.dt * (real(2) - a.omega) * wq;
+    real B[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const real s = (q & 1) ? real(-1) : real(1);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const real feq = div2D<real, D>(v[i] - s * Dc * Pk[i * D + A]);
+            const real fv = f[q * K + i];
+            a.fdst[(long long)(q * K + i) * P + node] = fv + a.omega * (feq - fv) + src * B[i];
+        }
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            #pragma unroll
+            for (int Bc = 0; Bc < D; ++Bc) {
+                const int k = D + i * D + Bc;
+                const real X = kShifted<real> ? G[i * D + Bc] : F[i * D + Bc];
+                const real feq = (A == Bc) ? div2D<real, D>(X - s * Dc * v[i]) : div2D<real, D>(X);
+                const real fv = f[q * K + k];
+                a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv);
+            }
+    }
+}
+
+template <typename real, int D>
+__device__ __forceinline__ int check_state(const real v[D], const real F[D * D], real J) {
+    int st = 0;
+    if (!(J > real(0))) st |= kStJacobian;
+    bool fin = isfinite(J);
+    #pragma unroll
+    for (int i = 0; i < D; ++i) fin = fin && isfinite(v[i]);
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) fin = fin && isfinite(F[k]);
+    if (!fin) st |= kStNonfinite;
+    return st;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K3: fused gather + closure + recovery + collision (+ u quadrature), one thread per node
+// ---------------------------------------------------------------------------------------------
+template <typename real, int D, int MODE>
+__global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (sgi >= a.nseg) return;
+    const int2 sg = __ldg(&a.seg[sgi]);
+    const int lane = threadIdx.x & 31;
+    const int x = sg.x - sg.y * a.b.nx + lane;
+    if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
+    const uint8_t fl = __ldg(a.flags + node);
+    if (!(fl & kActive)) return;
+    const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
+    const unsigned cut = fl & kCutMask;
+    real f[Q * K];
+    gather<real, D, MODE>(a, node, x, y, z, cut, f);
+    real v[D], G[D * D], F[D * D], Pk[D * D];
+    recover<real, D>(a, f, v, G, F);
+    const real J = piola<real, D>(F, a.mu, a.lam, Pk);
+    const int st = check_state<real, D>(v, F, J);
+    if (st) set_status(a.status, st);
+    const long long P = a.b.npad;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const real un = a.ustar[i * P + node] + real(0.5) * a.dt * v[i];  // u^n (Eq. u-recovery-general)
+        if (fl & kNeedU) a.un[i * P + node] = un;
+        a.ustar[i * P + node] = un + real(0.5) * a.dt * v[i];              // u*^{n+1}
+    }
+    collide_store<real, D>(a, node, f, v, G, F, Pk);
+}
+
+// projection steps, part 1: gather + recovery; stores f^n (pre-collision), v^n, G^n, u^n (FP64)
+template <typename real, int D, int MODE>
+__global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (sgi >= a.nseg) return;
+    const int2 sg = __ldg(&a.seg[sgi]);
+    const int lane = threadIdx.x & 31;
+    const int x = sg.x - sg.y * a.b.nx + lane;
+    if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
+    const uint8_t fl = __ldg(a.flags + node);
+    if (!(fl & kActive)) return;
+    const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
+    real f[Q * K];
+    gather<real, D, MODE>(a, node, x, y, z, fl & kCutMask, f);
+    real v[D], G[D * D], F[D * D];
+    recover<real, D>(a, f, v, G, F);
+    const long long P = a.b.npad;
+    #pragma unroll
+    for (int j = 0; j < Q * K; ++j) a.fdst[(long long)j * P + node] = f[j];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        a.vst[i * P + node] = v[i];
+        a.u0[i * P + node] = (double)a.ustar[i * P + node] + 0.5 * (double)a.dt * (double)v[i];
+    }
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = G[k];
+}
+
+// field output: v, F, u at the current time (FP64, box planes)
+template <typename real, int D, int MODE>
+__global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *vout, double *Fout, double *uout) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (sgi >= a.nseg) return;
+    const int2 sg = __ldg(&a.seg[sgi]);
+    const int lane = threadIdx.x & 31;
+    const int x = sg.x - sg.y * a.b.nx + lane;
+    if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
+    const uint8_t fl = __ldg(a.flags + node);
+    if (!(fl & kActive)) return;
+    const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
+    real f[Q * K];
+    gather<real, D, MODE>(a, node, x, y, z, fl & kCutMask, f);
+    real v[D], G[D * D], F[D * D];
+    recover<real, D>(a, f, v, G, F);
+    const long long N = a.b.nbox, P = a.b.npad;
+    for (int i = 0; i < D; ++i) {
+        if (vout) vout[i * N + node] = (double)v[i];
+        if (uout) uout[i * N + node] = (double)a.ustar[i * P + node] + 0.5 * (double)a.dt * (double)v[i];
+    }
+    if (Fout)
+        for (int i = 0; i < D; ++i)
+            for (int B = 0; B < D; ++B)
+                Fout[(i * D + B) * N + node] =
+                    kShifted<real> ? (double)G[i * D + B] + (i == B ? 1.0 : 0.0) : (double)F[i * D + B];
+}
+
+// =============================================================================================
+// K4: boundary sources S~_b per cut link (Secs. 3.3-3.4)
+// =============================================================================================
+
+template <typename real> struct CutArgs {
+    LinkGeom<real> L;
+    const BCD *bcs;
+    const real *un;
+    long long npad;
+    double t, dt, c, mu, lam;
+    int D;
+    int *status;
+};
+
+template <typename real, int D>
+__device__ __forceinline__ bool traction_residual(const real h[D], const real N[D], const real g[D - 1][D],
+                                                  const real t[D - 1][D], const real T[D], real mu, real lam, real R[D]) {
+    real F[D * D], P[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int A = 0; A < D; ++A) {
+            real v = h[i] * N[A];
+            #pragma unroll
+            for (int al = 0; al < D - 1; ++al) v += g[al][i] * t[al][A];
+            F[i * D + A] = v;
+        }
+    const real J = det<real, D>(F);
+    if (!(J > real(0))) return false;
+    piola<real, D>(F, mu, lam, P);
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        real s = 0;
+        #pragma unroll
+        for (int A = 0; A < D; ++A) s += P[i * D + A] * N[A];
+        R[i] = s - T[i];
+    }
+    return true;
+}
+
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
+    constexpr int K = D + D * D, LREC = K + 2;
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= a.L.ncut) return;
+    const int q = a.L.q[l], A = q >> 1;
+    const real s = (q & 1) ? real(-1) : real(1);  // e = s e_A, d = -e
+    const BCD &bc = a.bcs[a.L.bc[l]];
+    const double Xb[3] = {a.L.Xb[3 * l], a.L.Xb[3 * l + 1], a.L.Xb[3 * l + 2]};
+    const double th = a.t + 0.5 * a.dt;  // boundary data at t^n + dt/2
+    const real c = (real)a.c;
+    real S[K];
+    if (bc.kind == 0) {
+        // velocity Dirichlet rows (Eqs. dirichlet-rows-curved, dirichlet-compact-curved)
+        double vb[3];
+        dirichlet_eval(bc, D, Xb, th, false, vb);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            S[i] = (real)vb[i] / real(D);
+            #pragma unroll
+            for (int B = 0; B < D; ++B) S[D + i * D + B] = (B == A) ? s * (real)vb[i] / c : real(0);
+        }
+    } else {
+        // nominal-traction Neumann rows (Eqs. neumann-rows-curved, neumann-compact-curved)
+        const real mu = (real)a.mu, lam = (real)a.lam;
+        real N[D], t[D - 1][D], g[D - 1][D];
+        #pragma unroll
+        for (int i = 0; i < D; ++i) N[i] = (real)a.L.Nb[3 * l + i];
+        #pragma unroll
+        for (int al = 0; al < D - 1; ++al)
+            #pragma unroll
+            for (int i = 0; i < D; ++i) { t[al][i] = (real)a.L.tan[6 * l + 3 * al + i]; g[al][i] = real(0); }
+        // tangent images g_a = t_a + sum_j w_aj (u_j - u_m)  (Eqs. tangent-derivative-2d, tangent-image-3d-lsq)
+        const int m = a.L.node[l];
+        const long long P = a.npad;
+        real um[D];
+        #pragma unroll
+        for (int i = 0; i < D; ++i) um[i] = a.un[i * P + m];
+        const int ns = a.L.ns[l];
+        if constexpr (!kShifted<real>) {
+            // FP64: g = t + sum_j w_j u_j in stencil order, as the oracle sums it
+            #pragma unroll
+            for (int al = 0; al < D - 1; ++al)
+                #pragma unroll
+                for (int i = 0; i < D; ++i) g[al][i] = t[al][i];
+        }
+        for (int j = 0; j < ns; ++j) {
+            const int k = a.L.sidx[(long long)j * a.L.ncut + l];
+            real w[D - 1];
+            #pragma unroll
+            for (int al = 0; al < D - 1; ++al) w[al] = a.L.w[((long long)al * kLsqCap + j) * a.L.ncut + l];
+            #pragma unroll
+            for (int i = 0; i < D; ++i) {
+                // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation
+                const real du = kShifted<real> ? a.un[i * P + k] - um[i] : a.un[i * P + k];
+                #pragma unroll
+                for (int al = 0; al < D - 1; ++al) g[al][i] += w[al] * du;
+            }
+        }
+        if constexpr (kShifted<real>) {
+            #pragma unroll
+            for (int al = 0; al < D - 1; ++al)
+                #pragma unroll
+                for (int i = 0; i < D; ++i) g[al][i] += t[al][i];
+        }
+        double Td[3];
+        traction_eval(bc, D, Xb, th, Td);
+        real T[D];
+        real tinf = 0;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) { T[i] = (real)Td[i]; tinf = fmax(tinf, fabs(T[i])); }
+        // Newton for the normal image h (Eqs. Fb-decomp-2d/3d, neumann-newton-2d/3d), central FD Jacobian,
+        // halving line search that rejects det F_b <= 0
+        constexpr bool dbl = sizeof(real) == 8;
+        const real tol = (dbl ? real(1e-13) : real(2e-6)) * (mu + lam + tinf);
+        const real fd = dbl ? real(1e-6) : real(1e-3);
+        real h[D], R[D];
+        #pragma unroll
+        for (int i = 0; i < D; ++i) h[i] = a.L.h[3 * l + i];
+        bool ok = traction_residual<real, D>(h, N, g, t, T, mu, lam, R);
+        if (!ok) {
+            #pragma unroll
+            for (int i = 0; i < D; ++i) h[i] = N[i];
+            ok = traction_residual<real, D>(h, N, g, t, T, mu, lam, R);
+        }
+        bool conv = false;
+        for (int it = 0; ok && it < 30; ++it) {
+            real rinf = 0, r2 = 0;
+            #pragma unroll
+            for (int i = 0; i < D; ++i) { rinf = fmax(rinf, fabs(R[i])); r2 += R[i] * R[i]; }
+            if (rinf <= tol) { conv = true; break; }
+            real hinf = 0;
+            #pragma unroll
+            for (int i = 0; i < D; ++i) hinf = fmax(hinf, fabs(h[i]));
+            const real del = fd * fmax(real(1), hinf);
+            real Jm[D * D];
+            #pragma unroll
+            for (int j = 0; j < D; ++j) {
+                real hp[D], hm[D], Rp[D], Rm[D];
+                #pragma unroll
+                for (int i = 0; i < D; ++i) { hp[i] = h[i]; hm[i] = h[i]; }
+                hp[j] += del;
+                hm[j] -= del;
+                ok = traction_residual<real, D>(hp, N, g, t, T, mu, lam, Rp) &&
+                     traction_residual<real, D>(hm, N, g, t, T, mu, lam, Rm);
+                if (!ok) break;
+                #pragma unroll
+                for (int i = 0; i < D; ++i) Jm[i * D + j] = (Rp[i] - Rm[i]) / (real(2) * del);
+            }
+            if (!ok) break;
+            real mR[D], dh[D];
+            #pragma unroll
+            for (int i = 0; i < D; ++i) mR[i] = -R[i];
+            if (!solve_small<real, D>(Jm, mR, dh)) { ok = false; break; }
+            real al = 1;
+            bool acc = false;
+            real ht[D], Rt[D];
+            for (int ls = 0; ls < 20; ++ls) {
+                #pragma unroll
+                for (int i = 0; i < D; ++i) ht[i] = h[i] + al * dh[i];
+                if (traction_residual<real, D>(ht, N, g, t, T, mu, lam, Rt)) {
+                    real rt2 = 0;
+                    #pragma unroll
+                    for (int i = 0; i < D; ++i) rt2 += Rt[i] * Rt[i];
+                    if (rt2 < r2) { acc = true; break; }
+                }
+                al *= real(0.5);
+            }
+            if (!acc) { conv = rinf <= (dbl ? real(1e3) : real(10)) * tol; break; }
+            #pragma unroll
+            for (int i = 0; i < D; ++i) { h[i] = ht[i]; R[i] = Rt[i]; }
+        }
+        if (!(ok && conv)) {
+            set_status(a.status, kStNewton);
+            #pragma unroll
+            for (int i = 0; i < D; ++i) h[i] = a.L.h[3 * l + i];
+        } else {
+            #pragma unroll
+            for (int i = 0; i < D; ++i) a.L.h[3 * l + i] = h[i];
+        }
+        real Fb[D * D], Pb[D * D];
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            #pragma unroll
+            for (int B = 0; B < D; ++B) {
+                real v = h[i] * N[B];
+                #pragma unroll
+                for (int al = 0; al < D - 1; ++al) v += g[al][i] * t[al][B];
+                Fb[i * D + B] = v;
+            }
+        piola<real, D>(Fb, mu, lam, Pb);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            S[i] = s * Pb[i * D + A] / c;  // -d_A P_iA / c with d = -s e_A
+            #pragma unroll
+            for (int B = 0; B < D; ++B)
+                S[D + i * D + B] = kShifted<real> ? (Fb[i * D + B] - ((i == B) ? real(1) : real(0))) / real(D)
+                                                  : Fb[i * D + B] / real(D);
+        }
+    }
+    real *rec = a.L.rec + l * LREC;
+    #pragma unroll
+    for (int k = 0; k < K; ++k) rec[2 + k] = S[k];
+}
+
+// =============================================================================================
+// compatibility projection (Sec. 3.5), FP64 accumulation
+// =============================================================================================
+
+template <typename real> struct ProjArgs {
+    Box b;
+    const int2 *seg;
+    int nseg;
+    const uint8_t *flags;
+    const uint8_t *dmask;
+    const int *lstart;
+    LinkGeom<real> L;
+    const BCD *bcs;
+    const real *Gst;
+    const double *u0;  // warm start (FP64, D planes)
+    real *resid;       // residual of the normal equations at the warm start (D planes)
+    double t, beta;
+};
+
+// node weight of the normal equations: active axis neighbours plus Dirichlet boundary edges
+__device__ __forceinline__ int proj_degree(int D, unsigned cut, uint8_t dm) {
+    return (2 * D - __popc(cut & ((1u << (2 * D)) - 1u))) + __popc((unsigned)dm);
+}
+
+#define TLV_NODE_PROLOGUE(a)                                      \
+    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);          \
+    if (sgi >= (a).nseg) return;                                  \
+    const int2 sg = __ldg(&(a).seg[sgi]);                         \
+    const int lane = threadIdx.x & 31;                            \
+    const int x = sg.x - sg.y * (a).b.nx + lane;                  \
+    if (x >= (a).b.nx) return;                                    \
+    const int node = sg.x + lane;                                 \
+    const uint8_t fl = __ldg((a).flags + node);                   \
+    if (!(fl & kActive)) return;                                  \
+    const int y = sg.y % (a).b.ny, z = sg.y / (a).b.ny;           \
+    (void)y;                                                      \
+    (void)z;
+
+// Residual of the normal equations of Eq. (projection-edge-relation) at the warm start u0,
+//   r_m = b_m + sum_l u0_l - deg_m u0_m,   b_m = sum_l g_ml + sum_b (u_D(X_b, t^n) + G_m (X_m - X_b)),
+// accumulated in FP64 (interior edges plus boundary edges to the prescribed displacement).
+// Damped Jacobi on u from u0 equals damped Jacobi on the correction d = u - u0 from 0 with this
+// right-hand side, so the sweeps can run on d in the population precision.
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
+    TLV_NODE_PROLOGUE(a)
+    const long long P = a.b.npad;
+    const unsigned cut = fl & kCutMask;
+    const uint8_t dm = a.dmask[node];
+    double r[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) r[i] = 0.0;
+    if (dm) {
+        int l = a.lstart[node];
+        for (int q = 0; q < 2 * D; ++q) {
+            if (!((cut >> q) & 1)) continue;
+            if ((dm >> q) & 1) {
+                const int A = q >> 1;
+                const double s = (q & 1) ? -1.0 : 1.0;
+                const double Xb[3] = {a.L.Xb[3 * l], a.L.Xb[3 * l + 1], a.L.Xb[3 * l + 2]};
+                double uD[3];
+                dirichlet_eval(a.bcs[a.L.bc[l]], D, Xb, a.t, true, uD);
+                for (int i = 0; i < D; ++i)
+                    r[i] += uD[i] + (double)a.Gst[(i * D + A) * P + node] * (-s * a.L.eta[l] * a.b.dx) -
+                            a.u0[i * P + node];
+            }
+            ++l;
+        }
+    }
+    #pragma unroll
+    for (int q = 0; q < 2 * D; ++q) {
+        if ((cut >> q) & 1) continue;
+        const int A = q >> 1;
+        const double s = (q & 1) ? -1.0 : 1.0;
+        const int ln = nbr(a.b, node, x, y, z, q);
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            r[i] += a.u0[i * P + ln] - a.u0[i * P + node] +
+                    0.5 * ((double)a.Gst[(i * D + A) * P + node] + (double)a.Gst[(i * D + A) * P + ln]) * (-s * a.b.dx);
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i];
+}
+
+// one damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr)
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
+    TLV_NODE_PROLOGUE(a)
+    const long long P = a.b.npad;
+    const unsigned cut = fl & kCutMask;
+    const int deg = proj_degree(D, cut, __ldg(a.dmask + node));
+    const real beta = (real)a.beta;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        real acc = a.resid[i * P + node];
+        real d = 0;
+        if (din) {
+            d = din[i * P + node];
+            #pragma unroll
+            for (int q = 0; q < 2 * D; ++q)
+                if (!((cut >> q) & 1)) acc += __ldg(din + i * P + nbr(a.b, node, x, y, z, q));
+        }
+        dout[i * P + node] = deg > 0 ? (real(1) - beta) * d + beta * acc / (real)deg : d;
+    }
+}
+
+// block partial sums of the correction (u^c - u^0) per component: warp shuffles, then shared memory
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_reduce_partial(const ProjArgs<real> a, const real *__restrict__ dc,
+                                                        double *partial) {
+    __shared__ double sm[4][D];
+    double d[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) d[i] = 0.0;
+    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (sgi < a.nseg) {
+        const int2 sg = __ldg(&a.seg[sgi]);
+        const int x = sg.x - sg.y * a.b.nx + lane;
+        const int node = sg.x + lane;
+        if (x < a.b.nx && (__ldg(a.flags + node) & kActive)) {
+            #pragma unroll
+            for (int i = 0; i < D; ++i) d[i] = (double)dc[i * a.b.npad + node];
+        }
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d[i] += __shfl_down_sync(0xffffffffu, d[i], o);
+    if (lane == 0)
+        #pragma unroll
+        for (int i = 0; i < D; ++i) sm[threadIdx.x >> 5][i] = d[i];
+    __syncthreads();
+    if (threadIdx.x < D) partial[blockIdx.x * D + threadIdx.x] = sm[0][threadIdx.x] + sm[1][threadIdx.x] + sm[2][threadIdx.x] + sm[3][threadIdx.x];
+}
+
+// deterministic final reduction (one block of 256): mean[i] = sum / n_active
+template <int D>
+__global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__ partial, int nblocks, double inv_n, double *mean) {
+    __shared__ double sm[8][D];
+    double s[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) s[i] = 0.0;
+    for (int j = threadIdx.x; j < nblocks; j += 256)
+        #pragma unroll
+        for (int i = 0; i < D; ++i) s[i] += partial[j * D + i];
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_down_sync(0xffffffffu, s[i], o);
+    if ((threadIdx.x & 31) == 0)
+        #pragma unroll
+        for (int i = 0; i < D; ++i) sm[threadIdx.x >> 5][i] = s[i];
+    __syncthreads();
+    if (threadIdx.x < D) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w][threadIdx.x];
+        mean[threadIdx.x] = t * inv_n;
+    }
+}
+
+// after the first solve: u^n = u0 + d - mean (written to u1), F^c (Eq. projection-compatible-F), F^r
+// (Eq. projection-F-repair-weight), population repair (Eq. projection-population-repair),
+// collision and u*^{n+1}.  f^n is read from and f*^n written to fdst (in place).
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, const double *__restrict__ u0,
+                                                        const real *__restrict__ dc, const double *__restrict__ mean,
+                                                        double theta, double *u1) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    TLV_NODE_PROLOGUE(a)
+    const long long P = a.b.npad;
+    const unsigned cut = fl & kCutMask;
+    real v[D], G[D * D], F[D * D], Pold[D * D], Fr[D * D], Gr[D * D], Pk[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = a.vst[i * P + node];
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) G[k] = a.Gst[k * P + node];
+    #pragma unroll
+    for (int A = 0; A < D; ++A) {
+        const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
+        const int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
+        const int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double gc;
+            bool keep = false;
+            const double up = u0[i * P + lp] + (double)dc[i * P + lp];
+            const double um = u0[i * P + lm] + (double)dc[i * P + lm];
+            const double uo = u0[i * P + node] + (double)dc[i * P + node];
+            if (ap && am) gc = (up - um) / (2.0 * a.b.dx);
+            else if (ap) gc = (up - uo) / a.b.dx;
+            else if (am) gc = (uo - um) / a.b.dx;
+            else { gc = 0.0; keep = true; }
+            const real Gc = keep ? G[i * D + A] : (real)gc;
+            Gr[i * D + A] = (real)((1.0 - theta) * (double)G[i * D + A] + theta * (double)Gc);
+        }
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int B = 0; B < D; ++B) {
+            const real one = (i == B) ? real(1) : real(0);
+            F[i * D + B] = G[i * D + B] + one;
+            Fr[i * D + B] = Gr[i * D + B] + one;
+        }
+    piola<real, D>(F, a.mu, a.lam, Pold);
+    const real J = piola<real, D>(Fr, a.mu, a.lam, Pk);
+    const int st = check_state<real, D>(v, Fr, J);
+    if (st) set_status(a.status, st);
+    real f[Q * K];
+    const real Dc = real(D) / a.c;
+    if constexpr (kShifted<real>) {
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int A = q >> 1;
+            const real s = (q & 1) ? real(-1) : real(1);
+            #pragma unroll
+            for (int i = 0; i < D; ++i)  // f += f^eq(v, F^r) - f^eq(v, F): v rows carry -(s/2c)(P^r - P)_{iA}
+                f[q * K + i] = a.fdst[(long long)(q * K + i) * P + node] -
+                               div2D<real, D>(s * Dc * (Pk[i * D + A] - Pold[i * D + A]));
+            #pragma unroll
+            for (int k = 0; k < D * D; ++k)
+                f[q * K + D + k] = a.fdst[(long long)(q * K + D + k) * P + node] + div2D<real, D>(Gr[k] - G[k]);
+        }
+    } else {
+        real fr[Q * K], fo[Q * K];
+        equilibrium<real, D>(v, Fr, Pk, Dc, fr);
+        equilibrium<real, D>(v, F, Pold, Dc, fo);
+        #pragma unroll
+        for (int j = 0; j < Q * K; ++j) f[j] = a.fdst[(long long)j * P + node] + (fr[j] - fo[j]);
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const double un = u0[i * P + node] + (double)dc[i * P + node] - mean[i];
+        u1[i * P + node] = un;
+        a.ustar[i * P + node] = (real)(un + 0.5 * (double)a.dt * (double)v[i]);
+    }
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = Gr[k];
+    collide_store<real, D>(a, node, f, v, Gr, Fr, Pk);
+}
+
+// after the second solve: u^n = u0 + d - mean and u*^{n+1} = u^n + dt/2 v^n
+template <typename real, int D>
+__global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, const double *__restrict__ u0,
+                                                    const real *__restrict__ dc, const double *__restrict__ mean) {
+    TLV_NODE_PROLOGUE(a)
+    const long long P = a.b.npad;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const double un = u0[i * P + node] + (double)dc[i * P + node] - mean[i];
+        a.un[i * P + node] = (real)un;
+        a.ustar[i * P + node] = (real)(un + 0.5 * (double)a.dt * (double)a.vst[i * P + node]);
+    }
+}
+
+}  // namespace tlv

@@ -1,0 +1,14 @@
+// Entry points of one precision: defined in lbm_fp64.cu (built with -fmad=false so its
+// arithmetic matches the FP64 oracle operation for operation) and lbm_fp32.cu.
+#pragma once
+#include "lbm_impl.cuh"
+
+struct PrecOps {
+    int (*link_build)(lbm_handle *);
+    int (*init)(lbm_handle *, int, const double *, const double *, const double *, const double *);
+    int (*step)(lbm_handle *, int);
+    int (*fields)(lbm_handle *, double *, double *, double *);
+};
+
+const PrecOps &ops_fp64();
+const PrecOps &ops_fp32();

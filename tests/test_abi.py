@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point include/lbm.h declares, and its
+host-side validation answers without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2606_20646_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    from paper_2606_20646_b300 import lbm
+    return lbm.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2606_20646_b300 import lbm
+    assert set(names) == set(lbm.SIGNATURES)
+
+
+def test_error_strings(lib):
+    for code in range(0, -8, -1):
+        assert lib.lbm_error_string(code)
+    assert lib.lbm_error_string(-3).decode() == "CUDA runtime error"
+
+
+def test_geometry_bytes_and_validation_without_gpu(lib):
+    from paper_2606_20646_b300 import inputs as I, lbm
+    p = I.shell_3d(64)
+    g, shapes, ls, mat, bcs, opt = lbm.descriptors(p)
+    n = C.c_size_t(0)
+    assert lib.lbm_geometry_bytes(C.byref(g), C.byref(n)) == 0
+    assert n.value >= p.n_box * 9
+    bad = lbm.lbm_grid.from_buffer_copy(g)
+    bad.dim = 4
+    assert lib.lbm_geometry_bytes(C.byref(bad), C.byref(n)) == -1
+    h = C.c_void_p()
+    # descriptor errors are reported before any device work
+    opt.omega = 2.5
+    assert lib.lbm_create(C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None,
+                          C.byref(h)) == -1
+    opt.omega = 1.8
+    # missing geometry storage
+    assert lib.lbm_create(C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None,
+                          C.byref(h)) == -4
+    # an unknown boundary profile for a Neumann condition
+    bcs[0].profile = 1
+    assert lib.lbm_create(C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None,
+                          C.byref(h)) == -1
