@@ -644,6 +644,7 @@ int orc_newton(int D, double mu, double lam, const double *N, const double *g, c
             rinf = fabs(R[i]) > rinf ? fabs(R[i]) : rinf;
             r2 += R[i] * R[i];
         }
+        if (!isfinite(r2)) return -1; /* a non-finite residual is a failed inversion */
         if (rinf <= tol) return it;
         double hinf = 0.0;
         for (int i = 0; i < D; i++) hinf = fabs(h[i]) > hinf ? fabs(h[i]) : hinf;

@@ -893,6 +893,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
             real rinf = 0, r2 = 0;
             #pragma unroll
             for (int i = 0; i < D; ++i) { rinf = fmax(rinf, fabs(R[i])); r2 += R[i] * R[i]; }
+            if (!isfinite(r2)) { ok = false; break; }  // fmax drops NaN; r2 does not
             if (rinf <= tol) { conv = true; break; }
             real hinf = 0;
             #pragma unroll

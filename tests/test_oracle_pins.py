@@ -450,3 +450,11 @@ def test_spherical_shell_converges_to_bvp_3d():
     ue = rb.displacement_field(r, p.coords(), (0.5, 0.5, 0.5))
     Eu = np.sqrt((((u - ue) ** 2) * act).sum() / ((ue ** 2) * act).sum())
     assert Eu < 3e-2
+
+
+def test_newton_reports_nonfinite_traction():
+    """A non-finite prescribed traction is a failed inversion, not a converged one."""
+    N = np.array([1.0, 0.0])
+    h, it = oracle.newton(2, 1.0, 1.0, N, [np.array([0.0, 1.0])], [np.array([0.0, 1.0])],
+                          np.array([np.nan, 0.0]), N.copy())
+    assert it == -1
