@@ -60,7 +60,8 @@ enum lbm_device_status {
     LBM_DEV_JACOBIAN = 2,  /* J = det F <= 0 at an active node (Eq. positive-jacobian) */
     LBM_DEV_NEWTON = 4,    /* traction inversion failed (Eqs. neumann-newton-2d/3d)   */
     LBM_DEV_LSQ = 8,       /* no least-squares fit at a Neumann link                   */
-    LBM_DEV_CAPACITY = 16  /* LSQ stencil larger than LBM_LSQ_CAPACITY                */
+    LBM_DEV_CAPACITY = 16, /* LSQ stencil larger than LBM_LSQ_CAPACITY                */
+    LBM_DEV_TIMEOUT = 128  /* a bounded wait for a TMA copy ran out; that step is invalid */
 };
 
 enum lbm_precision { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1 };

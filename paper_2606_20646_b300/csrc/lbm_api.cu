@@ -359,8 +359,8 @@ int lbm_sync(lbm_handle *h, int *device_status) {
     int stv = 0;
     CK(cudaMemcpyAsync(&stv, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (device_status) *device_status = stv & 31;
-    if (stv & 31) {
+    if (device_status) *device_status = stv & (31 | kStTimeout);
+    if (stv & (31 | kStTimeout)) {
         CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
         CK(cudaStreamSynchronize(h->stream));
         return LBM_ERR_DEVICE;

@@ -11,12 +11,17 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+#include <cstdlib>
+
 #include "lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 using namespace tlv;
 
 constexpr size_t kAlign = 256;
+constexpr unsigned kReduceBlocks = 4 * 148;  // fixed grid of the gauge reduction (4 blocks per SM)
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -77,6 +82,10 @@ struct lbm_handle {
     int phase = 0;  // 0: fA holds pre-collision f^0; 1: fA holds post-collision f*^{n-1}
     long long step = 0;
     long long launches = 0;
+    // TMA staging of the FP32 gather: tensor maps of both population buffers
+    bool tma_ok = false;
+    void *tma_buf[2] = {nullptr, nullptr};
+    TmaMaps tma_maps[2];
     // timing
     bool timing = false;
     std::vector<EventPair> events;
@@ -162,6 +171,34 @@ inline void timing_fold(lbm_handle *h) {
     h->events.clear();
 }
 
+// Tensor maps of a population buffer viewed as a 2D tensor (node index, plane); cuTensorMapEncodeTiled
+// is fetched through the runtime's driver entry point so the library does not link libcuda.
+inline bool encode_population_maps(void *base, long long npad, int planes, int K, TmaMaps *out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)planes};
+    const cuuint64_t strides[1] = {(cuuint64_t)npad * 4};
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint32_t wide[2] = {(cuuint32_t)kTmaWide, (cuuint32_t)K}, narrow[2] = {(cuuint32_t)kTmaNarrow, (cuuint32_t)K};
+    CUresult r1 = encode(&out->wide, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, wide, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = encode(&out->narrow, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, narrow, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
 // =============================================================================================
 // precision- and dimension-specialised operations
 // =============================================================================================
@@ -232,7 +269,31 @@ template <typename real, int D> struct Impl {
         return p;
     }
 
+    // FP32 only: tensor maps for the TMA-staged gather (needs node rows aligned to 4 floats)
+    static void setup_tma(lbm_handle *h) {
+        h->tma_ok = false;
+        if constexpr (sizeof(real) == 4) {
+            const char *off = std::getenv("LBM_B300_NO_TMA");
+            if ((off && off[0] == '1') || (h->box.nx % 4) != 0) return;
+            bool ok = true;
+            for (int j = 0; j < 2; ++j) {
+                h->tma_buf[j] = j == 0 ? h->fA : h->fB;
+                ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j]);
+            }
+            if (ok) {
+                cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                cudaFuncSetAttribute(k_gather_moments_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            }
+            h->tma_ok = ok;
+        }
+    }
+
+    static const TmaMaps *maps_of(lbm_handle *h, const void *buf) {
+        return h->tma_buf[0] == buf ? &h->tma_maps[0] : &h->tma_maps[1];
+    }
+
     static int link_build(lbm_handle *h) {
+        setup_tma(h);
         if (h->nseg == 0) return LBM_OK;
         k_link_build<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
             h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, h->dshapes, h->nshapes, h->dbcs, h->nbc,
@@ -298,8 +359,9 @@ template <typename real, int D> struct Impl {
             src = A;
         }
         if (h->n_dir == 0) {
-            k_reduce_partial<real, D><<<g, 128, 0, h->stream>>>(p, src, h->partial);
-            k_reduce_final<D><<<1, 256, 0, h->stream>>>(h->partial, (int)g, 1.0 / (double)h->n_active, h->mean);
+            const unsigned gr = std::min<unsigned>(g, kReduceBlocks);
+            k_reduce_partial<real, D><<<gr, 128, 0, h->stream>>>(p, src, h->partial);
+            k_reduce_final<D><<<1, 256, 0, h->stream>>>(h->partial, (int)gr, 1.0 / (double)h->n_active, h->mean);
             h->launches += 2;
             CKL();
         } else {
@@ -320,7 +382,12 @@ template <typename real, int D> struct Impl {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 0);
                 if (h->phase == 0) k_stream_collide<real, D, 0><<<g, 128, 0, h->stream>>>(a);
-                else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                else if constexpr (sizeof(real) == 4) {
+                    if (h->tma_ok)
+                        k_stream_collide_tma<D><<<g, 128, TmaLayout<D>::block_bytes(4), h->stream>>>(a, *maps_of(h, h->fA));
+                    else
+                        k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                } else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
                 if (h->timing) timing_end(h, ep);
                 h->launches++;
                 CKL();
@@ -328,7 +395,12 @@ template <typename real, int D> struct Impl {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 2);
                 if (h->phase == 0) k_gather_moments<real, D, 0><<<g, 128, 0, h->stream>>>(a);
-                else k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                else if constexpr (sizeof(real) == 4) {
+                    if (h->tma_ok)
+                        k_gather_moments_tma<D><<<g, 128, TmaLayout<D>::block_bytes(4), h->stream>>>(a, *maps_of(h, h->fA));
+                    else
+                        k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                } else k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
                 h->launches++;
                 CKL();
                 real *d = nullptr;

@@ -1038,16 +1038,26 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
             ++l;
         }
     }
+    double um[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) um[i] = a.u0[i * P + node];
     #pragma unroll
     for (int q = 0; q < 2 * D; ++q) {
         if ((cut >> q) & 1) continue;
         const int A = q >> 1;
-        const double s = (q & 1) ? -1.0 : 1.0;
         const int ln = nbr(a.b, node, x, y, z, q);
         #pragma unroll
-        for (int i = 0; i < D; ++i)
-            r[i] += a.u0[i * P + ln] - a.u0[i * P + node] +
-                    0.5 * ((double)a.Gst[(i * D + A) * P + node] + (double)a.Gst[(i * D + A) * P + ln]) * (-s * a.b.dx);
+        for (int i = 0; i < D; ++i) {
+            const real Gm = a.Gst[(i * D + A) * P + node], Gl = a.Gst[(i * D + A) * P + ln];
+            if constexpr (kShifted<real>) {
+                // FP32 edge term (a difference of nearby displacements and a dx-sized G term), FP64 sum
+                const real sdx = (q & 1) ? (real)a.b.dx : -(real)a.b.dx;
+                r[i] += (double)((real)(a.u0[i * P + ln] - um[i]) + real(0.5) * (Gm + Gl) * sdx);
+            } else {
+                const double s = (q & 1) ? -1.0 : 1.0;
+                r[i] += a.u0[i * P + ln] - um[i] + 0.5 * ((double)Gm + (double)Gl) * (-s * a.b.dx);
+            }
+        }
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i];
@@ -1061,17 +1071,22 @@ __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const re
     const unsigned cut = fl & kCutMask;
     const int deg = proj_degree(D, cut, __ldg(a.dmask + node));
     const real beta = (real)a.beta;
+    const real w = deg > 0 ? beta / (real)deg : real(0);
+    int nb[2 * D];
+    #pragma unroll
+    for (int q = 0; q < 2 * D; ++q) nb[q] = ((cut >> q) & 1) ? -1 : nbr(a.b, node, x, y, z, q);
     #pragma unroll
     for (int i = 0; i < D; ++i) {
+        const real *di = din + i * P;
         real acc = a.resid[i * P + node];
         real d = 0;
         if (din) {
-            d = din[i * P + node];
+            d = di[node];
             #pragma unroll
             for (int q = 0; q < 2 * D; ++q)
-                if (!((cut >> q) & 1)) acc += __ldg(din + i * P + nbr(a.b, node, x, y, z, q));
+                if (nb[q] >= 0) acc += __ldg(di + nb[q]);
         }
-        dout[i * P + node] = deg > 0 ? (real(1) - beta) * d + beta * acc / (real)deg : d;
+        dout[i * P + node] = deg > 0 ? (real(1) - beta) * d + w * acc : d;
     }
 }
 
@@ -1083,15 +1098,15 @@ __global__ void __launch_bounds__(128) k_reduce_partial(const ProjArgs<real> a, 
     double d[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) d[i] = 0.0;
-    const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (sgi < a.nseg) {
+    // fixed grid, segments strided over it, so the partial count (and the summation order) is fixed
+    for (int sgi = blockIdx.x * 4 + (threadIdx.x >> 5); sgi < a.nseg; sgi += gridDim.x * 4) {
         const int2 sg = __ldg(&a.seg[sgi]);
         const int x = sg.x - sg.y * a.b.nx + lane;
         const int node = sg.x + lane;
         if (x < a.b.nx && (__ldg(a.flags + node) & kActive)) {
             #pragma unroll
-            for (int i = 0; i < D; ++i) d[i] = (double)dc[i * a.b.npad + node];
+            for (int i = 0; i < D; ++i) d[i] += (double)dc[i * a.b.npad + node];
         }
     }
     #pragma unroll
@@ -1178,27 +1193,37 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     const real J = piola<real, D>(Fr, a.mu, a.lam, Pk);
     const int st = check_state<real, D>(v, Fr, J);
     if (st) set_status(a.status, st);
-    real f[Q * K];
     const real Dc = real(D) / a.c;
-    if constexpr (kShifted<real>) {
+    const real src = a.dt * (real(2) - a.omega) * (real(1) / real(4 * D));
+    real B[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const real s = (q & 1) ? real(-1) : real(1);
         #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int A = q >> 1;
-            const real s = (q & 1) ? real(-1) : real(1);
-            #pragma unroll
-            for (int i = 0; i < D; ++i)  // f += f^eq(v, F^r) - f^eq(v, F): v rows carry -(s/2c)(P^r - P)_{iA}
-                f[q * K + i] = a.fdst[(long long)(q * K + i) * P + node] -
-                               div2D<real, D>(s * Dc * (Pk[i * D + A] - Pold[i * D + A]));
-            #pragma unroll
-            for (int k = 0; k < D * D; ++k)
-                f[q * K + D + k] = a.fdst[(long long)(q * K + D + k) * P + node] + div2D<real, D>(Gr[k] - G[k]);
+        for (int k = 0; k < K; ++k) {
+            real fv = a.fdst[(long long)(q * K + k) * P + node];
+            real feq;  // equilibrium at the repaired state (Eq. feq-general-d)
+            if (k < D) {
+                const int i = k;
+                feq = div2D<real, D>(v[i] - s * Dc * Pk[i * D + A]);
+                // repair: f += f^eq(v, F^r) - f^eq(v, F) (Eq. projection-population-repair)
+                if constexpr (kShifted<real>) fv = fv - div2D<real, D>(s * Dc * (Pk[i * D + A] - Pold[i * D + A]));
+                else fv = fv + (feq - div2D<real, D>(v[i] - s * Dc * Pold[i * D + A]));
+            } else {
+                const int i = (k - D) / D, Bc = (k - D) % D;
+                const real Xr = kShifted<real> ? Gr[i * D + Bc] : Fr[i * D + Bc];
+                const real Xo = kShifted<real> ? G[i * D + Bc] : F[i * D + Bc];
+                const real vs = (A == Bc) ? s * Dc * v[i] : real(0);
+                feq = (A == Bc) ? div2D<real, D>(Xr - vs) : div2D<real, D>(Xr);
+                if constexpr (kShifted<real>) fv = fv + div2D<real, D>(Gr[i * D + Bc] - G[i * D + Bc]);
+                else fv = fv + (feq - ((A == Bc) ? div2D<real, D>(Xo - vs) : div2D<real, D>(Xo)));
+            }
+            // BGK collision with source (Eq. collision-general-d)
+            a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : real(0));
         }
-    } else {
-        real fr[Q * K], fo[Q * K];
-        equilibrium<real, D>(v, Fr, Pk, Dc, fr);
-        equilibrium<real, D>(v, F, Pold, Dc, fo);
-        #pragma unroll
-        for (int j = 0; j < Q * K; ++j) f[j] = a.fdst[(long long)j * P + node] + (fr[j] - fo[j]);
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -1208,7 +1233,6 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = Gr[k];
-    collide_store<real, D>(a, node, f, v, Gr, Fr, Pk);
 }
 
 // after the second solve: u^n = u0 + d - mean and u*^{n+1} = u^n + dt/2 v^n

@@ -1,0 +1,281 @@
+// TMA-staged gather for the FP32 fused collide-stream kernel (sm_103a).
+//
+// The pull gather of one 32-node x-segment reads, for every direction q, the K component
+// planes of f* at the segment shifted by -e_q.  Population planes are consecutive in a
+// 2D tensor (dim 0: node index, npad; dim 1: plane q*K + k), so the K planes of one
+// direction are one box of (width, K).  One elected lane per warp issues Q bulk tensor
+// copies into the warp's shared-memory slots, completed on a per-warp mbarrier:
+//   +-x: box (40, K) starting 4 nodes before the segment (a TMA start coordinate must be a
+//        multiple of 4 floats, so the +-1 shifted windows are read from an aligned wider box)
+//   +-y, +-z: box (32, K) at the source row (periodic rows wrapped).
+// The wait is bounded; on timeout the kernel latches a status bit, waits once more (bounded)
+// for its copies in flight and returns without writing.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_kernels.cuh"
+
+namespace tlv {
+
+constexpr int kStTimeout = 128;        // device status bit: a TMA wait ran out
+constexpr int kTmaSpin = 1 << 22;      // try_wait polls before giving up
+constexpr int kTmaWide = 40, kTmaNarrow = 32;
+
+template <int D> struct TmaLayout {
+    static constexpr int K = D + D * D, Q = 2 * D;
+    static constexpr int wide_bytes = ((kTmaWide * K * 4 + 127) / 128) * 128;
+    static constexpr int narrow_bytes = ((kTmaNarrow * K * 4 + 127) / 128) * 128;
+    static constexpr int warp_bytes = 2 * wide_bytes + (Q - 2) * narrow_bytes;
+    static constexpr int tx_bytes = 2 * kTmaWide * K * 4 + (Q - 2) * kTmaNarrow * K * 4;
+    // byte offset of direction q's slot in a warp region
+    __device__ static constexpr int slot(int q) { return q < 2 ? q * wide_bytes : 2 * wide_bytes + (q - 2) * narrow_bytes; }
+    __device__ static constexpr int width(int q) { return q < 2 ? kTmaWide : kTmaNarrow; }
+    // element offset of lane 0's source inside the box row
+    __device__ static constexpr int lane0(int q) { return q == 0 ? 3 : (q == 1 ? 5 : 0); }
+    static constexpr int block_bytes(int warps) { return warps * warp_bytes + warps * 8; }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < kTmaSpin; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Issue the Q bulk copies of segment sg into the warp's slots and wait for them.  Returns false
+// (status latched) if the wait ran out.  Every lane of the warp must call it.
+template <int D>
+__device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorMap *wide, const CUtensorMap *narrow,
+                                                   char *wsm, uint64_t *bar, int2 sg, int lane, int *status) {
+    using L = TmaLayout<D>;
+    constexpr int K = L::K, Q = L::Q;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int y = sg.y % b.ny, z = sg.y / b.ny, x0 = sg.x - sg.y * b.nx;
+        mbar_arrive_expect_tx(bar, L::tx_bytes);
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int A = q >> 1, s = (q & 1) ? -1 : 1;  // pull source of direction q is m - s e_A
+            int start;
+            if (A == 0) {
+                start = sg.x - 4;
+            } else if (A == 1) {
+                int yy = y - s;
+                if (b.per[1]) yy = yy < 0 ? yy + b.ny : (yy >= b.ny ? yy - b.ny : yy);
+                start = (z * b.ny + yy) * b.nx + x0;
+            } else {
+                int zz = z - s;
+                if (b.per[2]) zz = zz < 0 ? zz + b.nz : (zz >= b.nz ? zz - b.nz : zz);
+                start = (zz * b.ny + y) * b.nx + x0;
+            }
+            tma_load_2d(wsm + L::slot(q), A == 0 ? wide : narrow, bar, start, q * K);
+        }
+    }
+    bool ok = mbar_wait_bounded(bar, 0);
+    if (!ok) {
+        if (lane == 0) set_status(status, kStTimeout);
+        mbar_wait_bounded(bar, 0);  // let the copies in flight land before the block can exit
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// value of direction q, component k for this lane from the staged slots
+template <int D> __device__ __forceinline__ float &staged(char *wsm, int q, int k, int lane) {
+    using L = TmaLayout<D>;
+    return reinterpret_cast<float *>(wsm + L::slot(q))[k * L::width(q) + L::lane0(q) + lane];
+}
+
+// gather + closure with TMA staging; the gathered (and reconstructed) values stay in shared memory
+template <int D>
+__device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm, int node, int x, int lane,
+                                            unsigned cut) {
+    constexpr int K = D + D * D, Q = 2 * D, LREC = K + 2;
+    const long long P = a.b.npad;
+    const float *__restrict__ fs = a.fsrc;
+    if (a.b.per[0]) {  // the aligned x windows do not wrap: patch the periodic ends
+        if (x == 0 && !((cut >> 1) & 1))
+            #pragma unroll
+            for (int k = 0; k < K; ++k) staged<D>(wsm, 0, k, lane) = __ldg(fs + (long long)(0 * K + k) * P + node + a.b.nx - 1);
+        if (x == a.b.nx - 1 && !(cut & 1))
+            #pragma unroll
+            for (int k = 0; k < K; ++k) staged<D>(wsm, 1, k, lane) = __ldg(fs + (long long)(1 * K + k) * P + node - (a.b.nx - 1));
+    }
+    if (!cut) return;
+    const float *rec0 = a.lrec + (long long)__ldg(a.lstart + node) * LREC;
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int qo = q ^ 1;
+        if ((cut >> qo) & 1) {
+            const float *rec = rec0 + __popc(cut & ((1u << qo) - 1u)) * LREC;
+            const float eta = rec[0];
+            const bool neu = rec[1] != 0.0f;
+            const bool up = !((cut >> q) & 1);
+            #pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float Dk = ((k < D) == neu) ? 1.0f : -1.0f;
+                const float S = rec[2 + k];
+                const float fo = __ldg(fs + (long long)(qo * K + k) * P + node);
+                const float fi = __ldg(fs + (long long)(q * K + k) * P + node);
+                float r;
+                if (eta >= 0.5f) {
+                    r = (Dk * fo + S) / (2.0f * eta) + (1.0f - 1.0f / (2.0f * eta)) * fi;
+                } else {
+                    const float fu = up ? staged<D>(wsm, qo, k, lane) : fo;
+                    r = Dk * (2.0f * eta * fo + (1.0f - 2.0f * eta) * fu) + S;
+                }
+                staged<D>(wsm, q, k, lane) = r;
+            }
+        }
+    }
+}
+
+struct TmaMaps {
+    CUtensorMap wide, narrow;
+};
+
+// K3 with TMA staging (FP32): one warp per 32-node segment, 4 warps per block
+template <int D>
+__global__ void __launch_bounds__(128, 4) k_stream_collide_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    using L = TmaLayout<D>;
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sgi = blockIdx.x * 4 + warp;
+    if (sgi >= a.nseg) return;
+    char *wsm = smem + warp * L::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
+    const int2 sg = __ldg(&a.seg[sgi]);
+    if (!tma_gather_segment<D>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
+    const int x = sg.x - sg.y * a.b.nx + lane;
+    if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
+    const uint8_t fl = __ldg(a.flags + node);
+    if (!(fl & kActive)) return;
+    const unsigned cut = fl & kCutMask;
+    tma_closure<D>(a, wsm, node, x, lane, cut);
+    // recovery (Eq. state-recovery-general) from the staged populations
+    float v[D], G[D * D], F[D * D], Pk[D * D];
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float s = staged<D>(wsm, 0, k, lane);
+        #pragma unroll
+        for (int q = 1; q < Q; ++q) s += staged<D>(wsm, q, k, lane);
+        if (k < D) v[k] = (s + 0.5f * a.dt * a.bf[k]) / (1.0f + 0.5f * a.dt * a.gamma);
+        else { G[k - D] = s; F[k - D] = s + ((((k - D) / D) == ((k - D) % D)) ? 1.0f : 0.0f); }
+    }
+    const float J = piola<float, D>(F, a.mu, a.lam, Pk);
+    const int st = check_state<float, D>(v, F, J);
+    if (st) set_status(a.status, st);
+    const long long P = a.b.npad;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const float un = a.ustar[i * P + node] + 0.5f * a.dt * v[i];
+        if (fl & kNeedU) a.un[i * P + node] = un;
+        a.ustar[i * P + node] = un + 0.5f * a.dt * v[i];
+    }
+    // BGK collision with source (Eq. collision-general-d), shifted storage
+    const float Dc = float(D) / a.c, inv2D = 1.0f / float(2 * D);
+    const float src = a.dt * (2.0f - a.omega) * (1.0f / float(4 * D));
+    float B[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const float s = (q & 1) ? -1.0f : 1.0f;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float feq = (v[i] - s * Dc * Pk[i * D + A]) * inv2D;
+            const float fv = staged<D>(wsm, q, i, lane);
+            a.fdst[(long long)(q * K + i) * P + node] = fv + a.omega * (feq - fv) + src * B[i];
+        }
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            #pragma unroll
+            for (int Bc = 0; Bc < D; ++Bc) {
+                const int k = D + i * D + Bc;
+                const float feq = (A == Bc) ? (G[i * D + Bc] - s * Dc * v[i]) * inv2D : G[i * D + Bc] * inv2D;
+                const float fv = staged<D>(wsm, q, k, lane);
+                a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv);
+            }
+    }
+}
+
+// projection steps, part 1, with TMA staging (FP32)
+template <int D>
+__global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    using L = TmaLayout<D>;
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sgi = blockIdx.x * 4 + warp;
+    if (sgi >= a.nseg) return;
+    char *wsm = smem + warp * L::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
+    const int2 sg = __ldg(&a.seg[sgi]);
+    if (!tma_gather_segment<D>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
+    const int x = sg.x - sg.y * a.b.nx + lane;
+    if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
+    const uint8_t fl = __ldg(a.flags + node);
+    if (!(fl & kActive)) return;
+    tma_closure<D>(a, wsm, node, x, lane, fl & kCutMask);
+    const long long P = a.b.npad;
+    float v[D];
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float s = staged<D>(wsm, 0, k, lane);
+        a.fdst[(long long)(0 * K + k) * P + node] = s;
+        #pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const float fq = staged<D>(wsm, q, k, lane);
+            a.fdst[(long long)(q * K + k) * P + node] = fq;
+            s += fq;
+        }
+        if (k < D) v[k] = (s + 0.5f * a.dt * a.bf[k]) / (1.0f + 0.5f * a.dt * a.gamma);
+        else a.Gst[(k - D) * P + node] = s;
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        a.vst[i * P + node] = v[i];
+        a.u0[i * P + node] = (double)a.ustar[i * P + node] + 0.5 * (double)a.dt * (double)v[i];
+    }
+}
+
+}  // namespace tlv
