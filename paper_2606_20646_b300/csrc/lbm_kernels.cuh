@@ -849,17 +849,33 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
                 #pragma unroll
                 for (int i = 0; i < D; ++i) g[al][i] = t[al][i];
         }
-        for (int j = 0; j < ns; ++j) {
-            const int k = a.L.sidx[(long long)j * a.L.ncut + l];
-            real w[D - 1];
+        // stencil entries in groups of 4: all index loads, then all displacement loads, then the sums,
+        // so each thread keeps several independent loads in flight
+        constexpr int U = 4;
+        for (int j0 = 0; j0 < ns; j0 += U) {
+            int kk[U];
+            real w[U][D - 1], uu[U][D];
             #pragma unroll
-            for (int al = 0; al < D - 1; ++al) w[al] = a.L.w[((long long)al * kLsqCap + j) * a.L.ncut + l];
-            #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation
-                const real du = kShifted<real> ? a.un[i * P + k] - um[i] : a.un[i * P + k];
+            for (int jj = 0; jj < U; ++jj) {
+                const int j = j0 + jj < ns ? j0 + jj : ns - 1;
+                kk[jj] = __ldg(a.L.sidx + (long long)j * a.L.ncut + l);
                 #pragma unroll
-                for (int al = 0; al < D - 1; ++al) g[al][i] += w[al] * du;
+                for (int al = 0; al < D - 1; ++al) w[jj][al] = __ldg(a.L.w + ((long long)al * kLsqCap + j) * a.L.ncut + l);
+            }
+            #pragma unroll
+            for (int jj = 0; jj < U; ++jj)
+                #pragma unroll
+                for (int i = 0; i < D; ++i) uu[jj][i] = a.un[i * P + kk[jj]];
+            #pragma unroll
+            for (int jj = 0; jj < U; ++jj) {
+                if (j0 + jj >= ns) break;
+                #pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation
+                    const real du = kShifted<real> ? uu[jj][i] - um[i] : uu[jj][i];
+                    #pragma unroll
+                    for (int al = 0; al < D - 1; ++al) g[al][i] += w[jj][al] * du;
+                }
             }
         }
         if constexpr (kShifted<real>) {
@@ -1039,8 +1055,9 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
         }
     }
     double um[D];
+    real rf[D];
     #pragma unroll
-    for (int i = 0; i < D; ++i) um[i] = a.u0[i * P + node];
+    for (int i = 0; i < D; ++i) { um[i] = a.u0[i * P + node]; rf[i] = real(0); }
     #pragma unroll
     for (int q = 0; q < 2 * D; ++q) {
         if ((cut >> q) & 1) continue;
@@ -1050,9 +1067,9 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
         for (int i = 0; i < D; ++i) {
             const real Gm = a.Gst[(i * D + A) * P + node], Gl = a.Gst[(i * D + A) * P + ln];
             if constexpr (kShifted<real>) {
-                // FP32 edge term (a difference of nearby displacements and a dx-sized G term), FP64 sum
+                // FP32 edge term: FP64 difference of the nearby displacements, then FP32
                 const real sdx = (q & 1) ? (real)a.b.dx : -(real)a.b.dx;
-                r[i] += (double)((real)(a.u0[i * P + ln] - um[i]) + real(0.5) * (Gm + Gl) * sdx);
+                rf[i] += (real)(a.u0[i * P + ln] - um[i]) + real(0.5) * (Gm + Gl) * sdx;
             } else {
                 const double s = (q & 1) ? -1.0 : 1.0;
                 r[i] += a.u0[i * P + ln] - um[i] + 0.5 * ((double)Gm + (double)Gl) * (-s * a.b.dx);
@@ -1060,7 +1077,7 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
         }
     }
     #pragma unroll
-    for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i];
+    for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i] + rf[i];
 }
 
 // one damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr)
@@ -1095,20 +1112,24 @@ template <typename real, int D>
 __global__ void __launch_bounds__(128) k_reduce_partial(const ProjArgs<real> a, const real *__restrict__ dc,
                                                         double *partial) {
     __shared__ double sm[4][D];
-    double d[D];
+    real dl[D];
     #pragma unroll
-    for (int i = 0; i < D; ++i) d[i] = 0.0;
+    for (int i = 0; i < D; ++i) dl[i] = real(0);
     const int lane = threadIdx.x & 31;
-    // fixed grid, segments strided over it, so the partial count (and the summation order) is fixed
+    // fixed grid, segments strided over it, so the partial count (and the summation order) is fixed;
+    // each thread pre-sums its own few values in the correction's precision, the rest is FP64
     for (int sgi = blockIdx.x * 4 + (threadIdx.x >> 5); sgi < a.nseg; sgi += gridDim.x * 4) {
         const int2 sg = __ldg(&a.seg[sgi]);
         const int x = sg.x - sg.y * a.b.nx + lane;
         const int node = sg.x + lane;
         if (x < a.b.nx && (__ldg(a.flags + node) & kActive)) {
             #pragma unroll
-            for (int i = 0; i < D; ++i) d[i] += (double)dc[i * a.b.npad + node];
+            for (int i = 0; i < D; ++i) dl[i] += dc[i * a.b.npad + node];
         }
     }
+    double d[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) d[i] = (double)dl[i];
     #pragma unroll
     for (int i = 0; i < D; ++i)
         #pragma unroll
@@ -1168,17 +1189,31 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         const int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
         #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double gc;
-            bool keep = false;
-            const double up = u0[i * P + lp] + (double)dc[i * P + lp];
-            const double um = u0[i * P + lm] + (double)dc[i * P + lm];
-            const double uo = u0[i * P + node] + (double)dc[i * P + node];
-            if (ap && am) gc = (up - um) / (2.0 * a.b.dx);
-            else if (ap) gc = (up - uo) / a.b.dx;
-            else if (am) gc = (uo - um) / a.b.dx;
-            else { gc = 0.0; keep = true; }
-            const real Gc = keep ? G[i * D + A] : (real)gc;
-            Gr[i * D + A] = (real)((1.0 - theta) * (double)G[i * D + A] + theta * (double)Gc);
+            real Gc;
+            if constexpr (kShifted<real>) {
+                // FP32 form: u^c differences taken in FP64 (u carries the large offset), the rest in FP32
+                const double uo = u0[i * P + node];
+                const real dp = (real)(u0[i * P + lp] - uo) + (dc[i * P + lp] - dc[i * P + node]);
+                const real dm = (real)(uo - u0[i * P + lm]) + (dc[i * P + node] - dc[i * P + lm]);
+                const real inv = real(1) / (real)a.b.dx;
+                if (ap && am) Gc = real(0.5) * (dp + dm) * inv;
+                else if (ap) Gc = dp * inv;
+                else if (am) Gc = dm * inv;
+                else Gc = G[i * D + A];
+                Gr[i * D + A] = (real(1) - (real)theta) * G[i * D + A] + (real)theta * Gc;
+            } else {
+                double gc;
+                bool keep = false;
+                const double up = u0[i * P + lp] + (double)dc[i * P + lp];
+                const double um = u0[i * P + lm] + (double)dc[i * P + lm];
+                const double uo = u0[i * P + node] + (double)dc[i * P + node];
+                if (ap && am) gc = (up - um) / (2.0 * a.b.dx);
+                else if (ap) gc = (up - uo) / a.b.dx;
+                else if (am) gc = (uo - um) / a.b.dx;
+                else { gc = 0.0; keep = true; }
+                Gc = keep ? G[i * D + A] : (real)gc;
+                Gr[i * D + A] = (real)((1.0 - theta) * (double)G[i * D + A] + theta * (double)Gc);
+            }
         }
     }
     #pragma unroll
@@ -1227,9 +1262,9 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const double un = u0[i * P + node] + (double)dc[i * P + node] - mean[i];
+        const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
         u1[i * P + node] = un;
-        a.ustar[i * P + node] = (real)(un + 0.5 * (double)a.dt * (double)v[i]);
+        a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = Gr[k];
@@ -1243,9 +1278,9 @@ __global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, cons
     const long long P = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const double un = u0[i * P + node] + (double)dc[i * P + node] - mean[i];
-        a.un[i * P + node] = (real)un;
-        a.ustar[i * P + node] = (real)(un + 0.5 * (double)a.dt * (double)a.vst[i * P + node]);
+        const real un = (real)(u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]));
+        a.un[i * P + node] = un;
+        a.ustar[i * P + node] = un + real(0.5) * a.dt * a.vst[i * P + node];
     }
 }
 

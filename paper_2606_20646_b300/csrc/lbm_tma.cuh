@@ -169,27 +169,40 @@ struct TmaMaps {
     CUtensorMap wide, narrow;
 };
 
-// K3 with TMA staging (FP32): one warp per 32-node segment, 4 warps per block
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// issue the Q bulk copies of segment sg into slots wsm (lane 0 only)
 template <int D>
-__global__ void __launch_bounds__(128, 4) k_stream_collide_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
-    constexpr int K = D + D * D, Q = 2 * D;
+__device__ __forceinline__ void tma_issue(const Box &b, const TmaMaps &maps, char *wsm, uint64_t *bar, int2 sg) {
     using L = TmaLayout<D>;
-    extern __shared__ __align__(128) char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sgi = blockIdx.x * 4 + warp;
-    if (sgi >= a.nseg) return;
-    char *wsm = smem + warp * L::warp_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
-    const int2 sg = __ldg(&a.seg[sgi]);
-    if (!tma_gather_segment<D>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
-    const int x = sg.x - sg.y * a.b.nx + lane;
-    if (x >= a.b.nx) return;
-    const int node = sg.x + lane;
-    const uint8_t fl = __ldg(a.flags + node);
-    if (!(fl & kActive)) return;
-    const unsigned cut = fl & kCutMask;
-    tma_closure<D>(a, wsm, node, x, lane, cut);
-    // recovery (Eq. state-recovery-general) from the staged populations
+    constexpr int K = L::K, Q = L::Q;
+    const int y = sg.y % b.ny, z = sg.y / b.ny, x0 = sg.x - sg.y * b.nx;
+    fence_proxy_async_smem();  // generic-proxy writes to these slots (closure) precede the async copies
+    mbar_arrive_expect_tx(bar, L::tx_bytes);
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1, s = (q & 1) ? -1 : 1;  // pull source of direction q is m - s e_A
+        int start;
+        if (A == 0) {
+            start = sg.x - 4;
+        } else if (A == 1) {
+            int yy = y - s;
+            if (b.per[1]) yy = yy < 0 ? yy + b.ny : (yy >= b.ny ? yy - b.ny : yy);
+            start = (z * b.ny + yy) * b.nx + x0;
+        } else {
+            int zz = z - s;
+            if (b.per[2]) zz = zz < 0 ? zz + b.nz : (zz >= b.nz ? zz - b.nz : zz);
+            start = (zz * b.ny + y) * b.nx + x0;
+        }
+        tma_load_2d(wsm + L::slot(q), A == 0 ? &maps.wide : &maps.narrow, bar, start, q * K);
+    }
+}
+
+// recovery, collision and u quadrature of one node from its staged populations
+template <int D>
+__device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
+                                               const float us[D]) {
+    constexpr int K = D + D * D, Q = 2 * D;
     float v[D], G[D * D], F[D * D], Pk[D * D];
     #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -205,11 +218,10 @@ __global__ void __launch_bounds__(128, 4) k_stream_collide_tma(const StepArgs<fl
     const long long P = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const float un = a.ustar[i * P + node] + 0.5f * a.dt * v[i];
+        const float un = us[i] + 0.5f * a.dt * v[i];
         if (fl & kNeedU) a.un[i * P + node] = un;
         a.ustar[i * P + node] = un + 0.5f * a.dt * v[i];
     }
-    // BGK collision with source (Eq. collision-general-d), shifted storage
     const float Dc = float(D) / a.c, inv2D = 1.0f / float(2 * D);
     const float src = a.dt * (2.0f - a.omega) * (1.0f / float(4 * D));
     float B[D];
@@ -234,6 +246,65 @@ __global__ void __launch_bounds__(128, 4) k_stream_collide_tma(const StepArgs<fl
                 const float fv = staged<D>(wsm, q, k, lane);
                 a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv);
             }
+    }
+}
+
+// K3 with TMA staging (FP32), persistent: each warp walks segments w, w + W, ... with two stages,
+// the bulk copies of its next segment in flight while it computes the current one.
+template <int D>
+__global__ void __launch_bounds__(128) k_stream_collide_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
+    using L = TmaLayout<D>;
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i = blockIdx.x * 4 + warp;
+    if (i >= a.nseg) return;
+    const int W = gridDim.x * 4;
+    char *const buf0 = smem + (2 * warp) * L::warp_bytes, *const buf1 = buf0 + L::warp_bytes;
+    uint64_t *const bar0 = reinterpret_cast<uint64_t *>(smem + 8 * L::warp_bytes) + 2 * warp, *const bar1 = bar0 + 1;
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    int2 sg = __ldg(&a.seg[i]);
+    if (lane == 0) tma_issue<D>(a.b, maps, buf0, bar0, sg);
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool odd = false;  // current stage: buf0/bar0 when false
+    for (;;) {
+        const int inext = i + W;
+        int2 sgn = make_int2(0, 0);
+        if (inext < a.nseg) {
+            sgn = __ldg(&a.seg[inext]);
+            if (lane == 0) tma_issue<D>(a.b, maps, odd ? buf0 : buf1, odd ? bar0 : bar1, sgn);
+        }
+        // per-lane reads of the current segment, issued before waiting for its copies
+        const int x = sg.x - sg.y * a.b.nx + lane;
+        const int node = sg.x + lane;
+        const uint8_t fl = x < a.b.nx ? __ldg(a.flags + node) : (uint8_t)0;
+        const bool act = fl & kActive;
+        float us[D];
+        #pragma unroll
+        for (int d = 0; d < D; ++d) us[d] = act ? a.ustar[d * a.b.npad + node] : 0.0f;
+        char *const cur = odd ? buf1 : buf0;
+        uint64_t *const cbar = odd ? bar1 : bar0;
+        const uint32_t cph = odd ? ph1 : ph0;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(cbar, cph))) {  // warp-uniform outcome
+            if (lane == 0) set_status(a.status, kStTimeout);
+            mbar_wait_bounded(cbar, cph);  // let copies in flight land before exiting
+            if (inext < a.nseg) mbar_wait_bounded(odd ? bar0 : bar1, odd ? ph0 : ph1);
+            return;
+        }
+        if (odd) ph1 ^= 1u; else ph0 ^= 1u;
+        if (act) {
+            tma_closure<D>(a, cur, node, x, lane, fl & kCutMask);
+            collide_staged<D>(a, cur, node, lane, fl, us);
+        }
+        __syncwarp();  // every lane is done with this stage before it is refilled
+        if (inext >= a.nseg) break;
+        i = inext;
+        sg = sgn;
+        odd = !odd;
     }
 }
 
