@@ -257,6 +257,29 @@ int lbm_copy_active(lbm_handle *h, unsigned char *mask);
 void lbm_destroy(lbm_handle *h);
 const char *lbm_error_string(int code);
 
+/* Largest box (nodes) lbm_census_static accepts: 2^24, e.g. 256^3. */
+#define LBM_CENSUS_MAX_NODES (1LL << 24)
+
+/* Geometry census that allocates nothing.  No counterpart in the paper: it exists for
+ * callers that must not allocate device memory when they size a simulation -- code running
+ * while a CUDA graph is being captured (an allocation would break or end the capture) and
+ * embedding runtimes whose device memory belongs to their own pool.  It returns the same
+ * counts that lbm_create computes (lbm_info.n_active, n_cut, n_segments) for the grid and
+ * level set, which size the storage of lbm_create and lbm_bind_storage.
+ *
+ * Scratch: one file-scope device array of 256 + LBM_CENSUS_MAX_NODES bytes (the active mask
+ * and three counters), held by every GPU that loads the library until the process exits.
+ * The first call on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture.  All
+ * calls on a device share the array, so calls that overlap on the GPU race; each call clears
+ * the counters and rewrites the mask before use.  Work is enqueued on cuda_stream, then the
+ * call synchronises that stream to return the counts.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ * Errors: LBM_ERR_ARG (invalid grid or level set), LBM_ERR_CAPACITY (more than
+ * LBM_CENSUS_MAX_NODES box nodes), LBM_ERR_CUDA. */
+int lbm_census_static(const lbm_grid *grid, const lbm_levelset *levelset, void *cuda_stream, long long *n_active,
+                      long long *n_cut, long long *n_segments);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,8 @@ LIB = os.path.join(HERE, "liblbm_b300.so")
 # its arithmetic follows the FP64 oracle operation for operation
 SOURCES = [(os.path.join(HERE, "csrc", "lbm_api.cu"), []),
            (os.path.join(HERE, "csrc", "lbm_fp32.cu"), []),
-           (os.path.join(HERE, "csrc", "lbm_fp64.cu"), ["-fmad=false"])]
+           (os.path.join(HERE, "csrc", "lbm_fp64.cu"), ["-fmad=false"]),
+           (os.path.join(HERE, "csrc", "lbm_static.cu"), [])]
 DEPENDS = glob.glob(os.path.join(HERE, "csrc", "*")) + [os.path.join(ROOT, "include", "lbm.h")]
 
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -21,7 +21,7 @@ _BCKIND = {"dirichlet": 0, "neumann": 1}
 _PROFILE = {"zero": 0, "affine": 1, "radial": 2, "twist_stretch": 3, "const": 4}
 _RAMP = {"one": 0, "linear": 1, "sin2": 2, "cos": 3, "time": 4}
 PREC = {"fp64": 0, "fp32": 1}
-DEV_STATUS = {1: "nonfinite", 2: "jacobian", 4: "newton", 8: "lsq", 16: "capacity"}
+DEV_STATUS = {1: "nonfinite", 2: "jacobian", 4: "newton", 8: "lsq", 16: "capacity", 128: "timeout"}
 MAX_SHAPES = 16
 MAX_BCS = 16
 
@@ -89,6 +89,8 @@ SIGNATURES = {
     "lbm_copy_active": (C.c_int, [_vp, C.POINTER(C.c_ubyte)]),
     "lbm_destroy": (None, [_vp]),
     "lbm_error_string": (C.c_char_p, [C.c_int]),
+    "lbm_census_static": (C.c_int, [C.POINTER(lbm_grid), C.POINTER(lbm_levelset), _vp, C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
 }
 
 _lib = None
@@ -274,3 +276,15 @@ class Simulation:
         m = np.zeros(self.p.n_box, dtype=np.uint8)
         _check(load_library().lbm_copy_active(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte))), "lbm_copy_active")
         return m.reshape(self.p.box_shape).astype(bool)
+
+
+def census_static(p, stream: torch.cuda.Stream | None = None) -> dict:
+    """Active nodes, cut links and active segments of a problem's grid and level set, computed
+    by lbm_census_static (no device allocation; scratch in the library's fixed device array)."""
+    lib = load_library()
+    g, shapes, ls, mat, bcs, opt = descriptors(p)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    a, c, s = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+    _check(lib.lbm_census_static(C.byref(g), C.byref(ls), C.c_void_p(st.cuda_stream), C.byref(a), C.byref(c),
+                                 C.byref(s)), "lbm_census_static")
+    return {"n_active": a.value, "n_cut": c.value, "n_segments": s.value}
