@@ -85,7 +85,7 @@ struct lbm_handle {
     // TMA staging of the FP32 gather: tensor maps of both population buffers
     bool tma_ok = false;
     unsigned tma_grid = 0;  // persistent grid of the fused kernel: SMs x resident blocks
-    int tma_smem = 0;
+    int tma_smem = 0, tma_stages = 0;
     void *tma_buf[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
     // timing
@@ -283,18 +283,24 @@ template <typename real, int D> struct Impl {
                 ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j]);
             }
             if (ok) {
-                const int bytes = 2 * TmaLayout<D>::block_bytes(4);
-                ok = cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
+                // stages of the producer/consumer ring: as many as fit next to the barriers
+                int dev = 0, smem_optin = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+                const int per_stage = TmaLayout<D>::warp_bytes + 16;
+                h->tma_stages = std::min(32, (smem_optin - 1024) / per_stage);
+                const int bytes = h->tma_stages * per_stage;
+                ok = h->tma_stages >= 4 &&
+                     cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
                          cudaSuccess &&
                      cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess &&
                      cudaFuncSetAttribute(k_gather_moments_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess;
-                int dev = 0, sms = 0, per_sm = 0;
-                ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
-                     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_tma<D>, 128, bytes) ==
-                         cudaSuccess &&
+                int sms = 0, per_sm = 0;
+                ok = ok && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_tma<D>, kPipeThreads,
+                                                                   bytes) == cudaSuccess &&
                      per_sm > 0;
                 h->tma_grid = (unsigned)(sms * per_sm);
                 h->tma_smem = bytes;
@@ -400,7 +406,8 @@ template <typename real, int D> struct Impl {
                 if (h->phase == 0) k_stream_collide<real, D, 0><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
                     if (h->tma_ok)
-                        k_stream_collide_tma<D><<<std::min(g, h->tma_grid), 128, h->tma_smem, h->stream>>>(a, *maps_of(h, h->fA));
+                        k_stream_collide_tma<D><<<h->tma_grid, kPipeThreads, h->tma_smem, h->stream>>>(
+                            a, *maps_of(h, h->fA), h->tma_stages);
                     else
                         k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
                 } else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);

@@ -249,36 +249,68 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     }
 }
 
-// K3 with TMA staging (FP32), persistent: each warp walks segments w, w + W, ... with two stages,
-// the bulk copies of its next segment in flight while it computes the current one.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kPipeConsumers = 12;                    // consumer warps per CTA
+constexpr int kPipeThreads = 32 * (1 + kPipeConsumers);
+
+// K3 with TMA staging (FP32), warp-specialised and persistent: one CTA per SM; warp 0 is the
+// producer, which streams the bulk copies of the CTA's segments (b, b + G, b + 2G, ...) into a
+// ring of `stages` shared-memory stages; consumer warp c computes the CTA's segments
+// c-1, c-1+C, ... .  Stage t % stages has a full barrier (completed by the copies' bytes) and
+// an empty barrier (arrived by the consumer when it is done with the stage).
 template <int D>
-__global__ void __launch_bounds__(128) k_stream_collide_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
+__global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const StepArgs<float> a,
+                                                                     const __grid_constant__ TmaMaps maps, int stages) {
     using L = TmaLayout<D>;
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int i = blockIdx.x * 4 + warp;
-    if (i >= a.nseg) return;
-    const int W = gridDim.x * 4;
-    char *const buf0 = smem + (2 * warp) * L::warp_bytes, *const buf1 = buf0 + L::warp_bytes;
-    uint64_t *const bar0 = reinterpret_cast<uint64_t *>(smem + 8 * L::warp_bytes) + 2 * warp, *const bar1 = bar0 + 1;
-    if (lane == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+    const int G = gridDim.x, b = blockIdx.x;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * L::warp_bytes);
+    uint64_t *empty = full + stages;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
         mbar_fence_init();
     }
-    __syncwarp();
-    int2 sg = __ldg(&a.seg[i]);
-    if (lane == 0) tma_issue<D>(a.b, maps, buf0, bar0, sg);
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool odd = false;  // current stage: buf0/bar0 when false
-    for (;;) {
-        const int inext = i + W;
-        int2 sgn = make_int2(0, 0);
-        if (inext < a.nseg) {
-            sgn = __ldg(&a.seg[inext]);
-            if (lane == 0) tma_issue<D>(a.b, maps, odd ? buf0 : buf1, odd ? bar0 : bar1, sgn);
+    __syncthreads();
+    const int nlocal = a.nseg > b ? (a.nseg - b + G - 1) / G : 0;  // segments of this CTA
+    if (warp == 0) {
+        // ---- producer ----
+        bool ok = true;
+        for (int t0 = 0; t0 < nlocal && ok; t0 += 32) {
+            // segment coordinates of the next 32 local segments, one round trip
+            const int tl = t0 + lane;
+            const int2 sgl = tl < nlocal ? __ldg(&a.seg[b + (long long)G * tl]) : make_int2(0, 0);
+            const int n = min(32, nlocal - t0);
+            for (int k = 0; k < n; ++k) {
+                const int t = t0 + k;
+                const int s = t % stages, use = t / stages;
+                const int2 sg = make_int2(__shfl_sync(0xffffffffu, sgl.x, k), __shfl_sync(0xffffffffu, sgl.y, k));
+                if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (use - 1) & 1));
+                if (!ok) break;
+                if (lane == 0) tma_issue<D>(a.b, maps, smem + (size_t)s * L::warp_bytes, &full[s], sg);
+                __syncwarp();
+            }
         }
-        // per-lane reads of the current segment, issued before waiting for its copies
+        if (!ok && lane == 0) set_status(a.status, kStTimeout);
+        // before the CTA can retire, every issued stage must have landed
+        const int last = nlocal < stages ? nlocal : stages;
+        for (int k = 0; k < last; ++k) {
+            const int t = nlocal - 1 - k;
+            mbar_wait_bounded(&full[t % stages], (t / stages) & 1);
+        }
+        return;
+    }
+    // ---- consumers ----
+    for (int t = warp - 1; t < nlocal; t += kPipeConsumers) {
+        const int s = t % stages, use = t / stages;
+        char *const cur = smem + (size_t)s * L::warp_bytes;
+        const int2 sg = __ldg(&a.seg[b + (long long)G * t]);
         const int x = sg.x - sg.y * a.b.nx + lane;
         const int node = sg.x + lane;
         const uint8_t fl = x < a.b.nx ? __ldg(a.flags + node) : (uint8_t)0;
@@ -286,25 +318,19 @@ __global__ void __launch_bounds__(128) k_stream_collide_tma(const StepArgs<float
         float us[D];
         #pragma unroll
         for (int d = 0; d < D; ++d) us[d] = act ? a.ustar[d * a.b.npad + node] : 0.0f;
-        char *const cur = odd ? buf1 : buf0;
-        uint64_t *const cbar = odd ? bar1 : bar0;
-        const uint32_t cph = odd ? ph1 : ph0;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(cbar, cph))) {  // warp-uniform outcome
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], use & 1))) {
             if (lane == 0) set_status(a.status, kStTimeout);
-            mbar_wait_bounded(cbar, cph);  // let copies in flight land before exiting
-            if (inext < a.nseg) mbar_wait_bounded(odd ? bar0 : bar1, odd ? ph0 : ph1);
             return;
         }
-        if (odd) ph1 ^= 1u; else ph0 ^= 1u;
         if (act) {
             tma_closure<D>(a, cur, node, x, lane, fl & kCutMask);
             collide_staged<D>(a, cur, node, lane, fl, us);
         }
-        __syncwarp();  // every lane is done with this stage before it is refilled
-        if (inext >= a.nseg) break;
-        i = inext;
-        sg = sgn;
-        odd = !odd;
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();  // this stage's shared-memory writes precede its next refill
+            mbar_arrive(&empty[s]);
+        }
     }
 }
 
