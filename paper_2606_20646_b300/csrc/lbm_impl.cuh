@@ -369,8 +369,9 @@ template <typename real, int D> struct Impl {
         real *A = static_cast<real *>(h->dA), *B = static_cast<real *>(h->dB);
         const real *src = nullptr;
         real *dst = A;
+        const unsigned gj = grid_for(h->nseg, 4 * kJacobiSegs);
         for (int it = 0; it < h->opt.proj_iters; ++it) {
-            k_jacobi<real, D><<<g, 128, 0, h->stream>>>(p, src, dst);
+            k_jacobi<real, D><<<gj, 128, 0, h->stream>>>(p, src, dst);
             h->launches++;
             src = dst;
             dst = (dst == A) ? B : A;

@@ -1080,30 +1080,62 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
     for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i] + rf[i];
 }
 
-// one damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr)
+constexpr int kJacobiSegs = 4;  // segments per warp in a Jacobi sweep (independent loads in flight)
+
+// one damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr);
+// warp w handles segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1
 template <typename real, int D>
 __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
-    TLV_NODE_PROLOGUE(a)
+    constexpr int S = kJacobiSegs;
+    const int lane = threadIdx.x & 31;
+    const int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
+    if (s0 >= a.nseg) return;
     const long long P = a.b.npad;
-    const unsigned cut = fl & kCutMask;
-    const int deg = proj_degree(D, cut, __ldg(a.dmask + node));
     const real beta = (real)a.beta;
-    const real w = deg > 0 ? beta / (real)deg : real(0);
-    int nb[2 * D];
+    int node[S], xs[S], ys[S], zs[S];
+    uint8_t fl[S], dm[S];
     #pragma unroll
-    for (int q = 0; q < 2 * D; ++q) nb[q] = ((cut >> q) & 1) ? -1 : nbr(a.b, node, x, y, z, q);
+    for (int j = 0; j < S; ++j) {
+        const int2 sg = s0 + j < a.nseg ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
+        xs[j] = s0 + j < a.nseg ? sg.x - sg.y * a.b.nx + lane : a.b.nx;
+        ys[j] = sg.y % a.b.ny;
+        zs[j] = sg.y / a.b.ny;
+        node[j] = sg.x + lane;
+    }
     #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const real *di = din + i * P;
-        real acc = a.resid[i * P + node];
-        real d = 0;
-        if (din) {
-            d = di[node];
-            #pragma unroll
-            for (int q = 0; q < 2 * D; ++q)
-                if (nb[q] >= 0) acc += __ldg(di + nb[q]);
+    for (int j = 0; j < S; ++j) {
+        const bool in = xs[j] < a.b.nx;
+        fl[j] = in ? __ldg(a.flags + node[j]) : (uint8_t)0;
+        dm[j] = in ? __ldg(a.dmask + node[j]) : (uint8_t)0;
+    }
+    real acc[S][D], dold[S][D];
+    #pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const bool act = fl[j] & kActive;
+        const unsigned cut = fl[j] & kCutMask;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            acc[j][i] = act ? a.resid[i * P + node[j]] : real(0);
+            dold[j][i] = (act && din) ? din[i * P + node[j]] : real(0);
         }
-        dout[i * P + node] = deg > 0 ? (real(1) - beta) * d + w * acc : d;
+        if (act && din) {
+            #pragma unroll
+            for (int q = 0; q < 2 * D; ++q) {
+                if ((cut >> q) & 1) continue;
+                const int ln = nbr(a.b, node[j], xs[j], ys[j], zs[j], q);
+                #pragma unroll
+                for (int i = 0; i < D; ++i) acc[j][i] += __ldg(din + i * P + ln);
+            }
+        }
+    }
+    #pragma unroll
+    for (int j = 0; j < S; ++j) {
+        if (!(fl[j] & kActive)) continue;
+        const int deg = proj_degree(D, fl[j] & kCutMask, dm[j]);
+        const real w = deg > 0 ? beta / (real)deg : real(0);
+        #pragma unroll
+        for (int i = 0; i < D; ++i)
+            dout[i * P + node[j]] = deg > 0 ? (real(1) - beta) * dold[j][i] + w * acc[j][i] : dold[j][i];
     }
 }
 

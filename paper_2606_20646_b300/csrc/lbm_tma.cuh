@@ -198,54 +198,78 @@ __device__ __forceinline__ void tma_issue(const Box &b, const TmaMaps &maps, cha
     }
 }
 
-// recovery, collision and u quadrature of one node from its staged populations
+// recovery, collision and u quadrature of one node from its staged populations (FP32 form).
+// Arithmetic is arranged to avoid divisions in the per-node path:
+//   v = (sum f_v + dt/2 b) * 1/(1 + gamma dt/2),  F^{-T} = cof(F) * (1/J),
+//   f*_q = (1 - omega) f_q + omega f^eq_q + src_q with omega f^eq_q = base_k +- (omega D/(2Dc)) Phi_A,k
 template <int D>
 __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
                                                const float us[D]) {
     constexpr int K = D + D * D, Q = 2 * D;
-    float v[D], G[D * D], F[D * D], Pk[D * D];
+    float S[K];
     #pragma unroll
     for (int k = 0; k < K; ++k) {
         float s = staged<D>(wsm, 0, k, lane);
         #pragma unroll
         for (int q = 1; q < Q; ++q) s += staged<D>(wsm, q, k, lane);
-        if (k < D) v[k] = (s + 0.5f * a.dt * a.bf[k]) / (1.0f + 0.5f * a.dt * a.gamma);
-        else { G[k - D] = s; F[k - D] = s + ((((k - D) / D) == ((k - D) % D)) ? 1.0f : 0.0f); }
+        S[k] = s;
     }
-    const float J = piola<float, D>(F, a.mu, a.lam, Pk);
-    const int st = check_state<float, D>(v, F, J);
-    if (st) set_status(a.status, st);
-    const long long P = a.b.npad;
+    const float hdt = 0.5f * a.dt;
+    const float inv_damp = 1.0f / (1.0f + hdt * a.gamma);
+    float v[D], F[D * D], C[D * D], P[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = (S[i] + hdt * a.bf[i]) * inv_damp;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) F[k] = S[D + k] + ((k / D == k % D) ? 1.0f : 0.0f);
+    cofactor<float, D>(F, C);
+    const float J = det<float, D>(F);
+    const float sJ = (0.5f * a.lam * (J * J - 1.0f) - a.mu) * (1.0f / J);
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) P[k] = a.mu * F[k] + sJ * C[k];
+    float chk = J;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) chk += v[i];
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) chk += P[k];
+    if (!(J > 0.0f) || !isfinite(chk)) set_status(a.status, (J > 0.0f ? 0 : kStJacobian) | (isfinite(chk) ? 0 : kStNonfinite));
+    const long long Pn = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const float un = us[i] + 0.5f * a.dt * v[i];
-        if (fl & kNeedU) a.un[i * P + node] = un;
-        a.ustar[i * P + node] = un + 0.5f * a.dt * v[i];
+        const float un = us[i] + hdt * v[i];
+        if (fl & kNeedU) a.un[i * Pn + node] = un;
+        a.ustar[i * Pn + node] = un + hdt * v[i];
     }
-    const float Dc = float(D) / a.c, inv2D = 1.0f / float(2 * D);
+    const float om1 = 1.0f - a.omega;
+    const float wf = a.omega * (1.0f / float(2 * D));  // omega/(2D)
+    const float wc = wf * (float(D) / a.c);             // omega/(2D) * D/c
     const float src = a.dt * (2.0f - a.omega) * (1.0f / float(4 * D));
-    float B[D];
+    float base[K];
     #pragma unroll
-    for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    for (int i = 0; i < D; ++i) base[i] = wf * v[i] + src * (a.bf[i] - a.gamma * v[i]);
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) base[D + k] = wf * S[D + k];
+    float wv[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) wv[i] = wc * v[i];
+    float *out = a.fdst + node;
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int A = q >> 1;
-        const float s = (q & 1) ? -1.0f : 1.0f;
+        const bool neg = q & 1;
         #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const float feq = (v[i] - s * Dc * Pk[i * D + A]) * inv2D;
-            const float fv = staged<D>(wsm, q, i, lane);
-            a.fdst[(long long)(q * K + i) * P + node] = fv + a.omega * (feq - fv) + src * B[i];
-        }
-        #pragma unroll
-        for (int i = 0; i < D; ++i)
-            #pragma unroll
-            for (int Bc = 0; Bc < D; ++Bc) {
-                const int k = D + i * D + Bc;
-                const float feq = (A == Bc) ? (G[i * D + Bc] - s * Dc * v[i]) * inv2D : G[i * D + Bc] * inv2D;
-                const float fv = staged<D>(wsm, q, k, lane);
-                a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv);
+        for (int k = 0; k < K; ++k) {
+            float t;
+            if (k < D) {
+                const float fl_ = wc * P[k * D + A];   // omega/(2D) (D/c) P_kA
+                t = neg ? base[k] + fl_ : base[k] - fl_;
+            } else if (((k - D) % D) == A) {
+                const int i = (k - D) / D;
+                t = neg ? base[k] + wv[i] : base[k] - wv[i];
+            } else {
+                t = base[k];
             }
+            out[(long long)(q * K + k) * Pn] = fmaf(om1, staged<D>(wsm, q, k, lane), t);
+        }
     }
 }
 
@@ -253,7 +277,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kPipeConsumers = 12;                    // consumer warps per CTA
+constexpr int kPipeConsumers = 14;                    // consumer warps per CTA
 constexpr int kPipeThreads = 32 * (1 + kPipeConsumers);
 
 // K3 with TMA staging (FP32), warp-specialised and persistent: one CTA per SM; warp 0 is the
