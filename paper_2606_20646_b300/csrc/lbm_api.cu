@@ -70,7 +70,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->resid = c.take<char>((size_t)D * np * rs);
         h->vst = c.take<char>((size_t)D * np * rs);
         h->Gst = c.take<char>((size_t)D * D * np * rs);
-        h->partial = c.take<double>((size_t)D * (grid_for(h->nseg, 4) + 1));
+        h->partial = c.take<double>((size_t)D * (std::max<size_t>(grid_for(h->nseg, 4), kReduceBlocks) + 1));
         h->mean = c.take<double>(4);
     } else {
         h->l_sidx = nullptr;

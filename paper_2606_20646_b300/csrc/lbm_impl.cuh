@@ -21,7 +21,7 @@
 using namespace tlv;
 
 constexpr size_t kAlign = 256;
-constexpr unsigned kReduceBlocks = 4 * 148;  // fixed grid of the gauge reduction (4 blocks per SM)
+constexpr unsigned kReduceBlocks = 16 * 148;  // fixed grid of the gauge reduction (16 blocks per SM)
 
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -175,6 +175,42 @@ inline void timing_fold(lbm_handle *h) {
 
 // Tensor maps of a population buffer viewed as a 2D tensor (node index, plane); cuTensorMapEncodeTiled
 // is fetched through the runtime's driver entry point so the library does not link libcuda.
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    return encode;
+}
+
+// u* planes (npad, D) with (32, D) boxes, and the flag bytes viewed as (nx, ny*nz) with (32, 1) boxes
+inline bool encode_meta_maps(void *ustar, long long npad, int D, void *flags, int nx, long long rows, TmaMaps *out) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint64_t udims[2] = {(cuuint64_t)npad, (cuuint64_t)D};
+    const cuuint64_t ustr[1] = {(cuuint64_t)npad * 4};
+    const cuuint32_t ubox[2] = {32, (cuuint32_t)D};
+    const cuuint64_t fdims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
+    const cuuint64_t fstr[1] = {(cuuint64_t)nx};
+    const cuuint32_t fbox[2] = {32, 1};
+    CUresult r1 = encode(&out->ustar, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ustar, udims, ustr, ubox, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = encode(&out->flags, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, flags, fdims, fstr, fbox, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
 inline bool encode_population_maps(void *base, long long npad, int planes, int K, TmaMaps *out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -276,18 +312,21 @@ template <typename real, int D> struct Impl {
         h->tma_ok = false;
         if constexpr (sizeof(real) == 4) {
             const char *off = std::getenv("LBM_B300_NO_TMA");
-            if ((off && off[0] == '1') || (h->box.nx % 4) != 0) return;
+            // population boxes need rows aligned to 4 floats; the flag box needs rows of 16 bytes
+            if ((off && off[0] == '1') || (h->box.nx % 16) != 0) return;
             bool ok = true;
             for (int j = 0; j < 2; ++j) {
                 h->tma_buf[j] = j == 0 ? h->fA : h->fB;
-                ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j]);
+                ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j]) &&
+                     encode_meta_maps(h->ustar, h->box.npad, D, h->flags, h->box.nx,
+                                      (long long)h->box.ny * h->box.nz, &h->tma_maps[j]);
             }
             if (ok) {
                 // stages of the producer/consumer ring: as many as fit next to the barriers
                 int dev = 0, smem_optin = 0;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-                const int per_stage = TmaLayout<D>::warp_bytes + 16;
+                const int per_stage = TmaLayout<D>::stage_bytes + 16;
                 h->tma_stages = std::min(32, (smem_optin - 1024) / per_stage);
                 const int bytes = h->tma_stages * per_stage;
                 ok = h->tma_stages >= 4 &&

@@ -40,9 +40,11 @@ __device__ __forceinline__ void node_xyz(const Box &b, int node, int &x, int &y,
     z = r / b.ny;
 }
 
-// neighbour m + e_q with periodic wrap (callers only use it for in-box or periodic neighbours)
+// neighbour m + e_q with periodic wrap (callers only use it for in-box or periodic neighbours);
+// without periodic axes it is a plain offset and the coordinates are not needed
 __device__ __forceinline__ int nbr(const Box &b, int node, int x, int y, int z, int q) {
     const int A = q >> 1, s = (q & 1) ? -1 : 1;
+    if (!(b.per[0] | b.per[1] | b.per[2])) return node + s * (A == 0 ? 1 : (A == 1 ? b.nx : b.nx * b.ny));
     if (A == 0) {
         int xn = x + s;
         xn = xn < 0 ? xn + b.nx : (xn >= b.nx ? xn - b.nx : xn);
@@ -1019,7 +1021,9 @@ __device__ __forceinline__ int proj_degree(int D, unsigned cut, uint8_t dm) {
     const int node = sg.x + lane;                                 \
     const uint8_t fl = __ldg((a).flags + node);                   \
     if (!(fl & kActive)) return;                                  \
-    const int y = sg.y % (a).b.ny, z = sg.y / (a).b.ny;           \
+    const bool per_ = (a).b.per[0] | (a).b.per[1] | (a).b.per[2]; \
+    const int y = per_ ? sg.y % (a).b.ny : 0;                     \
+    const int z = per_ ? sg.y / (a).b.ny : 0;                     \
     (void)y;                                                      \
     (void)z;
 
@@ -1097,9 +1101,10 @@ __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const re
     #pragma unroll
     for (int j = 0; j < S; ++j) {
         const int2 sg = s0 + j < a.nseg ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
+        const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
         xs[j] = s0 + j < a.nseg ? sg.x - sg.y * a.b.nx + lane : a.b.nx;
-        ys[j] = sg.y % a.b.ny;
-        zs[j] = sg.y / a.b.ny;
+        ys[j] = per ? sg.y % a.b.ny : 0;
+        zs[j] = per ? sg.y / a.b.ny : 0;
         node[j] = sg.x + lane;
     }
     #pragma unroll
@@ -1150,14 +1155,25 @@ __global__ void __launch_bounds__(128) k_reduce_partial(const ProjArgs<real> a, 
     const int lane = threadIdx.x & 31;
     // fixed grid, segments strided over it, so the partial count (and the summation order) is fixed;
     // each thread pre-sums its own few values in the correction's precision, the rest is FP64
-    for (int sgi = blockIdx.x * 4 + (threadIdx.x >> 5); sgi < a.nseg; sgi += gridDim.x * 4) {
-        const int2 sg = __ldg(&a.seg[sgi]);
-        const int x = sg.x - sg.y * a.b.nx + lane;
-        const int node = sg.x + lane;
-        if (x < a.b.nx && (__ldg(a.flags + node) & kActive)) {
-            #pragma unroll
-            for (int i = 0; i < D; ++i) dl[i] += dc[i * a.b.npad + node];
+    const int stride = gridDim.x * 4;
+    for (int s0 = blockIdx.x * 4 + (threadIdx.x >> 5); s0 < a.nseg; s0 += 4 * stride) {
+        // four segments per pass: their loads are independent
+        int node[4];
+        bool ok[4];
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int sgi = s0 + j * stride;
+            const int2 sg = sgi < a.nseg ? __ldg(&a.seg[sgi]) : make_int2(0, 0);
+            node[j] = sg.x + lane;
+            ok[j] = sgi < a.nseg && sg.x - sg.y * a.b.nx + lane < a.b.nx;
         }
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = ok[j] && (__ldg(a.flags + node[j]) & kActive);
+        #pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j])
+                #pragma unroll
+                for (int i = 0; i < D; ++i) dl[i] += dc[i * a.b.npad + node[j]];
     }
     double d[D];
     #pragma unroll

@@ -34,6 +34,12 @@ template <int D> struct TmaLayout {
     // element offset of lane 0's source inside the box row
     __device__ static constexpr int lane0(int q) { return q == 0 ? 3 : (q == 1 ? 5 : 0); }
     static constexpr int block_bytes(int warps) { return warps * warp_bytes + warps * 8; }
+    // pipeline stage: population slots, then u* (D x 32 floats), flags (32 bytes), header (segment)
+    static constexpr int us_off = warp_bytes;
+    static constexpr int fl_off = us_off + ((D * 32 * 4 + 127) / 128) * 128;
+    static constexpr int hdr_off = fl_off + 128;
+    static constexpr int stage_bytes = hdr_off + 128;
+    static constexpr int stage_tx = tx_bytes + D * 32 * 4 + 32;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -138,7 +144,7 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
     }
     if (!cut) return;
     const float *rec0 = a.lrec + (long long)__ldg(a.lstart + node) * LREC;
-    #pragma unroll
+    #pragma unroll 1
     for (int q = 0; q < Q; ++q) {
         const int qo = q ^ 1;
         if ((cut >> qo) & 1) {
@@ -146,7 +152,7 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
             const float eta = rec[0];
             const bool neu = rec[1] != 0.0f;
             const bool up = !((cut >> q) & 1);
-            #pragma unroll
+            #pragma unroll 4
             for (int k = 0; k < K; ++k) {
                 const float Dk = ((k < D) == neu) ? 1.0f : -1.0f;
                 const float S = rec[2 + k];
@@ -166,19 +172,29 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
 }
 
 struct TmaMaps {
-    CUtensorMap wide, narrow;
+    CUtensorMap wide, narrow;  // population planes of the source buffer: (40, K) and (32, K) boxes
+    CUtensorMap ustar;         // u* planes: (32, D) boxes
+    CUtensorMap flags;         // flag bytes as (nx, ny*nz): (32, 1) boxes
 };
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// issue the Q bulk copies of segment sg into slots wsm (lane 0 only)
-template <int D>
+// issue the bulk copies of segment sg into stage wsm (lane 0 only): Q population boxes, and with
+// `with_meta` the segment's u* box and flag bytes plus a header holding sg
+template <int D, bool with_meta = false>
 __device__ __forceinline__ void tma_issue(const Box &b, const TmaMaps &maps, char *wsm, uint64_t *bar, int2 sg) {
     using L = TmaLayout<D>;
     constexpr int K = L::K, Q = L::Q;
     const int y = sg.y % b.ny, z = sg.y / b.ny, x0 = sg.x - sg.y * b.nx;
     fence_proxy_async_smem();  // generic-proxy writes to these slots (closure) precede the async copies
-    mbar_arrive_expect_tx(bar, L::tx_bytes);
+    if constexpr (with_meta) {
+        *reinterpret_cast<int2 *>(wsm + L::hdr_off) = sg;  // published by the arrive's release
+        mbar_arrive_expect_tx(bar, L::stage_tx);
+        tma_load_2d(wsm + L::us_off, &maps.ustar, bar, sg.x, 0);
+        tma_load_2d(wsm + L::fl_off, &maps.flags, bar, x0, sg.y);
+    } else {
+        mbar_arrive_expect_tx(bar, L::tx_bytes);
+    }
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int A = q >> 1, s = (q & 1) ? -1 : 1;  // pull source of direction q is m - s e_A
@@ -292,7 +308,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const St
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, b = blockIdx.x;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * L::warp_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * L::stage_bytes);
     uint64_t *empty = full + stages;
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const St
                 const int2 sg = make_int2(__shfl_sync(0xffffffffu, sgl.x, k), __shfl_sync(0xffffffffu, sgl.y, k));
                 if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (use - 1) & 1));
                 if (!ok) break;
-                if (lane == 0) tma_issue<D>(a.b, maps, smem + (size_t)s * L::warp_bytes, &full[s], sg);
+                if (lane == 0) tma_issue<D, true>(a.b, maps, smem + (size_t)s * L::stage_bytes, &full[s], sg);
                 __syncwarp();
             }
         }
@@ -333,19 +349,20 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const St
     // ---- consumers ----
     for (int t = warp - 1; t < nlocal; t += kPipeConsumers) {
         const int s = t % stages, use = t / stages;
-        char *const cur = smem + (size_t)s * L::warp_bytes;
-        const int2 sg = __ldg(&a.seg[b + (long long)G * t]);
-        const int x = sg.x - sg.y * a.b.nx + lane;
-        const int node = sg.x + lane;
-        const uint8_t fl = x < a.b.nx ? __ldg(a.flags + node) : (uint8_t)0;
-        const bool act = fl & kActive;
-        float us[D];
-        #pragma unroll
-        for (int d = 0; d < D; ++d) us[d] = act ? a.ustar[d * a.b.npad + node] : 0.0f;
+        char *const cur = smem + (size_t)s * L::stage_bytes;
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], use & 1))) {
             if (lane == 0) set_status(a.status, kStTimeout);
             return;
         }
+        // segment, flags and u* come with the stage: no global load on the interior path
+        const int2 sg = *reinterpret_cast<const int2 *>(cur + L::hdr_off);
+        const int x = sg.x - sg.y * a.b.nx + lane;
+        const int node = sg.x + lane;
+        const uint8_t fl = x < a.b.nx ? reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane] : (uint8_t)0;
+        const bool act = fl & kActive;
+        float us[D];
+        #pragma unroll
+        for (int d = 0; d < D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
         if (act) {
             tma_closure<D>(a, cur, node, x, lane, fl & kCutMask);
             collide_staged<D>(a, cur, node, lane, fl, us);

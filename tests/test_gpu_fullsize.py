@@ -1,0 +1,77 @@
+"""Full-size checks of the 3D FP32 shell workload (256^3 box, 5.84 M active nodes, 299 448
+Neumann links) in the launch configuration the benchmark times (TMA-staged pipeline kernel,
+per-link sources, projection every 20 steps).
+
+1. Against the FP64 oracle on the whole box for the first steps (a projection step and a
+   regular step) from a smooth, non-trivial initial state.
+2. A property that holds at any size and any step count: the shell problem is invariant under
+   the reflections X_A -> -X_A of the centred box, so v_A is odd and the other velocity
+   components even in X_A, to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_20646_b300 import inputs as I
+from parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_20646_b300 import build
+    build.build()
+
+
+def _smooth_initial(p, amp=0.02):
+    """Radially symmetric-free smooth perturbation: v0 and F0 - I from low Fourier modes."""
+    X = p.coords()
+    rng = np.random.default_rng(2606)
+    for i in range(3):
+        k = rng.integers(1, 3, size=3)
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        p.v0[i] = amp * np.sin(np.pi * k[0] * X[0] + ph[0]) * np.cos(np.pi * k[1] * X[1] + ph[1]) * \
+            np.cos(np.pi * k[2] * X[2] + ph[2])
+    for m in range(9):
+        k = rng.integers(1, 3, size=3)
+        p.F0[m] += 0.5 * amp * np.cos(np.pi * k[0] * X[0]) * np.sin(np.pi * k[1] * X[1] + 0.3 * m) * \
+            np.cos(np.pi * k[2] * X[2])
+    return p
+
+
+def test_shell_256_matches_oracle_first_steps():
+    import oracle
+    from paper_2606_20646_b300 import lbm
+    p = _smooth_initial(I.shell_3d(256))
+    steps = 2
+    sim = lbm.Simulation(p, precision="fp32")
+    assert sim.info()["n_active"] == 5841344
+    sim.set_initial().step(steps)
+    g = [t.cpu().numpy() for t in sim.fields()]
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
+    o = oracle.Oracle(p).set_initial()
+    o.step(steps)
+    r = o.fields()
+    mask = o.active_mask()
+    del o
+    assert rel_l2(g[0], r[0], mask) < 1e-5
+    assert rel_l2(g[1], r[1], mask) < 1e-5
+
+
+def test_shell_256_reflection_symmetry():
+    from paper_2606_20646_b300 import lbm
+    p = I.shell_3d(256)
+    sim = lbm.Simulation(p, precision="fp32")
+    sim.set_initial().step(200)                 # 10 projection steps, mid-ramp
+    v, F, u = [t.cpu().numpy() for t in sim.fields()]
+    assert sim.sync(raise_on_status=False) == 0
+    scale = np.abs(v).max()
+    assert scale > 0
+    for A in range(3):
+        axis = 2 - A                             # arrays are (z, y, x)
+        for i in range(3):
+            mirror = np.flip(v[i], axis=axis)
+            sign = -1.0 if i == A else 1.0
+            err = np.abs(v[i] - sign * mirror).max()
+            assert err < 1e-4 * scale, (A, i, err, scale)
