@@ -186,7 +186,9 @@ __device__ __forceinline__ void tma_issue(const Box &b, const TmaMaps &maps, cha
     using L = TmaLayout<D>;
     constexpr int K = L::K, Q = L::Q;
     const int y = sg.y % b.ny, z = sg.y / b.ny, x0 = sg.x - sg.y * b.nx;
-    fence_proxy_async_smem();  // generic-proxy writes to these slots (closure) precede the async copies
+    // in the pipeline the consumer that released this stage fenced its generic-proxy writes before
+    // arriving on the empty barrier; the warp-local double-buffered path fences here
+    if constexpr (!with_meta) fence_proxy_async_smem();
     if constexpr (with_meta) {
         *reinterpret_cast<int2 *>(wsm + L::hdr_off) = sg;  // published by the arrive's release
         mbar_arrive_expect_tx(bar, L::stage_tx);
@@ -320,22 +322,20 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const St
     __syncthreads();
     const int nlocal = a.nseg > b ? (a.nseg - b + G - 1) / G : 0;  // segments of this CTA
     if (warp == 0) {
-        // ---- producer ----
+        // ---- producer: each lane issues one segment of a batch of `batch` (<= stages) segments ----
+        const int batch = stages < 16 ? stages : 16;
         bool ok = true;
-        for (int t0 = 0; t0 < nlocal && ok; t0 += 32) {
-            // segment coordinates of the next 32 local segments, one round trip
-            const int tl = t0 + lane;
-            const int2 sgl = tl < nlocal ? __ldg(&a.seg[b + (long long)G * tl]) : make_int2(0, 0);
-            const int n = min(32, nlocal - t0);
-            for (int k = 0; k < n; ++k) {
-                const int t = t0 + k;
-                const int s = t % stages, use = t / stages;
-                const int2 sg = make_int2(__shfl_sync(0xffffffffu, sgl.x, k), __shfl_sync(0xffffffffu, sgl.y, k));
-                if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], (use - 1) & 1));
-                if (!ok) break;
-                if (lane == 0) tma_issue<D, true>(a.b, maps, smem + (size_t)s * L::stage_bytes, &full[s], sg);
-                __syncwarp();
-            }
+        for (int t0 = 0; t0 < nlocal && ok; t0 += batch) {
+            const int t = t0 + lane;
+            const bool mine = lane < batch && t < nlocal;
+            const int s = t % stages, use = t / stages;
+            const int2 sg = mine ? __ldg(&a.seg[b + (long long)G * t]) : make_int2(0, 0);
+            bool w = true;
+            if (mine && use > 0) w = mbar_wait_bounded(&empty[s], (use - 1) & 1);  // segment t - stages released
+            ok = __all_sync(0xffffffffu, w);
+            if (!ok) break;
+            if (mine) tma_issue<D, true>(a.b, maps, smem + (size_t)s * L::stage_bytes, &full[s], sg);
+            __syncwarp();
         }
         if (!ok && lane == 0) set_status(a.status, kStTimeout);
         // before the CTA can retire, every issued stage must have landed
