@@ -327,8 +327,9 @@ template <typename real, int D> struct Impl {
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
                 const int per_stage = TmaLayout<D>::stage_bytes + 16;
-                h->tma_stages = std::min(32, (smem_optin - 1024) / per_stage);
-                const int bytes = h->tma_stages * per_stage;
+                const int table = kPipeProducers * 32 * (int)sizeof(SegStarts);
+                h->tma_stages = std::min(32, (smem_optin - 1024 - table) / per_stage);
+                const int bytes = h->tma_stages * per_stage + table;
                 ok = h->tma_stages >= 4 &&
                      cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
                          cudaSuccess &&

@@ -19,7 +19,7 @@
 namespace tlv {
 
 constexpr int kStTimeout = 128;        // device status bit: a TMA wait ran out
-constexpr int kTmaSpin = 1 << 22;      // try_wait polls before giving up
+constexpr int kTmaSpin = 1 << 20;      // try_wait polls before giving up
 constexpr int kTmaWide = 40, kTmaNarrow = 32;
 
 template <int D> struct TmaLayout {
@@ -295,23 +295,63 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kPipeConsumers = 14;                    // consumer warps per CTA
-constexpr int kPipeThreads = 32 * (1 + kPipeConsumers);
+constexpr int kPipeProducers = 2;                     // producer warps per CTA
+constexpr int kPipeConsumers = 13;                    // consumer warps per CTA
+constexpr int kPipeThreads = 32 * (kPipeProducers + kPipeConsumers);
 
-// K3 with TMA staging (FP32), warp-specialised and persistent: one CTA per SM; warp 0 is the
-// producer, which streams the bulk copies of the CTA's segments (b, b + G, b + 2G, ...) into a
-// ring of `stages` shared-memory stages; consumer warp c computes the CTA's segments
-// c-1, c-1+C, ... .  Stage t % stages has a full barrier (completed by the copies' bytes) and
-// an empty barrier (arrived by the consumer when it is done with the stage).
+// TMA start coordinates of a segment: element x of every population box, then the flag box
+struct SegStarts {
+    int2 sg;
+    int x0, pad;
+    int start[6];
+};
+
+template <int D> __device__ __forceinline__ SegStarts seg_starts(const Box &b, int2 sg) {
+    SegStarts r;
+    r.sg = sg;
+    const int y = sg.y % b.ny, z = sg.y / b.ny;
+    r.x0 = sg.x - sg.y * b.nx;
+    r.pad = 0;
+    #pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int A = q >> 1, s = (q & 1) ? -1 : 1;  // pull source of direction q is m - s e_A
+        int start = 0;
+        if (q < 2 * D) {
+            if (A == 0) {
+                start = sg.x - 4;
+            } else if (A == 1) {
+                int yy = y - s;
+                if (b.per[1]) yy = yy < 0 ? yy + b.ny : (yy >= b.ny ? yy - b.ny : yy);
+                start = (z * b.ny + yy) * b.nx + r.x0;
+            } else {
+                int zz = z - s;
+                if (b.per[2]) zz = zz < 0 ? zz + b.nz : (zz >= b.nz ? zz - b.nz : zz);
+                start = (zz * b.ny + y) * b.nx + r.x0;
+            }
+        }
+        r.start[q] = start;
+    }
+    return r;
+}
+
+// K3 with TMA staging (FP32), warp-specialised and persistent: one CTA per SM.  Warps
+// 0..kPipeProducers-1 are producers that stream the bulk copies of the CTA's segments
+// (b, b + G, b + 2G, ...; producer p takes local segments t = p mod kPipeProducers) into a ring of
+// `stages` shared-memory stages; consumer warp c computes local segments c, c + C, ... .  Stage
+// t % stages has a full barrier (completed by the copies' bytes) and an empty barrier (arrived by
+// the consumer when done with the stage).  Each producer batch of 32 segments has its start
+// coordinates computed by all lanes into a shared table; lane 0 alone waits and issues.
 template <int D>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const StepArgs<float> a,
                                                                      const __grid_constant__ TmaMaps maps, int stages) {
     using L = TmaLayout<D>;
+    constexpr int K = L::K, Q = L::Q;
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, b = blockIdx.x;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * L::stage_bytes);
     uint64_t *empty = full + stages;
+    SegStarts *table = reinterpret_cast<SegStarts *>(empty + stages);  // [kPipeProducers][32]
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
@@ -321,33 +361,46 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_stream_collide_tma(const St
     }
     __syncthreads();
     const int nlocal = a.nseg > b ? (a.nseg - b + G - 1) / G : 0;  // segments of this CTA
-    if (warp == 0) {
-        // ---- producer: each lane issues one segment of a batch of `batch` (<= stages) segments ----
-        const int batch = stages < 16 ? stages : 16;
+    if (warp < kPipeProducers) {
+        // ---- producer p: local segments p, p + P, p + 2P, ... in batches of 32 ----
+        SegStarts *tab = table + warp * 32;
         bool ok = true;
-        for (int t0 = 0; t0 < nlocal && ok; t0 += batch) {
-            const int t = t0 + lane;
-            const bool mine = lane < batch && t < nlocal;
-            const int s = t % stages, use = t / stages;
-            const int2 sg = mine ? __ldg(&a.seg[b + (long long)G * t]) : make_int2(0, 0);
-            bool w = true;
-            if (mine && use > 0) w = mbar_wait_bounded(&empty[s], (use - 1) & 1);  // segment t - stages released
-            ok = __all_sync(0xffffffffu, w);
-            if (!ok) break;
-            if (mine) tma_issue<D, true>(a.b, maps, smem + (size_t)s * L::stage_bytes, &full[s], sg);
+        for (int k0 = 0; ok; k0 += 32) {
+            const int tfirst = warp + kPipeProducers * k0;
+            if (tfirst >= nlocal) break;
+            const int t = tfirst + kPipeProducers * lane;
+            if (t < nlocal) tab[lane] = seg_starts<D>(a.b, __ldg(&a.seg[b + (long long)G * t]));
             __syncwarp();
+            if (lane == 0) {
+                for (int k = 0; k < 32; ++k) {
+                    const int tk = tfirst + kPipeProducers * k;
+                    if (tk >= nlocal) break;
+                    const int s = tk % stages, use = tk / stages;
+                    if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1)) { ok = false; break; }
+                    const SegStarts st = tab[k];
+                    char *wsm = smem + (size_t)s * L::stage_bytes;
+                    *reinterpret_cast<int2 *>(wsm + L::hdr_off) = st.sg;  // published by the arrive's release
+                    mbar_arrive_expect_tx(&full[s], L::stage_tx);
+                    tma_load_2d(wsm + L::us_off, &maps.ustar, &full[s], st.sg.x, 0);
+                    tma_load_2d(wsm + L::fl_off, &maps.flags, &full[s], st.x0, st.sg.y);
+                    #pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        tma_load_2d(wsm + L::slot(q), (q >> 1) == 0 ? &maps.wide : &maps.narrow, &full[s], st.start[q],
+                                    q * K);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();  // the table is rewritten by the next batch
         }
         if (!ok && lane == 0) set_status(a.status, kStTimeout);
-        // before the CTA can retire, every issued stage must have landed
-        const int last = nlocal < stages ? nlocal : stages;
-        for (int k = 0; k < last; ++k) {
-            const int t = nlocal - 1 - k;
-            mbar_wait_bounded(&full[t % stages], (t / stages) & 1);
-        }
+        // before the CTA can retire, every copy this producer issued must have landed
+        if (lane == 0)
+            for (int t = warp; t < nlocal; t += kPipeProducers)
+                if (t >= nlocal - stages) mbar_wait_bounded(&full[t % stages], (t / stages) & 1);
         return;
     }
     // ---- consumers ----
-    for (int t = warp - 1; t < nlocal; t += kPipeConsumers) {
+    for (int t = warp - kPipeProducers; t < nlocal; t += kPipeConsumers) {
         const int s = t % stages, use = t / stages;
         char *const cur = smem + (size_t)s * L::stage_bytes;
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], use & 1))) {
