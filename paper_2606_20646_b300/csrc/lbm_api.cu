@@ -47,8 +47,9 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
     h->fA = c.take<char>((size_t)Q * K * np * rs);
     h->fB = c.take<char>((size_t)Q * K * np * rs);
-    h->ustar = c.take<char>((size_t)D * np * rs);
-    h->un = c.take<char>((size_t)D * np * rs);
+    // displacement accumulators: one FP64 plane per component, or a (hi, lo) pair of FP32 planes
+    h->ustar = c.take<char>((size_t)D * np * 8);
+    h->un = c.take<char>((size_t)D * np * 8);
     h->dmask = c.take<uint8_t>(np);
     h->l_node = c.take<int>(nc);
     h->l_q = c.take<int>(nc);
@@ -59,7 +60,8 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     h->l_Nb = c.take<double>(3 * nc);
     h->l_tan = c.take<double>(6 * nc);
     h->l_h = c.take<char>((size_t)3 * nc * rs);
-    h->l_rec = c.take<char>((size_t)(K + 2) * nc * rs);
+    h->l_rec = c.take<char>((size_t)K * nc * rs);
+    h->l_fo = c.take<char>((size_t)2 * K * nc * rs);
     if (h->has_neumann_bc) {
         h->l_sidx = c.take<int>((size_t)kLsqCap * nc);
         h->l_w = c.take<char>((size_t)2 * kLsqCap * nc * rs);

@@ -73,7 +73,7 @@ struct lbm_handle {
     uint8_t *dmask = nullptr;
     int *l_node = nullptr, *l_q = nullptr, *l_bc = nullptr, *l_ns = nullptr, *l_sidx = nullptr;
     double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
-    void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr;
+    void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr, *l_fo = nullptr;
     double *u0 = nullptr, *u1 = nullptr, *partial = nullptr, *mean = nullptr, *staging = nullptr;
     void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
     long long n_neu = 0, n_dir = 0, lsq_entries = 0;
@@ -84,8 +84,7 @@ struct lbm_handle {
     long long launches = 0;
     // TMA staging of the FP32 gather: tensor maps of both population buffers
     bool tma_ok = false;
-    unsigned tma_grid = 0;  // persistent grid of the fused kernel: SMs x resident blocks
-    int tma_smem = 0, tma_stages = 0;
+    int tma_smem = 0;  // dynamic shared memory of the fused kernel's blocks
     void *tma_buf[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
     // timing
@@ -191,14 +190,15 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return encode;
 }
 
-// u* planes (npad, D) with (32, D) boxes, and the flag bytes viewed as (nx, ny*nz) with (32, 1) boxes
+// u* planes (npad, 2D: hi then lo) with (32, 2D) boxes, and the flag bytes viewed as (nx, ny*nz) with
+// (32, 1) boxes
 inline bool encode_meta_maps(void *ustar, long long npad, int D, void *flags, int nx, long long rows, TmaMaps *out) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return false;
     const cuuint32_t es[2] = {1, 1};
-    const cuuint64_t udims[2] = {(cuuint64_t)npad, (cuuint64_t)D};
+    const cuuint64_t udims[2] = {(cuuint64_t)npad, (cuuint64_t)(2 * D)};
     const cuuint64_t ustr[1] = {(cuuint64_t)npad * 4};
-    const cuuint32_t ubox[2] = {32, (cuuint32_t)D};
+    const cuuint32_t ubox[2] = {32, (cuuint32_t)(2 * D)};
     const cuuint64_t fdims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
     const cuuint64_t fstr[1] = {(cuuint64_t)nx};
     const cuuint32_t fbox[2] = {32, 1};
@@ -242,7 +242,7 @@ inline bool encode_population_maps(void *base, long long npad, int planes, int K
 // =============================================================================================
 
 template <typename real, int D> struct Impl {
-    static constexpr int K = D + D * D, Q = 2 * D, LREC = K + 2;
+    static constexpr int K = D + D * D, Q = 2 * D;
 
     static LinkGeom<real> links(lbm_handle *h) {
         LinkGeom<real> L;
@@ -258,6 +258,7 @@ template <typename real, int D> struct Impl {
         L.sidx = h->l_sidx;
         L.w = static_cast<real *>(h->l_w);
         L.rec = static_cast<real *>(h->l_rec);
+        L.fo = static_cast<real *>(h->l_fo);
         L.ncut = h->n_cut;
         return L;
     }
@@ -274,6 +275,7 @@ template <typename real, int D> struct Impl {
         a.ustar = static_cast<real *>(h->ustar);
         a.un = static_cast<real *>(h->un);
         a.lrec = static_cast<const real *>(h->l_rec);
+        a.lfo = static_cast<real *>(h->l_fo);
         a.vst = static_cast<real *>(h->vst);
         a.Gst = static_cast<real *>(h->Gst);
         a.u0 = h->u0;
@@ -322,28 +324,13 @@ template <typename real, int D> struct Impl {
                                       (long long)h->box.ny * h->box.nz, &h->tma_maps[j]);
             }
             if (ok) {
-                // stages of the producer/consumer ring: as many as fit next to the barriers
-                int dev = 0, smem_optin = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-                const int per_stage = TmaLayout<D>::stage_bytes + 16;
-                const int table = kPipeProducers * 32 * (int)sizeof(SegStarts);
-                h->tma_stages = std::min(32, (smem_optin - 1024 - table) / per_stage);
-                const int bytes = h->tma_stages * per_stage + table;
-                ok = h->tma_stages >= 4 &&
-                     cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-                         cudaSuccess &&
+                h->tma_smem = kTmaWarps * (TmaLayout<D>::stage_bytes + 8);
+                ok = cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          h->tma_smem) == cudaSuccess &&
                      cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess &&
                      cudaFuncSetAttribute(k_gather_moments_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess;
-                int sms = 0, per_sm = 0;
-                ok = ok && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_tma<D>, kPipeThreads,
-                                                                   bytes) == cudaSuccess &&
-                     per_sm > 0;
-                h->tma_grid = (unsigned)(sms * per_sm);
-                h->tma_smem = bytes;
             }
             cudaGetLastError();
             h->tma_ok = ok;
@@ -378,6 +365,9 @@ template <typename real, int D> struct Impl {
         if (h->n_cut == 0) return LBM_OK;
         CutArgs<real> a;
         a.L = links(h);
+        a.b = h->box;
+        a.flags = h->flags;
+        a.fstar = static_cast<const real *>(h->fB);  // written by this step's collision, read by the next gather
         a.bcs = h->dbcs;
         a.un = static_cast<const real *>(h->un);
         a.npad = h->box.npad;
@@ -447,8 +437,8 @@ template <typename real, int D> struct Impl {
                 if (h->phase == 0) k_stream_collide<real, D, 0><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
                     if (h->tma_ok)
-                        k_stream_collide_tma<D><<<h->tma_grid, kPipeThreads, h->tma_smem, h->stream>>>(
-                            a, *maps_of(h, h->fA), h->tma_stages);
+                        k_stream_collide_tma<D><<<grid_for(h->nseg, kTmaWarps), 32 * kTmaWarps, h->tma_smem, h->stream>>>(
+                            a, *maps_of(h, h->fA));
                     else
                         k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
                 } else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);

@@ -25,6 +25,43 @@ template <typename real, int D> __device__ __forceinline__ real div2D(real x) {
     else return x / real(2 * D);
 }
 
+// Displacement accumulators u* and u^n.  The FP64 form keeps one FP64 plane per component.  The
+// FP32 form keeps each component as an unevaluated pair of FP32 planes, hi (planes 0..D-1) and lo
+// (planes D..2D-1) with |lo| <= ulp(hi)/2, so that u* = hi + lo carries about 48 significant bits:
+// u* gains dt v every step, and the projection and the LSQ tangent images difference u across one
+// lattice spacing, so one FP32 plane would drop the increments' low bits and, at fine spacings, most
+// of those differences.  Both forms use D * npad * 8 bytes per accumulator.
+template <typename real> constexpr bool kDispPair = sizeof(real) == 4;
+
+// (hi, lo) + d, renormalised: Knuth's TwoSum of hi and d, then Dekker's Fast2Sum of that sum and
+// the gathered low parts (the sum dominates).  Round-to-nearest intrinsics keep the compiler from
+// contracting or reordering the error-free steps.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float d) {
+    const float s = __fadd_rn(hi, d);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(d, bv));
+    const float t = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+template <typename real>
+__device__ __forceinline__ double disp_get(const real *p, long long P, int D, int i, long long node) {
+    if constexpr (kDispPair<real>) return (double)p[i * P + node] + (double)p[(D + i) * P + node];
+    else return p[i * P + node];
+}
+
+template <typename real>
+__device__ __forceinline__ void disp_set(real *p, long long P, int D, int i, long long node, double u) {
+    if constexpr (kDispPair<real>) {
+        const float hi = (float)u;
+        p[i * P + node] = hi;
+        p[(D + i) * P + node] = (float)(u - (double)hi);
+    } else {
+        p[i * P + node] = u;
+    }
+}
+
 struct Box {
     int D, nx, ny, nz;
     int per[3];
@@ -192,7 +229,8 @@ template <typename real> struct LinkGeom {
     int *ns;            // [ncut]
     int *sidx;          // [kLsqCap*ncut], entry j of link l at j*ncut + l
     real *w;            // [2*kLsqCap*ncut], tangent a, entry j at (a*kLsqCap + j)*ncut + l
-    real *rec;          // [ncut*LREC]
+    real *rec;          // [ncut*K] reconstructed incoming populations for the next gather (link-major)
+    real *fo;           // [ncut*2K] f*_c(m) then f*_{c^1}(m) of the link's node after the last collision
     long long ncut;
 };
 
@@ -245,7 +283,6 @@ template <typename real, int D>
 __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint8_t *flags, uint8_t *dmask,
                              const int *__restrict__ lstart, const ShapeD *__restrict__ shapes, int nshapes,
                              const BCD *__restrict__ bcs, int nbc, LinkGeom<real> L, int *status) {
-    constexpr int K = D + D * D, LREC = K + 2;
     int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (sgi >= nseg) return;
     int2 sg = seg[sgi];
@@ -323,10 +360,6 @@ __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint
             L.tan[6 * l + 3 + a] = t[1][a];
             L.h[3 * l + a] = (real)N[a];
         }
-        real *rec = L.rec + (long long)l * LREC;
-        rec[0] = (real)eta;
-        rec[1] = (real)kind;
-        for (int k = 0; k < K; ++k) rec[2 + k] = 0;
         int ns = 0;
         if (kind == 0) {
             dm |= (uint8_t)(1u << q);
@@ -504,7 +537,7 @@ __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint
         }
         for (int k = 0; k < K; ++k) f[(long long)(q * K + k) * P + node] = (real)fq[k];
     }
-    for (int i = 0; i < D; ++i) ustar[i * P + node] = (real)(u0[i * N + node] - 0.5 * dt * v0[i * N + node]);
+    for (int i = 0; i < D; ++i) disp_set<real>(ustar, P, D, i, node, u0[i * N + node] - 0.5 * dt * v0[i * N + node]);
 }
 
 // =============================================================================================
@@ -521,18 +554,75 @@ template <typename real> struct StepArgs {
     real *fdst;
     real *ustar;
     real *un;
-    const real *lrec;
+    const real *lrec;  // per cut link: reconstructed incoming populations (K), read by the gather
+    real *lfo;         // per cut link: f*_c(m), f*_{c^1}(m) (2K), written by the collision kernels
     real *vst, *Gst;   // projection steps: v^n and G^n = F^n - I (D and D*D planes)
     double *u0;        // projection steps: u^n in FP64
     real dt, c, omega, gamma, mu, lam, bf[3];
     int *status;
 };
 
+// N consecutive values at p (aligned to 16 bytes when N*sizeof(real) is a multiple of 16, else to
+// 8 bytes) as 16- or 8-byte vector loads and stores
+template <int N> __device__ __forceinline__ void vload(const float *p, float *d) {
+    if constexpr (N % 4 == 0) {
+        #pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            d[4 * i] = t.x; d[4 * i + 1] = t.y; d[4 * i + 2] = t.z; d[4 * i + 3] = t.w;
+        }
+    } else {
+        static_assert(N % 2 == 0, "even count");
+        #pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(p) + i);
+            d[2 * i] = t.x; d[2 * i + 1] = t.y;
+        }
+    }
+}
+template <int N> __device__ __forceinline__ void vload(const double *p, double *d) {
+    static_assert(N % 2 == 0, "even count");
+    #pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        d[2 * i] = t.x; d[2 * i + 1] = t.y;
+    }
+}
+template <int N> __device__ __forceinline__ void vstore(float *p, const float *d) {
+    if constexpr (N % 4 == 0) {
+        #pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+    } else {
+        static_assert(N % 2 == 0, "even count");
+        #pragma unroll
+        for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2 *>(p)[i] = make_float2(d[2 * i], d[2 * i + 1]);
+    }
+}
+template <int N> __device__ __forceinline__ void vstore(double *p, const double *d) {
+    static_assert(N % 2 == 0, "even count");
+    #pragma unroll
+    for (int i = 0; i < N / 2; ++i) reinterpret_cast<double2 *>(p)[i] = make_double2(d[2 * i], d[2 * i + 1]);
+}
+
+// link of node m (first link l0 = lstart[m]) whose cut bit is c: links are sorted by node, then bit
+__device__ __forceinline__ long long link_of(long long l0, unsigned cut, int c) {
+    return l0 + __popc(cut & ((1u << c) - 1u));
+}
+
+// After computing the post-collision values out[0..K) of direction q at a node with cut bits `cut`,
+// keep the ones its cut links need: f*_c(m) for a cut direction c = q, f*_{c^1}(m) for c = q^1.
+template <typename real, int K>
+__device__ __forceinline__ void keep_link_values(real *lfo, long long l0, unsigned cut, int q, const real *out) {
+    if ((cut >> q) & 1) vstore<K>(lfo + link_of(l0, cut, q) * (2 * K), out);
+    if ((cut >> (q ^ 1)) & 1) vstore<K>(lfo + link_of(l0, cut, q ^ 1) * (2 * K) + K, out);
+}
+
 // MODE 0: state is pre-collision f^0 (first step, no streaming); MODE 1: state is f*^{n-1}
 template <typename real, int D, int MODE>
 __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x, int y, int z, unsigned cut,
                                        real (&f)[2 * D * (D + D * D)]) {
-    constexpr int K = D + D * D, Q = 2 * D, LREC = K + 2;
+    constexpr int K = D + D * D, Q = 2 * D;
     const long long P = a.b.npad;
     const real *__restrict__ fs = a.fsrc;
     if constexpr (MODE == 0) {
@@ -551,32 +641,11 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
         }
     }
     if (cut) {
-        const real *rec0 = a.lrec + (long long)__ldg(a.lstart + node) * LREC;
+        // the populations a cut link leaves unknown arrive reconstructed by the link kernel
+        const long long l0 = __ldg(a.lstart + node);
         #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int qo = q ^ 1;  // outgoing direction of the cut link; q is the missing incoming one
-            if ((cut >> qo) & 1) {
-                const real *rec = rec0 + __popc(cut & ((1u << qo) - 1u)) * LREC;
-                const real eta = rec[0];
-                const bool neu = rec[1] != real(0);
-                const bool up = !((cut >> q) & 1);  // m^- = m - e_{qo} = m + e_q active
-                #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const real Dk = ((k < D) == neu) ? real(1) : real(-1);  // D_N = diag(I,-I), D_D = diag(-I,I)
-                    const real S = rec[2 + k];
-                    const real fo = __ldg(fs + (long long)(qo * K + k) * P + node);  // f*_{-d}(X_f)
-                    const real fi = __ldg(fs + (long long)(q * K + k) * P + node);   // f*_{d}(X_f)
-                    real r;
-                    if (eta >= real(0.5)) {
-                        r = (Dk * fo + S) / (real(2) * eta) + (real(1) - real(1) / (real(2) * eta)) * fi;
-                    } else {
-                        const real fu = up ? f[qo * K + k] : fo;  // f*_{-d}(X_f - dx e)
-                        r = Dk * (real(2) * eta * fo + (real(1) - real(2) * eta) * fu) + S;
-                    }
-                    f[q * K + k] = r;
-                }
-            }
-        }
+        for (int q = 0; q < Q; ++q)
+            if ((cut >> (q ^ 1)) & 1) vload<K>(a.lrec + link_of(l0, cut, q ^ 1) * K, &f[q * K]);
     }
     }
 }
@@ -624,9 +693,9 @@ __device__ __forceinline__ void equilibrium(const real v[D], const real X[D * D]
 }
 
 template <typename real, int D>
-__device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node, real (&f)[2 * D * (D + D * D)],
-                                              const real v[D], const real G[D * D], const real F[D * D],
-                                              const real Pk[D * D]) {
+__device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node, unsigned cut,
+                                              real (&f)[2 * D * (D + D * D)], const real v[D], const real G[D * D],
+                                              const real F[D * D], const real Pk[D * D]) {
     constexpr int K = D + D * D, Q = 2 * D;
     const long long P = a.b.npad;
     const real Dc = real(D) / a.c;
@@ -635,15 +704,17 @@ __device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node,
     real B[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    const long long l0 = cut ? __ldg(a.lstart + node) : 0;
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int A = q >> 1;
         const real s = (q & 1) ? real(-1) : real(1);
+        real out[K];
         #pragma unroll
         for (int i = 0; i < D; ++i) {
             const real feq = div2D<real, D>(v[i] - s * Dc * Pk[i * D + A]);
             const real fv = f[q * K + i];
-            a.fdst[(long long)(q * K + i) * P + node] = fv + a.omega * (feq - fv) + src * B[i];
+            out[i] = fv + a.omega * (feq - fv) + src * B[i];
         }
         #pragma unroll
         for (int i = 0; i < D; ++i)
@@ -653,8 +724,11 @@ __device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node,
                 const real X = kShifted<real> ? G[i * D + Bc] : F[i * D + Bc];
                 const real feq = (A == Bc) ? div2D<real, D>(X - s * Dc * v[i]) : div2D<real, D>(X);
                 const real fv = f[q * K + k];
-                a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv);
+                out[k] = fv + a.omega * (feq - fv);
             }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) a.fdst[(long long)(q * K + k) * P + node] = out[k];
+        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
     }
 }
 
@@ -698,11 +772,21 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     const long long P = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const real un = a.ustar[i * P + node] + real(0.5) * a.dt * v[i];  // u^n (Eq. u-recovery-general)
-        if (fl & kNeedU) a.un[i * P + node] = un;
-        a.ustar[i * P + node] = un + real(0.5) * a.dt * v[i];              // u*^{n+1}
+        if constexpr (kDispPair<real>) {
+            float hi = a.ustar[i * P + node], lo = a.ustar[(D + i) * P + node];
+            const float d = real(0.5) * a.dt * v[i];
+            df_add(hi, lo, d);  // u^n (Eq. u-recovery-general)
+            if (fl & kNeedU) { a.un[i * P + node] = hi; a.un[(D + i) * P + node] = lo; }
+            df_add(hi, lo, d);  // u*^{n+1}
+            a.ustar[i * P + node] = hi;
+            a.ustar[(D + i) * P + node] = lo;
+        } else {
+            const real un = a.ustar[i * P + node] + real(0.5) * a.dt * v[i];  // u^n (Eq. u-recovery-general)
+            if (fl & kNeedU) a.un[i * P + node] = un;
+            a.ustar[i * P + node] = un + real(0.5) * a.dt * v[i];              // u*^{n+1}
+        }
     }
-    collide_store<real, D>(a, node, f, v, G, F, Pk);
+    collide_store<real, D>(a, node, cut, f, v, G, F, Pk);
 }
 
 // projection steps, part 1: gather + recovery; stores f^n (pre-collision), v^n, G^n, u^n (FP64)
@@ -729,7 +813,7 @@ __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) 
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         a.vst[i * P + node] = v[i];
-        a.u0[i * P + node] = (double)a.ustar[i * P + node] + 0.5 * (double)a.dt * (double)v[i];
+        a.u0[i * P + node] = disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i];
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = G[k];
@@ -756,7 +840,7 @@ __global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *
     const long long N = a.b.nbox, P = a.b.npad;
     for (int i = 0; i < D; ++i) {
         if (vout) vout[i * N + node] = (double)v[i];
-        if (uout) uout[i * N + node] = (double)a.ustar[i * P + node] + 0.5 * (double)a.dt * (double)v[i];
+        if (uout) uout[i * N + node] = disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i];
     }
     if (Fout)
         for (int i = 0; i < D; ++i)
@@ -771,6 +855,9 @@ __global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *
 
 template <typename real> struct CutArgs {
     LinkGeom<real> L;
+    Box b;
+    const uint8_t *flags;
+    const real *fstar;  // f* after the collision of the step just taken
     const BCD *bcs;
     const real *un;
     long long npad;
@@ -807,7 +894,7 @@ __device__ __forceinline__ bool traction_residual(const real h[D], const real N[
 
 template <typename real, int D>
 __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
-    constexpr int K = D + D * D, LREC = K + 2;
+    constexpr int K = D + D * D;
     const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (l >= a.L.ncut) return;
     const int q = a.L.q[l], A = q >> 1;
@@ -840,9 +927,12 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         // tangent images g_a = t_a + sum_j w_aj (u_j - u_m)  (Eqs. tangent-derivative-2d, tangent-image-3d-lsq)
         const int m = a.L.node[l];
         const long long P = a.npad;
-        real um[D];
+        real um[D], uml[D];
         #pragma unroll
-        for (int i = 0; i < D; ++i) um[i] = a.un[i * P + m];
+        for (int i = 0; i < D; ++i) {
+            um[i] = a.un[i * P + m];
+            uml[i] = kDispPair<real> ? a.un[(D + i) * P + m] : real(0);
+        }
         const int ns = a.L.ns[l];
         if constexpr (!kShifted<real>) {
             // FP64: g = t + sum_j w_j u_j in stencil order, as the oracle sums it
@@ -856,7 +946,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         constexpr int U = 4;
         for (int j0 = 0; j0 < ns; j0 += U) {
             int kk[U];
-            real w[U][D - 1], uu[U][D];
+            real w[U][D - 1], uu[U][D], uul[U][D];
             #pragma unroll
             for (int jj = 0; jj < U; ++jj) {
                 const int j = j0 + jj < ns ? j0 + jj : ns - 1;
@@ -867,14 +957,18 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
             #pragma unroll
             for (int jj = 0; jj < U; ++jj)
                 #pragma unroll
-                for (int i = 0; i < D; ++i) uu[jj][i] = a.un[i * P + kk[jj]];
+                for (int i = 0; i < D; ++i) {
+                    uu[jj][i] = a.un[i * P + kk[jj]];
+                    uul[jj][i] = kDispPair<real> ? a.un[(D + i) * P + kk[jj]] : real(0);
+                }
             #pragma unroll
             for (int jj = 0; jj < U; ++jj) {
                 if (j0 + jj >= ns) break;
                 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation
-                    const real du = kShifted<real> ? uu[jj][i] - um[i] : uu[jj][i];
+                    // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation; the
+                    // difference of the (hi, lo) pairs, hi parts first (exact for nearby values)
+                    const real du = kShifted<real> ? (uu[jj][i] - um[i]) + (uul[jj][i] - uml[i]) : uu[jj][i];
                     #pragma unroll
                     for (int al = 0; al < D - 1; ++al) g[al][i] += w[jj][al] * du;
                 }
@@ -982,9 +1076,36 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
                                                   : Fb[i * D + B] / real(D);
         }
     }
-    real *rec = a.L.rec + l * LREC;
-    #pragma unroll
-    for (int k = 0; k < K; ++k) rec[2 + k] = S[k];
+    // Interpolated bounce-back of the incoming population f_{c^1}(m) for the next gather
+    // (Eqs. bfl-curved-far, bfl-curved-near), from the node's post-collision values f*_c(m),
+    // f*_{c^1}(m) and, for eta < 1/2, f*_c of the upstream node m + e_{c^1} (m itself when that
+    // node is inactive); D_b = diag(-I, I) for Dirichlet, diag(I, -I) for Neumann links.
+    {
+        const int m = a.L.node[l];
+        real fo[K], fi[K], R[K];
+        vload<K>(a.L.fo + l * (2 * K), fo);
+        vload<K>(a.L.fo + l * (2 * K) + K, fi);
+        const real eta = (real)a.L.eta[l];
+        const bool neu = bc.kind != 0;
+        const bool up = !((__ldg(a.flags + m) >> (q ^ 1)) & 1);
+        int mup = m;
+        if (up && !(eta >= real(0.5))) {
+            int x, y, z;
+            node_xyz(a.b, m, x, y, z);
+            mup = nbr(a.b, m, x, y, z, q ^ 1);
+        }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const real Dk = ((k < D) == neu) ? real(1) : real(-1);
+            if (eta >= real(0.5)) {
+                R[k] = (Dk * fo[k] + S[k]) / (real(2) * eta) + (real(1) - real(1) / (real(2) * eta)) * fi[k];
+            } else {
+                const real fu = up ? a.fstar[(long long)(q * K + k) * a.b.npad + mup] : fo[k];
+                R[k] = Dk * (real(2) * eta * fo[k] + (real(1) - real(2) * eta) * fu) + S[k];
+            }
+        }
+        vstore<K>(a.L.rec + l * K, R);
+    }
 }
 
 // =============================================================================================
@@ -1281,10 +1402,12 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     real B[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    const long long l0 = cut ? __ldg(a.lstart + node) : 0;
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int A = q >> 1;
         const real s = (q & 1) ? real(-1) : real(1);
+        real out[K];
         #pragma unroll
         for (int k = 0; k < K; ++k) {
             real fv = a.fdst[(long long)(q * K + k) * P + node];
@@ -1305,14 +1428,18 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
                 else fv = fv + (feq - ((A == Bc) ? div2D<real, D>(Xo - vs) : div2D<real, D>(Xo)));
             }
             // BGK collision with source (Eq. collision-general-d)
-            a.fdst[(long long)(q * K + k) * P + node] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : real(0));
+            out[k] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : real(0));
         }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) a.fdst[(long long)(q * K + k) * P + node] = out[k];
+        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
         u1[i * P + node] = un;
-        a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
+        if constexpr (kDispPair<real>) disp_set<real>(a.ustar, P, D, i, node, un + (double)(real(0.5) * a.dt * v[i]));
+        else a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = Gr[k];
@@ -1326,9 +1453,15 @@ __global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, cons
     const long long P = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const real un = (real)(u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]));
-        a.un[i * P + node] = un;
-        a.ustar[i * P + node] = un + real(0.5) * a.dt * a.vst[i * P + node];
+        if constexpr (kDispPair<real>) {
+            const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
+            disp_set<real>(a.un, P, D, i, node, un);
+            disp_set<real>(a.ustar, P, D, i, node, un + (double)(real(0.5) * a.dt * a.vst[i * P + node]));
+        } else {
+            const real un = (real)(u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]));
+            a.un[i * P + node] = un;
+            a.ustar[i * P + node] = un + real(0.5) * a.dt * a.vst[i * P + node];
+        }
     }
 }
 

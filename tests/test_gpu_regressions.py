@@ -1,0 +1,122 @@
+"""The paper's exact-solution benchmarks at the paper's lattice sizes, on the CUDA path.
+
+Both prescribe affine Dirichlet data with an affine exact motion.  The annulus (Sec. 4.2,
+omega = 2) is kept exactly by the cut-link closure: the FP64 form reproduces it at round-off at
+every size, the FP32 form below the errors printed for N = 384 (Table tab:2d-curved-summary).
+The rotated ellipsoid (Sec. 5.1, omega = 1.8) is not exact: the FP64 form must refine at near
+second order from N = 80 to 160, and the FP32 form at N = 320 must reach the printed errors, final
+deformation gradient (Eq. ellipsoid-F-3d) and Jacobian range.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_20646_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_20646_b300 import build
+    build.build()
+
+
+def _run(p, precision):
+    from paper_2606_20646_b300 import lbm
+    sim = lbm.Simulation(p, precision=precision)
+    sim.set_initial().step(p.steps)
+    v, F, u = [t.cpu().numpy().astype(np.float64) for t in sim.fields()]
+    act = sim.active_mask()
+    info = sim.info()
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
+    return v, F, u, act, info
+
+
+def _annulus_errors(p, v, F, u, act):
+    """E_u and E_{F-I} of Sec. 4 (relative L2 over the active nodes)."""
+    A, T = p.meta["A"], p.meta["T"]
+    X, Y = p.coords()
+    s = p.steps * p.dt / T
+    ue = np.stack([(A[0, 0] * (X - .5) + A[0, 1] * (Y - .5)) * s, (A[1, 0] * (X - .5) + A[1, 1] * (Y - .5)) * s])
+    Fe = (np.eye(2) + A * s).reshape(-1)
+    Eu = np.sqrt((((u - ue) ** 2)[:, act]).sum() / ((ue ** 2)[:, act]).sum())
+    G = F[:, act] - np.eye(2).reshape(-1)[:, None]
+    Ge = (Fe - np.eye(2).reshape(-1))[:, None]
+    EF = np.linalg.norm(G - Ge) / np.linalg.norm(np.broadcast_to(Ge, G.shape))
+    return Eu, EF
+
+
+@pytest.mark.parametrize("N", [64, 128, 256, 384])
+def test_affine_annulus_fp64_exact_at_paper_sizes(N):
+    g = GOLD["affine_annulus"]
+    p = I.affine_annulus_2d(N)
+    v, F, u, act, info = _run(p, "fp64")
+    if N == 384:
+        assert (info["n_active"], info["n_cut"]) == tuple(g["active_cut_N384"])
+    Eu, EF = _annulus_errors(p, v, F, u, act)
+    print(f"affine annulus FP64 N={N}: E_u={Eu:.3e} E_F-I={EF:.3e}")
+    assert Eu < 1e-11 and EF < 1e-11
+    # the final state is the printed affine map at t = T
+    Fe = np.eye(2) + np.array(g["A"])
+    assert np.abs(F[:, act].mean(axis=1) - Fe.reshape(-1)).max() < 1e-11
+
+
+def test_affine_annulus_fp32_below_printed_errors_N384():
+    g = GOLD["affine_annulus"]
+    p = I.affine_annulus_2d(384)
+    v, F, u, act, _ = _run(p, "fp32")
+    Eu, EF = _annulus_errors(p, v, F, u, act)
+    print(f"affine annulus FP32 N=384: E_u={Eu:.3e} E_F-I={EF:.3e}")
+    assert Eu < g["E_u_N384"] and EF < g["E_FmI_N384"]
+
+
+def _ellipsoid_errors(p, v, F, u, act):
+    """E_L2(u), E_L2(v), E_L2(F) of Sec. 5.1 against the exact affine motion u = t A (X - X_c)."""
+    A = p.meta["A"]
+    X = p.coords()
+    t = p.steps * p.dt
+    d = [X[j] - 0.5 for j in range(3)]
+    ve = np.stack([sum(A[i, j] * d[j] for j in range(3)) for i in range(3)])
+    Ev = np.linalg.norm((v - ve)[:, act]) / np.linalg.norm(ve[:, act])
+    Eu = np.linalg.norm((u - t * ve)[:, act]) / np.linalg.norm((t * ve)[:, act])
+    Fe = (np.eye(3) + t * A).reshape(-1)[:, None]
+    EF = np.linalg.norm(F[:, act] - Fe) / np.linalg.norm(np.broadcast_to(Fe, F[:, act].shape))
+    print(f"ellipsoid N={p.n[0]}: E_u={Eu:.3e} E_v={Ev:.3e} E_F={EF:.3e}")
+    return Eu, Ev, EF, t
+
+
+def test_ellipsoid_fp64_second_order_80_to_160():
+    """The rotated ellipsoid is not reproduced exactly (omega = 1.8, oblique cut links); Sec. 5.1
+    reports near-second-order refinement.  Doubling N must cut every error by more than 3."""
+    e = {}
+    for N in (80, 160):
+        p = I.ellipsoid_3d(N)
+        v, F, u, act, _ = _run(p, "fp64")
+        e[N] = _ellipsoid_errors(p, v, F, u, act)[:3]
+    for k in range(3):
+        assert e[160][k] < e[80][k] / 3.0, (k, e)
+
+
+def test_ellipsoid_fp32_N320_against_printed_values():
+    g = GOLD["ellipsoid"]
+    p = I.ellipsoid_3d(320)
+    v, F, u, act, info = _run(p, "fp32")
+    na, nc = g["active_cut_N320_rounded"]
+    assert abs(info["n_active"] - na) < 0.05e6 and abs(info["n_cut"] - nc) < 5e3
+    Eu, Ev, EF, t = _ellipsoid_errors(p, v, F, u, act)
+    # errors printed for N = 320 (Sec. 5.1 and Table tab:3d-curved-summary), with 50 % headroom
+    assert Eu < 1.5 * g["E_u_N320"] and Ev < 1.5 * g["E_v_N320"] and EF < 1.5 * g["E_F_N320"]
+    assert abs(t - g["T"]) < 1e-3
+    Fm = F[:, act].mean(axis=1).reshape(3, 3)
+    assert np.abs(Fm - np.array(g["F_T"])).max() < 1.5e-4       # printed to 4 decimals at T = 0.4599
+    J = np.linalg.det(F[:, act].T.reshape(-1, 3, 3))
+    lo, hi = g["J_range_N320"]
+    print(f"ellipsoid N=320 J: median {np.median(J):.6f}, range [{J.min():.6f}, {J.max():.6f}]")
+    assert lo - 5e-6 <= np.median(J) <= hi + 5e-6
+    assert J.min() > lo - 2e-4 and J.max() < hi + 2e-4
