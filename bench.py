@@ -120,9 +120,16 @@ def captured_traffic(n):
 
 def bytes_per_node(D, real_size):
     """Algorithmic HBM bytes per active node of the fused collide-stream kernel: every
-    population component read once and written once, u* read and written, one flag byte."""
+    population component read once and written once, u* read and written (8 bytes per
+    component in both forms: an FP64 plane, or an FP32 hi/lo pair), one flag byte."""
     K, Q = D + D * D, 2 * D
-    return 2 * Q * K * real_size + 2 * D * real_size + 1
+    return 2 * Q * K * real_size + 2 * D * 8 + 1
+
+
+def jacobi_bytes_per_node(D, real_size):
+    """Algorithmic HBM bytes per active node of one damped-Jacobi sweep: correction read and
+    written, residual read, flag and Dirichlet-mask bytes (neighbour reads hit in cache)."""
+    return 3 * D * real_size + 2
 
 
 def dist_setup(args):
@@ -245,10 +252,14 @@ def run_ours(args, world, rank, local):
     bpn = bytes_per_node(3, 4)
     achieved = nact * bpn / (avg_sc / 1e3) / 1e9
     share = {"stream_collide": kt["stream_collide_ms"] / ms, "cutlink": kt["cutlink_ms"] / ms,
-             "projection": kt["projection_ms"] / ms}
+             "projection": kt["projection_ms"] / ms, "jacobi (within projection)": kt["jacobi_ms"] / ms}
+    avg_jac = kt["jacobi_ms"] / max(kt["jacobi_launches"], 1)
+    jacobi = {"avg_sweep_us": round(avg_jac * 1e3, 2), "sweeps": kt["jacobi_launches"],
+              "GBps": round(nact * jacobi_bytes_per_node(3, 4) / (avg_jac / 1e3) / 1e9, 1) if avg_jac > 0 else None}
+    avg_cut = kt["cutlink_ms"] / max(kt["cutlink_launches"], 1)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": captured_traffic(args.n),
-                "kernel": "k_stream_collide<float,3,1>", "bytes_per_launch": nact * bpn,
+                "kernel": "k_stream_collide_tma<3>", "bytes_per_launch": nact * bpn,
                 "avg_launch_ms": round(avg_sc, 4), "peak_kind": peak_kind}
     del sim
     torch.cuda.empty_cache()
@@ -315,6 +326,7 @@ def run_ours(args, world, rank, local):
                            "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
+                "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
                 "cpu_baseline": cpu, "device_status": st}
         print(json.dumps(line), flush=True)

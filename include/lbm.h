@@ -181,6 +181,8 @@ typedef struct lbm_kernel_time {
     double cutlink_ms;        /* per-link boundary source kernel                  */
     double projection_ms;     /* projection, repair and reset kernels             */
     long long stream_collide_launches, cutlink_launches, projection_launches;
+    double jacobi_ms;         /* damped-Jacobi sweeps alone (part of projection_ms) */
+    long long jacobi_launches;
 } lbm_kernel_time;
 
 typedef struct lbm_handle lbm_handle;

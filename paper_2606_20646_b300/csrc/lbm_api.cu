@@ -65,8 +65,8 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     if (h->has_neumann_bc) {
         h->l_sidx = c.take<int>((size_t)kLsqCap * nc);
         h->l_w = c.take<char>((size_t)2 * kLsqCap * nc * rs);
-        h->u0 = c.take<double>((size_t)D * np);
-        h->u1 = c.take<double>((size_t)D * np);
+        h->u0 = c.take<char>((size_t)D * np * 8);  // FP64 planes or FP32 (hi, lo) pairs
+        h->u1 = c.take<char>((size_t)D * np * 8);
         h->dA = c.take<char>((size_t)D * np * rs);
         h->dB = c.take<char>((size_t)D * np * rs);
         h->resid = c.take<char>((size_t)D * np * rs);
@@ -77,7 +77,8 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     } else {
         h->l_sidx = nullptr;
         h->l_w = nullptr;
-        h->u0 = h->u1 = h->partial = h->mean = nullptr;
+        h->u0 = h->u1 = nullptr;
+        h->partial = h->mean = nullptr;
         h->dA = h->dB = h->resid = h->vst = h->Gst = nullptr;
     }
     h->staging = h->opt.host_staging ? c.take<double>((size_t)(2 * D + D * D + D * K) * h->box.nbox) : nullptr;
@@ -121,7 +122,7 @@ int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes) {
     long long nz = grid->dim == 3 ? grid->n[2] : 1;
     tmp.box.nbox = (long long)grid->n[0] * grid->n[1] * nz;
     tmp.box.npad = (tmp.box.nbox + 31) / 32 * 32;
-    tmp.segs_per_row = (grid->n[0] + 31) / 32;
+    tmp.segs_per_row = (grid->n[0] + kSegAlign - 1) / kSegAlign;
     tmp.nsegmax = (long long)tmp.segs_per_row * grid->n[1] * nz;
     carve_geometry(&tmp, nullptr, bytes);
     return LBM_OK;
@@ -212,7 +213,7 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     bx.dx = h->grid.dx;
     bx.nbox = (long long)bx.nx * bx.ny * bx.nz;
     bx.npad = (bx.nbox + 31) / 32 * 32;
-    h->segs_per_row = (bx.nx + 31) / 32;
+    h->segs_per_row = (bx.nx + kSegAlign - 1) / kSegAlign;  // possible window starts per row
     h->nsegmax = (long long)h->segs_per_row * bx.ny * bx.nz;
     h->geo = static_cast<char *>(geometry_storage);
     carve_geometry(h, h->geo, &h->geo_bytes);
@@ -228,7 +229,8 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
                                                        h->status);
     if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
     if (scan(h->cnt, h->lstart, bx.nbox, h->scan_scratch, st)) return fail(LBM_ERR_CUDA);
-    k_seg_flags<<<grid_for(h->nsegmax, 256), 256, 0, st>>>(bx, h->flags, h->segs_per_row, h->nsegmax, h->segflag);
+    k_seg_flags<<<grid_for((long long)bx.ny * bx.nz, 128), 128, 0, st>>>(bx, h->flags, h->segs_per_row,
+                                                                      (long long)bx.ny * bx.nz, h->segflag);
     if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
     if (scan(h->segflag, h->segidx, h->nsegmax, h->scan_scratch, st)) return fail(LBM_ERR_CUDA);
     k_seg_write<<<grid_for(h->nsegmax, 256), 256, 0, st>>>(bx, h->segflag, h->segidx, h->segs_per_row, h->nsegmax,
@@ -395,7 +397,7 @@ int lbm_enable_timing(lbm_handle *h, int enable) {
     if (!h) return LBM_ERR_ARG;
     timing_fold(h);
     h->timing = enable != 0;
-    for (int i = 0; i < 3; ++i) { h->acc_ms[i] = 0.0; h->acc_n[i] = 0; }
+    for (int i = 0; i < 4; ++i) { h->acc_ms[i] = 0.0; h->acc_n[i] = 0; }
     return LBM_OK;
 }
 
@@ -408,6 +410,8 @@ int lbm_kernel_times(lbm_handle *h, lbm_kernel_time *out) {
     out->stream_collide_launches = h->acc_n[0];
     out->cutlink_launches = h->acc_n[1];
     out->projection_launches = h->acc_n[2];
+    out->jacobi_ms = h->acc_ms[3];
+    out->jacobi_launches = h->acc_n[3];
     return LBM_OK;
 }
 

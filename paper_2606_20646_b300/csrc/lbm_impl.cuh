@@ -38,6 +38,7 @@ struct Carver {
 struct EventPair {
     cudaEvent_t a, b;
     int cls;
+    int launches;  // kernels between the two events
 };
 
 struct lbm_handle {
@@ -74,7 +75,8 @@ struct lbm_handle {
     int *l_node = nullptr, *l_q = nullptr, *l_bc = nullptr, *l_ns = nullptr, *l_sidx = nullptr;
     double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
     void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr, *l_fo = nullptr;
-    double *u0 = nullptr, *u1 = nullptr, *partial = nullptr, *mean = nullptr, *staging = nullptr;
+    void *u0 = nullptr, *u1 = nullptr;  // projection warm starts (displacement-accumulator layout)
+    double *partial = nullptr, *mean = nullptr, *staging = nullptr;
     void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
     long long n_neu = 0, n_dir = 0, lsq_entries = 0;
     // state
@@ -90,8 +92,8 @@ struct lbm_handle {
     // timing
     bool timing = false;
     std::vector<EventPair> events;
-    double acc_ms[3] = {0, 0, 0};
-    long long acc_n[3] = {0, 0, 0};
+    double acc_ms[4] = {0, 0, 0, 0};  // stream-collide, cut links, projection, Jacobi sweeps
+    long long acc_n[4] = {0, 0, 0, 0};
 };
 
 // =============================================================================================
@@ -147,8 +149,9 @@ inline int scan(const int *in, int *out, long long n, int *scratch, cudaStream_t
     return LBM_OK;
 }
 
-inline void timing_begin(lbm_handle *h, EventPair &ep, int cls) {
+inline void timing_begin(lbm_handle *h, EventPair &ep, int cls, int launches = 1) {
     ep.cls = cls;
+    ep.launches = launches;
     cudaEventCreate(&ep.a);
     cudaEventCreate(&ep.b);
     cudaEventRecord(ep.a, h->stream);
@@ -165,7 +168,7 @@ inline void timing_fold(lbm_handle *h) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ep.a, ep.b);
         h->acc_ms[ep.cls] += ms;
-        h->acc_n[ep.cls] += 1;
+        h->acc_n[ep.cls] += ep.launches;
         cudaEventDestroy(ep.a);
         cudaEventDestroy(ep.b);
     }
@@ -278,7 +281,7 @@ template <typename real, int D> struct Impl {
         a.lfo = static_cast<real *>(h->l_fo);
         a.vst = static_cast<real *>(h->vst);
         a.Gst = static_cast<real *>(h->Gst);
-        a.u0 = h->u0;
+        a.u0 = static_cast<real *>(h->u0);
         const double dt = h->grid.dx / h->opt.c;
         a.dt = (real)dt;
         a.c = (real)h->opt.c;
@@ -291,7 +294,7 @@ template <typename real, int D> struct Impl {
         return a;
     }
 
-    static ProjArgs<real> proj_args(lbm_handle *h, double t, const double *warm) {
+    static ProjArgs<real> proj_args(lbm_handle *h, double t, const real *warm) {
         ProjArgs<real> p;
         p.b = h->box;
         p.seg = h->seg;
@@ -387,10 +390,10 @@ template <typename real, int D> struct Impl {
         return LBM_OK;
     }
 
-    // one projection solve from the warm start `warm` (FP64): FP64 residual, proj_iters damped-Jacobi
+    // one projection solve from the warm start `warm`: FP64-accumulated residual, proj_iters damped-Jacobi
     // sweeps on the correction d (population precision), gauge shift into h->mean (zero when Dirichlet
     // anchors exist).  Returns the final correction buffer in *d.
-    static int solve(lbm_handle *h, double t, const double *warm, real **d) {
+    static int solve(lbm_handle *h, double t, const real *warm, real **d) {
         ProjArgs<real> p = proj_args(h, t, warm);
         const unsigned g = grid_for(h->nseg, 4);
         k_proj_residual<real, D><<<g, 128, 0, h->stream>>>(p);
@@ -400,12 +403,15 @@ template <typename real, int D> struct Impl {
         const real *src = nullptr;
         real *dst = A;
         const unsigned gj = grid_for(h->nseg, 4 * kJacobiSegs);
+        EventPair ep;
+        if (h->timing && h->opt.proj_iters > 0) timing_begin(h, ep, 3, h->opt.proj_iters);
         for (int it = 0; it < h->opt.proj_iters; ++it) {
             k_jacobi<real, D><<<gj, 128, 0, h->stream>>>(p, src, dst);
             h->launches++;
             src = dst;
             dst = (dst == A) ? B : A;
         }
+        if (h->timing && h->opt.proj_iters > 0) timing_end(h, ep);
         CKL();
         if (!src) {  // no sweeps: zero correction
             CK(cudaMemsetAsync(A, 0, (size_t)D * h->box.npad * sizeof(real), h->stream));
@@ -458,14 +464,15 @@ template <typename real, int D> struct Impl {
                 h->launches++;
                 CKL();
                 real *d = nullptr;
-                int rc = solve(h, t, h->u0, &d);
+                int rc = solve(h, t, static_cast<const real *>(h->u0), &d);
                 if (rc) return rc;
-                k_repair_collide<real, D><<<g, 128, 0, h->stream>>>(a, h->u0, d, h->mean, h->opt.theta_F, h->u1);
+                k_repair_collide<real, D><<<g, 128, 0, h->stream>>>(a, static_cast<const real *>(h->u0), d, h->mean,
+                                                                     h->opt.theta_F, static_cast<real *>(h->u1));
                 h->launches++;
                 CKL();
-                rc = solve(h, t, h->u1, &d);
+                rc = solve(h, t, static_cast<const real *>(h->u1), &d);
                 if (rc) return rc;
-                k_proj_reset<real, D><<<g, 128, 0, h->stream>>>(a, h->u1, d, h->mean);
+                k_proj_reset<real, D><<<g, 128, 0, h->stream>>>(a, static_cast<const real *>(h->u1), d, h->mean);
                 h->launches++;
                 CKL();
                 if (h->timing) timing_end(h, ep);

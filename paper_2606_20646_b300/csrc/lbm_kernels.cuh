@@ -194,23 +194,45 @@ static __global__ void k_scan_add(int *out, const int *__restrict__ boff, long l
 }
 
 // one flag per 32-node x-segment of a row: does it hold an active node?
-static __global__ void k_seg_flags(Box b, const uint8_t *__restrict__ flags, int segs_per_row, long long nsegmax, int *segflag) {
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= nsegmax) return;
-    int row = (int)(s / segs_per_row), j = (int)(s % segs_per_row);
-    int x0 = 32 * j, x1 = min(x0 + 32, b.nx);
-    const uint8_t *r = flags + (long long)row * b.nx;
-    int any = 0;
-    for (int x = x0; x < x1; ++x) any |= (r[x] & kActive) ? 1 : 0;
-    segflag[s] = any;
+// Segments: 32-node x-windows starting at multiples of kSegAlign that cover every node of a row
+// carrying `bit`, chosen left to right: a window starts at the first kSegAlign-node block holding
+// such a node that the previous window does not cover, and spans that block and the next one.
+// Starting windows at the runs rather than at multiples of 32 raises the share of active slots
+// (the 256^3 shell: 86.9 % instead of 78.7 %); kSegAlign = 16 keeps every window start 16-byte
+// aligned for bulk tensor copies of byte and float planes.  f(j) is called with the block index
+// of each window start.
+constexpr int kSegAlign = 16;
+
+template <typename Fn>
+__device__ __forceinline__ void for_each_window(const uint8_t *r, int nx, uint8_t bit, Fn &&f) {
+    int covered = 0;  // first x not covered by the previous window
+    for (int j = 0; j * kSegAlign < nx; ++j) {
+        const int x0 = kSegAlign * j;
+        if (x0 < covered) continue;
+        bool any = false;
+        for (int x = x0; x < min(x0 + kSegAlign, nx); ++x) any |= (r[x] & bit) != 0;
+        if (any) {
+            f(j);
+            covered = x0 + 32;
+        }
+    }
 }
 
-static __global__ void k_seg_write(Box b, const int *__restrict__ segflag, const int *__restrict__ segidx, int segs_per_row,
-                            long long nsegmax, int2 *seg) {
+// one thread per row: segflag[row * slots + j] = 1 where a window starts at block j (0 elsewhere,
+// from the zeroed geometry storage)
+static __global__ void k_seg_flags(Box b, const uint8_t *__restrict__ flags, int slots, long long rows, int *segflag) {
+    const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    int *sf = segflag + row * slots;
+    for_each_window(flags + row * b.nx, b.nx, kActive, [&](int j) { sf[j] = 1; });
+}
+
+static __global__ void k_seg_write(Box b, const int *__restrict__ segflag, const int *__restrict__ segidx, int slots,
+                                   long long nsegmax, int2 *seg) {
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= nsegmax || !segflag[s]) return;
-    int row = (int)(s / segs_per_row), j = (int)(s % segs_per_row);
-    seg[segidx[s]] = make_int2(row * b.nx + 32 * j, row);
+    int row = (int)(s / slots), j = (int)(s % slots);
+    seg[segidx[s]] = make_int2(row * b.nx + kSegAlign * j, row);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -557,7 +579,7 @@ template <typename real> struct StepArgs {
     const real *lrec;  // per cut link: reconstructed incoming populations (K), read by the gather
     real *lfo;         // per cut link: f*_c(m), f*_{c^1}(m) (2K), written by the collision kernels
     real *vst, *Gst;   // projection steps: v^n and G^n = F^n - I (D and D*D planes)
-    double *u0;        // projection steps: u^n in FP64
+    real *u0;          // projection steps: u^n (displacement-accumulator layout)
     real dt, c, omega, gamma, mu, lam, bf[3];
     int *status;
 };
@@ -813,7 +835,14 @@ __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) 
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         a.vst[i * P + node] = v[i];
-        a.u0[i * P + node] = disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i];
+        if constexpr (kDispPair<real>) {
+            float hi = a.ustar[i * P + node], lo = a.ustar[(D + i) * P + node];
+            df_add(hi, lo, real(0.5) * a.dt * v[i]);
+            a.u0[i * P + node] = hi;
+            a.u0[(D + i) * P + node] = lo;
+        } else {
+            a.u0[i * P + node] = a.ustar[i * P + node] + 0.5 * a.dt * v[i];
+        }
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = G[k];
@@ -900,6 +929,25 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
     const int q = a.L.q[l], A = q >> 1;
     const real s = (q & 1) ? real(-1) : real(1);  // e = s e_A, d = -e
     const BCD &bc = a.bcs[a.L.bc[l]];
+    // operands of the reconstruction at the end, loaded first so that they arrive during the
+    // source computation: the node's kept pair f*_c(m), f*_{c^1}(m) and, for eta < 1/2 with an
+    // active upstream node m + e_{c^1}, that node's f*_c
+    const int mnode = a.L.node[l];
+    const real eta_r = (real)a.L.eta[l];
+    const bool up = !((__ldg(a.flags + mnode) >> (q ^ 1)) & 1);
+    real fo[K], fi[K], fu[K];
+    vload<K>(a.L.fo + l * (2 * K), fo);
+    vload<K>(a.L.fo + l * (2 * K) + K, fi);
+    if (up && !(eta_r >= real(0.5))) {
+        int x, y, z;
+        node_xyz(a.b, mnode, x, y, z);
+        const int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
+        #pragma unroll
+        for (int k = 0; k < K; ++k) fu[k] = a.fstar[(long long)(q * K + k) * a.b.npad + mup];
+    } else {
+        #pragma unroll
+        for (int k = 0; k < K; ++k) fu[k] = fo[k];
+    }
     const double Xb[3] = {a.L.Xb[3 * l], a.L.Xb[3 * l + 1], a.L.Xb[3 * l + 2]};
     const double th = a.t + 0.5 * a.dt;  // boundary data at t^n + dt/2
     const real c = (real)a.c;
@@ -1081,28 +1129,16 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
     // f*_{c^1}(m) and, for eta < 1/2, f*_c of the upstream node m + e_{c^1} (m itself when that
     // node is inactive); D_b = diag(-I, I) for Dirichlet, diag(I, -I) for Neumann links.
     {
-        const int m = a.L.node[l];
-        real fo[K], fi[K], R[K];
-        vload<K>(a.L.fo + l * (2 * K), fo);
-        vload<K>(a.L.fo + l * (2 * K) + K, fi);
-        const real eta = (real)a.L.eta[l];
+        const real eta = eta_r;
         const bool neu = bc.kind != 0;
-        const bool up = !((__ldg(a.flags + m) >> (q ^ 1)) & 1);
-        int mup = m;
-        if (up && !(eta >= real(0.5))) {
-            int x, y, z;
-            node_xyz(a.b, m, x, y, z);
-            mup = nbr(a.b, m, x, y, z, q ^ 1);
-        }
+        real R[K];
         #pragma unroll
         for (int k = 0; k < K; ++k) {
             const real Dk = ((k < D) == neu) ? real(1) : real(-1);
-            if (eta >= real(0.5)) {
+            if (eta >= real(0.5))
                 R[k] = (Dk * fo[k] + S[k]) / (real(2) * eta) + (real(1) - real(1) / (real(2) * eta)) * fi[k];
-            } else {
-                const real fu = up ? a.fstar[(long long)(q * K + k) * a.b.npad + mup] : fo[k];
-                R[k] = Dk * (real(2) * eta * fo[k] + (real(1) - real(2) * eta) * fu) + S[k];
-            }
+            else
+                R[k] = Dk * (real(2) * eta * fo[k] + (real(1) - real(2) * eta) * fu[k]) + S[k];
         }
         vstore<K>(a.L.rec + l * K, R);
     }
@@ -1122,7 +1158,7 @@ template <typename real> struct ProjArgs {
     LinkGeom<real> L;
     const BCD *bcs;
     const real *Gst;
-    const double *u0;  // warm start (FP64, D planes)
+    const real *u0;    // warm start (displacement-accumulator layout: FP64 planes or FP32 pairs)
     real *resid;       // residual of the normal equations at the warm start (D planes)
     double t, beta;
 };
@@ -1174,30 +1210,52 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
                 dirichlet_eval(a.bcs[a.L.bc[l]], D, Xb, a.t, true, uD);
                 for (int i = 0; i < D; ++i)
                     r[i] += uD[i] + (double)a.Gst[(i * D + A) * P + node] * (-s * a.L.eta[l] * a.b.dx) -
-                            a.u0[i * P + node];
+                            disp_get<real>(a.u0, P, D, i, node);
             }
             ++l;
         }
     }
-    double um[D];
+    // warm start at the node and its neighbours (FP32 form: hi and lo planes, differenced part by
+    // part); neighbour values of all 2D directions are loaded before use (a cut direction reads the
+    // node itself and is skipped below), so the loads do not wait on one another
+    constexpr int NP = kDispPair<real> ? 2 : 1;
+    real um[NP][D], ul[2 * D][NP][D];
     real rf[D];
+    real Gl_[2 * D][D], Gm_[D][D];
     #pragma unroll
-    for (int i = 0; i < D; ++i) { um[i] = a.u0[i * P + node]; rf[i] = real(0); }
+    for (int i = 0; i < D; ++i) {
+        rf[i] = real(0);
+        #pragma unroll
+        for (int h = 0; h < NP; ++h) um[h][i] = a.u0[(h * D + i) * P + node];
+    }
+    #pragma unroll
+    for (int q = 0; q < 2 * D; ++q) {
+        const int ln = ((cut >> q) & 1) ? node : nbr(a.b, node, x, y, z, q);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            #pragma unroll
+            for (int h = 0; h < NP; ++h) ul[q][h][i] = a.u0[(h * D + i) * P + ln];
+            Gl_[q][i] = a.Gst[(i * D + (q >> 1)) * P + ln];
+        }
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int A = 0; A < D; ++A) Gm_[i][A] = a.Gst[(i * D + A) * P + node];
     #pragma unroll
     for (int q = 0; q < 2 * D; ++q) {
         if ((cut >> q) & 1) continue;
         const int A = q >> 1;
-        const int ln = nbr(a.b, node, x, y, z, q);
         #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const real Gm = a.Gst[(i * D + A) * P + node], Gl = a.Gst[(i * D + A) * P + ln];
+            const real Gm = Gm_[i][A], Gl = Gl_[q][i];
             if constexpr (kShifted<real>) {
                 // FP32 edge term: FP64 difference of the nearby displacements, then FP32
                 const real sdx = (q & 1) ? (real)a.b.dx : -(real)a.b.dx;
-                rf[i] += (real)(a.u0[i * P + ln] - um[i]) + real(0.5) * (Gm + Gl) * sdx;
+                rf[i] += ((ul[q][0][i] - um[0][i]) + (ul[q][NP - 1][i] - um[NP - 1][i])) + real(0.5) * (Gm + Gl) * sdx;
             } else {
                 const double s = (q & 1) ? -1.0 : 1.0;
-                r[i] += a.u0[i * P + ln] - um[i] + 0.5 * ((double)Gm + (double)Gl) * (-s * a.b.dx);
+                r[i] += ul[q][0][i] - um[0][i] + 0.5 * ((double)Gm + (double)Gl) * (-s * a.b.dx);
             }
         }
     }
@@ -1205,63 +1263,68 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
     for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i] + rf[i];
 }
 
-constexpr int kJacobiSegs = 4;  // segments per warp in a Jacobi sweep (independent loads in flight)
+constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep
 
-// one damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr);
-// warp w handles segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1
+// One damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr),
+//   d'_m = (1 - beta) d_m + beta / deg_m (r_m + sum over active axis neighbours l of d_l),
+// warp w handling segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1.  Every load of the
+// warp's segments is issued before any of them is used: the six neighbour loads of each node do
+// not wait for its flags (a neighbour across a cut link, possibly outside the box, is read at a
+// clamped in-range index and dropped afterwards by selection, so values stored there never mix in;
+// lanes past the end of the last row read clamped indices too and store nothing).
 template <typename real, int D>
 __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
-    constexpr int S = kJacobiSegs;
+    constexpr int S = kJacobiSegs, Q = 2 * D;
     const int lane = threadIdx.x & 31;
     const int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
     if (s0 >= a.nseg) return;
     const long long P = a.b.npad;
     const real beta = (real)a.beta;
-    int node[S], xs[S], ys[S], zs[S];
-    uint8_t fl[S], dm[S];
+    const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
+    int node[S], xs[S];
+    long long ln[S][Q];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        const int2 sg = s0 + j < a.nseg ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
-        const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
-        xs[j] = s0 + j < a.nseg ? sg.x - sg.y * a.b.nx + lane : a.b.nx;
-        ys[j] = per ? sg.y % a.b.ny : 0;
-        zs[j] = per ? sg.y / a.b.ny : 0;
+        const bool seg_ok = s0 + j < a.nseg;
+        const int2 sg = seg_ok ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
+        xs[j] = seg_ok ? sg.x - sg.y * a.b.nx + lane : a.b.nx;
         node[j] = sg.x + lane;
+        const int y = per ? sg.y % a.b.ny : 0, z = per ? sg.y / a.b.ny : 0;
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            long long l = nbr(a.b, node[j], xs[j], y, z, q);
+            l = l < 0 ? 0 : (l >= P ? P - 1 : l);
+            ln[j][q] = l;
+        }
     }
+    uint8_t fl[S], dm[S];
+    real r[S][D], dold[S][D], nb[S][Q][D];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        const bool in = xs[j] < a.b.nx;
-        fl[j] = in ? __ldg(a.flags + node[j]) : (uint8_t)0;
-        dm[j] = in ? __ldg(a.dmask + node[j]) : (uint8_t)0;
-    }
-    real acc[S][D], dold[S][D];
-    #pragma unroll
-    for (int j = 0; j < S; ++j) {
-        const bool act = fl[j] & kActive;
-        const unsigned cut = fl[j] & kCutMask;
+        const long long nc = node[j] < P ? node[j] : P - 1;
+        fl[j] = __ldg(a.flags + nc);
+        dm[j] = __ldg(a.dmask + nc);
         #pragma unroll
         for (int i = 0; i < D; ++i) {
-            acc[j][i] = act ? a.resid[i * P + node[j]] : real(0);
-            dold[j][i] = (act && din) ? din[i * P + node[j]] : real(0);
-        }
-        if (act && din) {
+            r[j][i] = __ldg(a.resid + i * P + nc);
+            dold[j][i] = din ? __ldg(din + i * P + nc) : real(0);
             #pragma unroll
-            for (int q = 0; q < 2 * D; ++q) {
-                if ((cut >> q) & 1) continue;
-                const int ln = nbr(a.b, node[j], xs[j], ys[j], zs[j], q);
-                #pragma unroll
-                for (int i = 0; i < D; ++i) acc[j][i] += __ldg(din + i * P + ln);
-            }
+            for (int q = 0; q < Q; ++q) nb[j][q][i] = din ? __ldg(din + i * P + ln[j][q]) : real(0);
         }
     }
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        if (!(fl[j] & kActive)) continue;
-        const int deg = proj_degree(D, fl[j] & kCutMask, dm[j]);
+        if (xs[j] >= a.b.nx || !(fl[j] & kActive)) continue;
+        const unsigned cut = fl[j] & kCutMask;
+        const int deg = proj_degree(D, cut, dm[j]);
         const real w = deg > 0 ? beta / (real)deg : real(0);
         #pragma unroll
-        for (int i = 0; i < D; ++i)
-            dout[i * P + node[j]] = deg > 0 ? (real(1) - beta) * dold[j][i] + w * acc[j][i] : dold[j][i];
+        for (int i = 0; i < D; ++i) {
+            real acc = r[j][i];
+            #pragma unroll
+            for (int q = 0; q < Q; ++q) acc += ((cut >> q) & 1) ? real(0) : nb[j][q][i];
+            dout[i * P + node[j]] = deg > 0 ? (real(1) - beta) * dold[j][i] + w * acc : dold[j][i];
+        }
     }
 }
 
@@ -1339,13 +1402,22 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__
 // (Eq. projection-F-repair-weight), population repair (Eq. projection-population-repair),
 // collision and u*^{n+1}.  f^n is read from and f*^n written to fdst (in place).
 template <typename real, int D>
-__global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, const double *__restrict__ u0,
+__global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, const real *__restrict__ u0,
                                                         const real *__restrict__ dc, const double *__restrict__ mean,
-                                                        double theta, double *u1) {
+                                                        double theta, real *u1) {
     constexpr int K = D + D * D, Q = 2 * D;
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
     const unsigned cut = fl & kCutMask;
+    // the node's pre-collision populations, loaded before the stores to the same array (loads issued
+    // between those stores could not be moved ahead of them): all at once in the FP32 form, one
+    // direction at a time in the FP64 form, whose registers would not hold all of them
+    constexpr int kPre = sizeof(real) == 4 ? Q * K : K;
+    real fpre[kPre];
+    if constexpr (kPre == Q * K) {
+        #pragma unroll
+        for (int j = 0; j < Q * K; ++j) fpre[j] = a.fdst[(long long)j * P + node];
+    }
     real v[D], G[D * D], F[D * D], Pold[D * D], Fr[D * D], Gr[D * D], Pk[D * D];
     #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = a.vst[i * P + node];
@@ -1360,10 +1432,11 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         for (int i = 0; i < D; ++i) {
             real Gc;
             if constexpr (kShifted<real>) {
-                // FP32 form: u^c differences taken in FP64 (u carries the large offset), the rest in FP32
-                const double uo = u0[i * P + node];
-                const real dp = (real)(u0[i * P + lp] - uo) + (dc[i * P + lp] - dc[i * P + node]);
-                const real dm = (real)(uo - u0[i * P + lm]) + (dc[i * P + node] - dc[i * P + lm]);
+                // FP32 form: u^c differences from the (hi, lo) pairs, hi parts first (u carries the large
+                // offset; nearby hi parts subtract exactly), then the corrections
+                const real ho = u0[i * P + node], lo_ = u0[(D + i) * P + node];
+                const real dp = ((u0[i * P + lp] - ho) + (u0[(D + i) * P + lp] - lo_)) + (dc[i * P + lp] - dc[i * P + node]);
+                const real dm = ((ho - u0[i * P + lm]) + (lo_ - u0[(D + i) * P + lm])) + (dc[i * P + node] - dc[i * P + lm]);
                 const real inv = real(1) / (real)a.b.dx;
                 if (ap && am) Gc = real(0.5) * (dp + dm) * inv;
                 else if (ap) Gc = dp * inv;
@@ -1408,9 +1481,13 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         const int A = q >> 1;
         const real s = (q & 1) ? real(-1) : real(1);
         real out[K];
+        if constexpr (kPre == K) {
+            #pragma unroll
+            for (int k = 0; k < K; ++k) fpre[k] = a.fdst[(long long)(q * K + k) * P + node];
+        }
         #pragma unroll
         for (int k = 0; k < K; ++k) {
-            real fv = a.fdst[(long long)(q * K + k) * P + node];
+            real fv = fpre[kPre == K ? k : q * K + k];
             real feq;  // equilibrium at the repaired state (Eq. feq-general-d)
             if (k < D) {
                 const int i = k;
@@ -1436,10 +1513,19 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) {
-        const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
-        u1[i * P + node] = un;
-        if constexpr (kDispPair<real>) disp_set<real>(a.ustar, P, D, i, node, un + (double)(real(0.5) * a.dt * v[i]));
-        else a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
+        if constexpr (kDispPair<real>) {
+            float hi = u0[i * P + node], lo = u0[(D + i) * P + node];
+            df_add(hi, lo, dc[i * P + node] - (real)mean[i]);  // u^n after the first projection
+            u1[i * P + node] = hi;
+            u1[(D + i) * P + node] = lo;
+            df_add(hi, lo, real(0.5) * a.dt * v[i]);           // u*^{n+1}
+            a.ustar[i * P + node] = hi;
+            a.ustar[(D + i) * P + node] = lo;
+        } else {
+            const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
+            u1[i * P + node] = un;
+            a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
+        }
     }
     #pragma unroll
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = Gr[k];
@@ -1447,16 +1533,20 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
 
 // after the second solve: u^n = u0 + d - mean and u*^{n+1} = u^n + dt/2 v^n
 template <typename real, int D>
-__global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, const double *__restrict__ u0,
+__global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, const real *__restrict__ u0,
                                                     const real *__restrict__ dc, const double *__restrict__ mean) {
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         if constexpr (kDispPair<real>) {
-            const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
-            disp_set<real>(a.un, P, D, i, node, un);
-            disp_set<real>(a.ustar, P, D, i, node, un + (double)(real(0.5) * a.dt * a.vst[i * P + node]));
+            float hi = u0[i * P + node], lo = u0[(D + i) * P + node];
+            df_add(hi, lo, dc[i * P + node] - (real)mean[i]);  // u^n after the second projection
+            a.un[i * P + node] = hi;
+            a.un[(D + i) * P + node] = lo;
+            df_add(hi, lo, real(0.5) * a.dt * a.vst[i * P + node]);  // u*^{n+1}
+            a.ustar[i * P + node] = hi;
+            a.ustar[(D + i) * P + node] = lo;
         } else {
             const real un = (real)(u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]));
             a.un[i * P + node] = un;

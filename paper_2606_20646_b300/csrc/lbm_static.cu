@@ -55,7 +55,7 @@ __global__ void k_census_count(Box b, unsigned char *scratch) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(scratch);
     const unsigned char *mask = scratch + kMaskOffset;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    unsigned long long act = 0, cut = 0, seg = 0;
+    unsigned long long act = 0, cut = 0;
     if (i < b.nbox && mask[i]) {
         int x, y, z;
         node_xyz(b, (int)i, x, y, z);
@@ -67,23 +67,28 @@ __global__ void k_census_count(Box b, unsigned char *scratch) {
             if ((co < 0 || co >= n) && !b.per[A]) cut += 1;
             else if (!mask[nbr(b, (int)i, x, y, z, q)]) cut += 1;
         }
-        // an active segment is counted once, by its first active node
-        bool first = true;
-        for (int xx = (x / 32) * 32; xx < x; ++xx)
-            if (mask[i - (x - xx)]) { first = false; break; }
-        seg = first ? 1 : 0;
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         act += __shfl_down_sync(0xffffffffu, act, o);
         cut += __shfl_down_sync(0xffffffffu, cut, o);
-        seg += __shfl_down_sync(0xffffffffu, seg, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (act) atomicAdd(&cnt[0], act);
         if (cut) atomicAdd(&cnt[1], cut);
-        if (seg) atomicAdd(&cnt[2], seg);
     }
+}
+
+// segments: the solver's window rule applied to each row of the mask, one thread per row
+__global__ void k_census_rows(Box b, unsigned char *scratch) {
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(scratch);
+    const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned long long seg = 0;
+    if (row < (long long)b.ny * b.nz)
+        for_each_window(scratch + kMaskOffset + row * b.nx, b.nx, 1, [&](int) { seg += 1; });
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) seg += __shfl_down_sync(0xffffffffu, seg, o);
+    if ((threadIdx.x & 31) == 0 && seg) atomicAdd(&cnt[2], seg);
 }
 
 // device address of the scratch array on the current device, looked up once per device
@@ -147,6 +152,7 @@ extern "C" int lbm_census_static(const lbm_grid *grid, const lbm_levelset *ls, v
     const unsigned grid_n = (unsigned)((b.nbox + 255) / 256);
     k_census_mask<<<grid_n, 256, 0, st>>>(b, table, ls->nshapes, scratch);
     k_census_count<<<grid_n, 256, 0, st>>>(b, scratch);
+    k_census_rows<<<(unsigned)(((long long)b.ny * b.nz + 127) / 128), 128, 0, st>>>(b, scratch);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     unsigned long long host[3] = {0, 0, 0};
     if (cudaMemcpyAsync(host, scratch, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

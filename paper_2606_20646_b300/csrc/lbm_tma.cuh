@@ -278,13 +278,15 @@ template <int D> __device__ __forceinline__ SegStarts seg_starts(const Box &b, i
     return r;
 }
 
-constexpr int kTmaWarps = 4;  // warps (segments) per block of the fused kernel
+// warps (segments) per block of the fused kernel: one, so that a warp's slot frees as soon as that
+// warp is done rather than when the slowest warp of its block is
+constexpr int kTmaWarps = 1;
 
 // K3 with TMA staging (FP32): one warp per 32-node segment.  Lane 0 issues the bulk copies of the
 // segment's population boxes, u* box and flag bytes into the warp's stage; every lane waits on the
 // warp's mbarrier (bounded), so no warp can leave while one of its copies is still in flight.
 template <int D>
-__global__ void __launch_bounds__(32 * kTmaWarps, 4) k_stream_collide_tma(const StepArgs<float> a,
+__global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_collide_tma(const StepArgs<float> a,
                                                                         const __grid_constant__ TmaMaps maps) {
     using L = TmaLayout<D>;
     constexpr int K = L::K, Q = L::Q;
@@ -306,10 +308,10 @@ __global__ void __launch_bounds__(32 * kTmaWarps, 4) k_stream_collide_tma(const 
         for (int q = 0; q < Q; ++q)
             tma_load_2d(cur + L::slot(q), (q >> 1) == 0 ? &maps.wide : &maps.narrow, bar, st.start[q], q * K);
     }
-    // first cut link of each node (used by boundary nodes only), fetched while the copies are in flight;
-    // node < npad for every lane since segments start at multiples of 32 inside the padded box
+    // first cut link of each node (used by boundary nodes only), fetched while the copies are in
+    // flight; lanes past the end of the last row read a clamped index and never use it
     const int node = sg.x + lane;
-    const long long l0pre = __ldg(a.lstart + node);
+    const long long l0pre = __ldg(a.lstart + (node < a.b.npad ? node : a.b.npad - 1));
     __syncwarp();
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
         if (lane == 0) set_status(a.status, kStTimeout);
@@ -364,7 +366,10 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         a.vst[i * P + node] = v[i];
-        a.u0[i * P + node] = disp_get<float>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i];
+        float hi = a.ustar[i * P + node], lo = a.ustar[(D + i) * P + node];
+        df_add(hi, lo, 0.5f * a.dt * v[i]);
+        a.u0[i * P + node] = hi;
+        a.u0[(D + i) * P + node] = lo;
     }
 }
 

@@ -66,7 +66,7 @@ class lbm_info(C.Structure):
 class lbm_kernel_time(C.Structure):
     _fields_ = [("stream_collide_ms", C.c_double), ("cutlink_ms", C.c_double), ("projection_ms", C.c_double),
                 ("stream_collide_launches", C.c_longlong), ("cutlink_launches", C.c_longlong),
-                ("projection_launches", C.c_longlong)]
+                ("projection_launches", C.c_longlong), ("jacobi_ms", C.c_double), ("jacobi_launches", C.c_longlong)]
 
 
 # symbol -> (restype, argtypes); every entry point declared in include/lbm.h
