@@ -127,9 +127,11 @@ def bytes_per_node(D, real_size):
 
 
 def jacobi_bytes_per_node(D, real_size):
-    """Algorithmic HBM bytes per active node of one damped-Jacobi sweep: correction read and
-    written, residual read, flag and Dirichlet-mask bytes (neighbour reads hit in cache)."""
-    return 3 * D * real_size + 2
+    """Algorithmic HBM bytes per active node of one damped-Jacobi sweep: the node's correction
+    vector read and written (D values padded to 2 or 4), its residual vector (4 values: r and the
+    sweep weight) and its flag byte; neighbour reads hit in cache."""
+    dv = 4 if D == 3 else 2
+    return 2 * dv * real_size + 4 * real_size + 1
 
 
 def dist_setup(args):

@@ -49,7 +49,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     h->fB = c.take<char>((size_t)Q * K * np * rs);
     // displacement accumulators: one FP64 plane per component, or a (hi, lo) pair of FP32 planes
     h->ustar = c.take<char>((size_t)D * np * 8);
-    h->un = c.take<char>((size_t)D * np * 8);
+    h->un = c.take<char>((size_t)(D == 3 ? 32 : 16) * np);  // node-major u^n (see kUnStride)
     h->dmask = c.take<uint8_t>(np);
     h->l_node = c.take<int>(nc);
     h->l_q = c.take<int>(nc);
@@ -67,9 +67,10 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->l_w = c.take<char>((size_t)2 * kLsqCap * nc * rs);
         h->u0 = c.take<char>((size_t)D * np * 8);  // FP64 planes or FP32 (hi, lo) pairs
         h->u1 = c.take<char>((size_t)D * np * 8);
-        h->dA = c.take<char>((size_t)D * np * rs);
-        h->dB = c.take<char>((size_t)D * np * rs);
-        h->resid = c.take<char>((size_t)D * np * rs);
+        // correction d (2 or 4 values per node) and residual (4 values per node), node-major
+        h->dA = c.take<char>((size_t)(D == 3 ? 4 : 2) * np * rs);
+        h->dB = c.take<char>((size_t)(D == 3 ? 4 : 2) * np * rs);
+        h->resid = c.take<char>((size_t)4 * np * rs);
         h->vst = c.take<char>((size_t)D * np * rs);
         h->Gst = c.take<char>((size_t)D * D * np * rs);
         h->partial = c.take<double>((size_t)D * (std::max<size_t>(grid_for(h->nseg, 4), kReduceBlocks) + 1));

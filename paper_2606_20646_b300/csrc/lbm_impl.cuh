@@ -414,7 +414,7 @@ template <typename real, int D> struct Impl {
         if (h->timing && h->opt.proj_iters > 0) timing_end(h, ep);
         CKL();
         if (!src) {  // no sweeps: zero correction
-            CK(cudaMemsetAsync(A, 0, (size_t)D * h->box.npad * sizeof(real), h->stream));
+            CK(cudaMemsetAsync(A, 0, (size_t)kDV<D> * h->box.npad * sizeof(real), h->stream));
             src = A;
         }
         if (h->n_dir == 0) {

@@ -62,6 +62,48 @@ __device__ __forceinline__ void disp_set(real *p, long long P, int D, int i, lon
     }
 }
 
+// u^n of the nodes that Neumann LSQ stencils read, node-major so that one node is one or two
+// vector accesses: FP32 form [hi_1..hi_D, (pad), lo_1..lo_D, (pad)], FP64 form [u_1..u_D, (pad)];
+// 32 bytes per node in 3D, 16 in 2D.
+template <typename real, int D> constexpr int kUnStride = (D == 3 ? 32 : 16) / (int)sizeof(real);
+
+template <typename real, int D>
+__device__ __forceinline__ void un_store(real *un, long long node, const real *hi, const real *lo) {
+    real *p = un + (long long)kUnStride<real, D> * node;
+    if constexpr (kDispPair<real>) {
+        if constexpr (D == 3) {
+            reinterpret_cast<float4 *>(p)[0] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+            reinterpret_cast<float4 *>(p)[1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        } else {
+            reinterpret_cast<float4 *>(p)[0] = make_float4(hi[0], hi[1], lo[0], lo[1]);
+        }
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(hi[0], hi[1]);
+        if constexpr (D == 3) reinterpret_cast<double2 *>(p)[1] = make_double2(hi[2], 0.0);
+    }
+}
+
+template <typename real, int D>
+__device__ __forceinline__ void un_load(const real *un, long long node, real *hi, real *lo) {
+    const real *p = un + (long long)kUnStride<real, D> * node;
+    if constexpr (kDispPair<real>) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        if constexpr (D == 3) {
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+            hi[0] = a.x; hi[1] = a.y; hi[2] = a.z;
+            lo[0] = b.x; lo[1] = b.y; lo[2] = b.z;
+        } else {
+            hi[0] = a.x; hi[1] = a.y; lo[0] = a.z; lo[1] = a.w;
+        }
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        hi[0] = a.x; hi[1] = a.y;
+        if constexpr (D == 3) hi[2] = __ldg(reinterpret_cast<const double2 *>(p) + 1).x;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) lo[i] = 0.0;
+    }
+}
+
 struct Box {
     int D, nx, ny, nz;
     int per[3];
@@ -792,22 +834,26 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     const int st = check_state<real, D>(v, F, J);
     if (st) set_status(a.status, st);
     const long long P = a.b.npad;
+    real unh[D], unl[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         if constexpr (kDispPair<real>) {
             float hi = a.ustar[i * P + node], lo = a.ustar[(D + i) * P + node];
             const float d = real(0.5) * a.dt * v[i];
             df_add(hi, lo, d);  // u^n (Eq. u-recovery-general)
-            if (fl & kNeedU) { a.un[i * P + node] = hi; a.un[(D + i) * P + node] = lo; }
+            unh[i] = hi;
+            unl[i] = lo;
             df_add(hi, lo, d);  // u*^{n+1}
             a.ustar[i * P + node] = hi;
             a.ustar[(D + i) * P + node] = lo;
         } else {
             const real un = a.ustar[i * P + node] + real(0.5) * a.dt * v[i];  // u^n (Eq. u-recovery-general)
-            if (fl & kNeedU) a.un[i * P + node] = un;
+            unh[i] = un;
+            unl[i] = real(0);
             a.ustar[i * P + node] = un + real(0.5) * a.dt * v[i];              // u*^{n+1}
         }
     }
+    if (fl & kNeedU) un_store<real, D>(a.un, node, unh, unl);
     collide_store<real, D>(a, node, cut, f, v, G, F, Pk);
 }
 
@@ -976,11 +1022,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         const int m = a.L.node[l];
         const long long P = a.npad;
         real um[D], uml[D];
-        #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            um[i] = a.un[i * P + m];
-            uml[i] = kDispPair<real> ? a.un[(D + i) * P + m] : real(0);
-        }
+        un_load<real, D>(a.un, m, um, uml);
         const int ns = a.L.ns[l];
         if constexpr (!kShifted<real>) {
             // FP64: g = t + sum_j w_j u_j in stencil order, as the oracle sums it
@@ -1003,12 +1045,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
                 for (int al = 0; al < D - 1; ++al) w[jj][al] = __ldg(a.L.w + ((long long)al * kLsqCap + j) * a.L.ncut + l);
             }
             #pragma unroll
-            for (int jj = 0; jj < U; ++jj)
-                #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    uu[jj][i] = a.un[i * P + kk[jj]];
-                    uul[jj][i] = kDispPair<real> ? a.un[(D + i) * P + kk[jj]] : real(0);
-                }
+            for (int jj = 0; jj < U; ++jj) un_load<real, D>(a.un, kk[jj], uu[jj], uul[jj]);
             #pragma unroll
             for (int jj = 0; jj < U; ++jj) {
                 if (j0 + jj >= ns) break;
@@ -1159,9 +1196,44 @@ template <typename real> struct ProjArgs {
     const BCD *bcs;
     const real *Gst;
     const real *u0;    // warm start (displacement-accumulator layout: FP64 planes or FP32 pairs)
-    real *resid;       // residual of the normal equations at the warm start (D planes)
+    real *resid;       // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start
     double t, beta;
 };
+
+// Projection correction d and residual, node-major so that a neighbour is one vector load:
+// d holds kDV values per node (D components, padded to 2 or 4), the residual 4 values per node,
+// (r_1..r_D, w) padded, with the sweep weight w = beta/deg (0 where a node is inactive or has no
+// edge).  Inactive nodes keep d = 0 in both buffers (the storage is zeroed and sweeps write active
+// nodes only).
+template <int D> constexpr int kDV = D == 3 ? 4 : 2;
+
+template <int N, typename real> struct VecT;
+template <> struct VecT<4, float> { using T = float4; };
+template <> struct VecT<2, float> { using T = float2; };
+
+template <int N, typename real> __device__ __forceinline__ void ld_vec(const real *p, real *d) {
+    if constexpr (sizeof(real) == 4) {
+        const auto t = __ldg(reinterpret_cast<const typename VecT<N, float>::T *>(p));
+        d[0] = t.x; d[1] = t.y;
+        if constexpr (N == 4) { d[2] = t.z; d[3] = t.w; }
+    } else {
+        #pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + i);
+            d[2 * i] = t.x; d[2 * i + 1] = t.y;
+        }
+    }
+}
+
+template <int N, typename real> __device__ __forceinline__ void st_vec(real *p, const real *d) {
+    if constexpr (sizeof(real) == 4) {
+        if constexpr (N == 4) *reinterpret_cast<float4 *>(p) = make_float4(d[0], d[1], d[2], d[3]);
+        else *reinterpret_cast<float2 *>(p) = make_float2(d[0], d[1]);
+    } else {
+        #pragma unroll
+        for (int i = 0; i < N / 2; ++i) reinterpret_cast<double2 *>(p)[i] = make_double2(d[2 * i], d[2 * i + 1]);
+    }
+}
 
 // node weight of the normal equations: active axis neighbours plus Dirichlet boundary edges
 __device__ __forceinline__ int proj_degree(int D, unsigned cut, uint8_t dm) {
@@ -1259,72 +1331,83 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
             }
         }
     }
+    const int deg = proj_degree(D, cut, dm);
+    real out[4] = {real(0), real(0), real(0), real(0)};
     #pragma unroll
-    for (int i = 0; i < D; ++i) a.resid[i * P + node] = (real)r[i] + rf[i];
+    for (int i = 0; i < D; ++i) out[i] = (real)r[i] + rf[i];
+    out[D] = deg > 0 ? (real)a.beta / (real)deg : real(0);
+    st_vec<4, real>(a.resid + 4 * (long long)node, out);
 }
 
 constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep
 
 // One damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr),
 //   d'_m = (1 - beta) d_m + beta / deg_m (r_m + sum over active axis neighbours l of d_l),
-// warp w handling segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1.  Every load of the
-// warp's segments is issued before any of them is used: the six neighbour loads of each node do
-// not wait for its flags (a neighbour across a cut link, possibly outside the box, is read at a
-// clamped in-range index and dropped afterwards by selection, so values stored there never mix in;
-// lanes past the end of the last row read clamped indices too and store nothing).
+// warp w handling segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1.  A node is its flag
+// byte, one residual vector, its own d vector and 2D neighbour d vectors, all loaded before any is
+// used; a neighbour across a cut link (inactive, or outside a non-periodic box, where the index is
+// clamped into range) is dropped by selection, as a skipped term; nodes with w = 0 keep their d
+// and are not written.
 template <typename real, int D>
 __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
-    constexpr int S = kJacobiSegs, Q = 2 * D;
+    constexpr int S = kJacobiSegs, Q = 2 * D, V = kDV<D>;
     const int lane = threadIdx.x & 31;
     const int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
     if (s0 >= a.nseg) return;
     const long long P = a.b.npad;
     const real beta = (real)a.beta;
     const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
-    int node[S], xs[S];
-    long long ln[S][Q];
+    long long node[S], ln[S][Q];
+    bool in[S];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
         const bool seg_ok = s0 + j < a.nseg;
         const int2 sg = seg_ok ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
-        xs[j] = seg_ok ? sg.x - sg.y * a.b.nx + lane : a.b.nx;
-        node[j] = sg.x + lane;
+        const int x = sg.x - sg.y * a.b.nx + lane;
+        in[j] = seg_ok && x < a.b.nx;
+        const long long nd = in[j] ? sg.x + lane : 0;  // lanes outside the row read node 0, unused
+        node[j] = nd;
         const int y = per ? sg.y % a.b.ny : 0, z = per ? sg.y / a.b.ny : 0;
         #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            long long l = nbr(a.b, node[j], xs[j], y, z, q);
-            l = l < 0 ? 0 : (l >= P ? P - 1 : l);
-            ln[j][q] = l;
+            long long l = nbr(a.b, (int)nd, x, y, z, q);
+            ln[j][q] = l < 0 ? 0 : (l >= P ? P - 1 : l);  // only inactive nodes can point outside
         }
     }
-    uint8_t fl[S], dm[S];
-    real r[S][D], dold[S][D], nb[S][Q][D];
+    real r[S][4], dold[S][V], nb[S][Q][V];
+    unsigned cut[S];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        const long long nc = node[j] < P ? node[j] : P - 1;
-        fl[j] = __ldg(a.flags + nc);
-        dm[j] = __ldg(a.dmask + nc);
-        #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            r[j][i] = __ldg(a.resid + i * P + nc);
-            dold[j][i] = din ? __ldg(din + i * P + nc) : real(0);
+        cut[j] = __ldg(a.flags + node[j]) & kCutMask;
+        ld_vec<4, real>(a.resid + 4 * node[j], r[j]);
+        if (din) {
+            ld_vec<V, real>(din + V * node[j], dold[j]);
             #pragma unroll
-            for (int q = 0; q < Q; ++q) nb[j][q][i] = din ? __ldg(din + i * P + ln[j][q]) : real(0);
+            for (int q = 0; q < Q; ++q) ld_vec<V, real>(din + V * ln[j][q], nb[j][q]);
+        } else {
+            #pragma unroll
+            for (int i = 0; i < V; ++i) {
+                dold[j][i] = real(0);
+                #pragma unroll
+                for (int q = 0; q < Q; ++q) nb[j][q][i] = real(0);
+            }
         }
     }
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        if (xs[j] >= a.b.nx || !(fl[j] & kActive)) continue;
-        const unsigned cut = fl[j] & kCutMask;
-        const int deg = proj_degree(D, cut, dm[j]);
-        const real w = deg > 0 ? beta / (real)deg : real(0);
+        const real w = r[j][D];
+        if (!in[j] || !(w > real(0))) continue;
+        real out[V];
+        #pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = real(0);
         #pragma unroll
         for (int i = 0; i < D; ++i) {
             real acc = r[j][i];
             #pragma unroll
-            for (int q = 0; q < Q; ++q) acc += ((cut >> q) & 1) ? real(0) : nb[j][q][i];
-            dout[i * P + node[j]] = deg > 0 ? (real(1) - beta) * dold[j][i] + w * acc : dold[j][i];
+            for (int q = 0; q < Q; ++q) acc += ((cut[j] >> q) & 1) ? real(0) : nb[j][q][i];
+            out[i] = (real(1) - beta) * dold[j][i] + w * acc;
         }
+        st_vec<V, real>(dout + V * node[j], out);
     }
 }
 
@@ -1357,7 +1440,7 @@ __global__ void __launch_bounds__(128) k_reduce_partial(const ProjArgs<real> a, 
         for (int j = 0; j < 4; ++j)
             if (ok[j])
                 #pragma unroll
-                for (int i = 0; i < D; ++i) dl[i] += dc[i * a.b.npad + node[j]];
+                for (int i = 0; i < D; ++i) dl[i] += dc[(long long)kDV<D> * node[j] + i];
     }
     double d[D];
     #pragma unroll
@@ -1406,6 +1489,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
                                                         const real *__restrict__ dc, const double *__restrict__ mean,
                                                         double theta, real *u1) {
     constexpr int K = D + D * D, Q = 2 * D;
+    constexpr long long DV = kDV<D>;
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
     const unsigned cut = fl & kCutMask;
@@ -1435,8 +1519,8 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
                 // FP32 form: u^c differences from the (hi, lo) pairs, hi parts first (u carries the large
                 // offset; nearby hi parts subtract exactly), then the corrections
                 const real ho = u0[i * P + node], lo_ = u0[(D + i) * P + node];
-                const real dp = ((u0[i * P + lp] - ho) + (u0[(D + i) * P + lp] - lo_)) + (dc[i * P + lp] - dc[i * P + node]);
-                const real dm = ((ho - u0[i * P + lm]) + (lo_ - u0[(D + i) * P + lm])) + (dc[i * P + node] - dc[i * P + lm]);
+                const real dp = ((u0[i * P + lp] - ho) + (u0[(D + i) * P + lp] - lo_)) + (dc[DV * lp + i] - dc[DV * node + i]);
+                const real dm = ((ho - u0[i * P + lm]) + (lo_ - u0[(D + i) * P + lm])) + (dc[DV * node + i] - dc[DV * lm + i]);
                 const real inv = real(1) / (real)a.b.dx;
                 if (ap && am) Gc = real(0.5) * (dp + dm) * inv;
                 else if (ap) Gc = dp * inv;
@@ -1446,9 +1530,9 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
             } else {
                 double gc;
                 bool keep = false;
-                const double up = u0[i * P + lp] + (double)dc[i * P + lp];
-                const double um = u0[i * P + lm] + (double)dc[i * P + lm];
-                const double uo = u0[i * P + node] + (double)dc[i * P + node];
+                const double up = u0[i * P + lp] + (double)dc[DV * lp + i];
+                const double um = u0[i * P + lm] + (double)dc[DV * lm + i];
+                const double uo = u0[i * P + node] + (double)dc[DV * node + i];
                 if (ap && am) gc = (up - um) / (2.0 * a.b.dx);
                 else if (ap) gc = (up - uo) / a.b.dx;
                 else if (am) gc = (uo - um) / a.b.dx;
@@ -1515,14 +1599,14 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     for (int i = 0; i < D; ++i) {
         if constexpr (kDispPair<real>) {
             float hi = u0[i * P + node], lo = u0[(D + i) * P + node];
-            df_add(hi, lo, dc[i * P + node] - (real)mean[i]);  // u^n after the first projection
+            df_add(hi, lo, dc[DV * node + i] - (real)mean[i]);  // u^n after the first projection
             u1[i * P + node] = hi;
             u1[(D + i) * P + node] = lo;
             df_add(hi, lo, real(0.5) * a.dt * v[i]);           // u*^{n+1}
             a.ustar[i * P + node] = hi;
             a.ustar[(D + i) * P + node] = lo;
         } else {
-            const double un = u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]);
+            const double un = u0[i * P + node] + (double)(dc[DV * node + i] - (real)mean[i]);
             u1[i * P + node] = un;
             a.ustar[i * P + node] = (real)un + real(0.5) * a.dt * v[i];
         }
@@ -1535,24 +1619,28 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
 template <typename real, int D>
 __global__ void __launch_bounds__(128) k_proj_reset(const StepArgs<real> a, const real *__restrict__ u0,
                                                     const real *__restrict__ dc, const double *__restrict__ mean) {
+    constexpr long long DV = kDV<D>;
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
+    real unh[D], unl[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         if constexpr (kDispPair<real>) {
             float hi = u0[i * P + node], lo = u0[(D + i) * P + node];
-            df_add(hi, lo, dc[i * P + node] - (real)mean[i]);  // u^n after the second projection
-            a.un[i * P + node] = hi;
-            a.un[(D + i) * P + node] = lo;
+            df_add(hi, lo, dc[DV * node + i] - (real)mean[i]);  // u^n after the second projection
+            unh[i] = hi;
+            unl[i] = lo;
             df_add(hi, lo, real(0.5) * a.dt * a.vst[i * P + node]);  // u*^{n+1}
             a.ustar[i * P + node] = hi;
             a.ustar[(D + i) * P + node] = lo;
         } else {
-            const real un = (real)(u0[i * P + node] + (double)(dc[i * P + node] - (real)mean[i]));
-            a.un[i * P + node] = un;
+            const real un = (real)(u0[i * P + node] + (double)(dc[DV * node + i] - (real)mean[i]));
+            unh[i] = un;
+            unl[i] = real(0);
             a.ustar[i * P + node] = un + real(0.5) * a.dt * a.vst[i * P + node];
         }
     }
+    un_store<real, D>(a.un, node, unh, unl);
 }
 
 }  // namespace tlv

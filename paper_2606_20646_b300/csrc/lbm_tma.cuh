@@ -166,7 +166,7 @@ struct TmaMaps {
 //   f*_q = (1 - omega) f_q + omega f^eq_q + src_q with omega f^eq_q = base_k +- (omega D/(2Dc)) Phi_A,k
 template <int D>
 __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
-                                               const float us[2 * D], long long l0) {
+                                               const float us[2 * D], long long l0, bool act) {
     constexpr int K = D + D * D, Q = 2 * D;
     float S[K];
     #pragma unroll
@@ -193,18 +193,22 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     for (int i = 0; i < D; ++i) chk += v[i];
     #pragma unroll
     for (int k = 0; k < D * D; ++k) chk += P[k];
-    if (!(J > 0.0f) || !isfinite(chk)) set_status(a.status, (J > 0.0f ? 0 : kStJacobian) | (isfinite(chk) ? 0 : kStNonfinite));
+    if (act && (!(J > 0.0f) || !isfinite(chk)))
+        set_status(a.status, (J > 0.0f ? 0 : kStJacobian) | (isfinite(chk) ? 0 : kStNonfinite));
     const long long Pn = a.b.npad;
+    float unh[D], unl[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         float hi = us[i], lo = us[D + i];  // u*^n as a (hi, lo) pair
         const float d = hdt * v[i];
         df_add(hi, lo, d);  // u^n
-        if (fl & kNeedU) { a.un[i * Pn + node] = hi; a.un[(D + i) * Pn + node] = lo; }
+        unh[i] = hi;
+        unl[i] = lo;
         df_add(hi, lo, d);  // u*^{n+1}
-        a.ustar[i * Pn + node] = hi;
-        a.ustar[(D + i) * Pn + node] = lo;
+        a.ustar[i * Pn + node] = act ? hi : 0.0f;
+        a.ustar[(D + i) * Pn + node] = act ? lo : 0.0f;
     }
+    if (fl & kNeedU) un_store<float, D>(a.un, node, unh, unl);
     const float om1 = 1.0f - a.omega;
     const float wf = a.omega * (1.0f / float(2 * D));  // omega/(2D)
     const float wc = wf * (float(D) / a.c);             // omega/(2D) * D/c
@@ -236,7 +240,7 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
             } else {
                 t = base[k];
             }
-            o[k] = fmaf(om1, staged<D>(wsm, q, k, lane), t);
+            o[k] = act ? fmaf(om1, staged<D>(wsm, q, k, lane), t) : 0.0f;
             out[(long long)(q * K + k) * Pn] = o[k];
         }
         if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, o);
@@ -318,15 +322,20 @@ __global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_colli
         mbar_wait_bounded(bar, 0);  // let the copies in flight land before the warp exits
         return;
     }
+    // Every lane inside the row stores: inactive nodes receive zeros, so each warp writes whole
+    // 32-byte sectors of every plane (a partly written sector costs the memory system a read of
+    // the rest).  Nothing reads an inactive node's populations or u*: pulls across cut links are
+    // replaced by the closure.  Lanes past the row end belong to the next row and store nothing.
     const int x = sg.x - sg.y * a.b.nx + lane;
-    const uint8_t fl = x < a.b.nx ? reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane] : (uint8_t)0;
-    if (!(fl & kActive)) return;
+    if (x >= a.b.nx) return;
+    const uint8_t fl = reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane];
+    const bool act = fl & kActive;
     float us[2 * D];
     #pragma unroll
     for (int d = 0; d < 2 * D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
     const long long l0 = (fl & kCutMask) ? l0pre : 0;
-    tma_closure<D>(a, cur, node, x, lane, fl & kCutMask, l0);
-    collide_staged<D>(a, cur, node, lane, fl, us, l0);
+    if (act) tma_closure<D>(a, cur, node, x, lane, fl & kCutMask, l0);
+    collide_staged<D>(a, cur, node, lane, fl, us, l0, act);
 }
 
 // projection steps, part 1, with TMA staging (FP32)

@@ -450,3 +450,36 @@ def random_box(dim: int, n: int, seed: int, precision_note: str = "") -> Problem
              BC(1, "neumann", "const", ramp="sin2", t_ramp=0.05, vec=tuple(tr))]
     _rest_fields(p)
     return p
+
+
+def face_touching_box(dim: int, n: int, seed: int) -> Problem:
+    """Seeded axis-aligned ellipsoidal body whose surface passes between the outermost node centres
+    and every box face (semi-axes = half box extent - 0.2 dx), so active nodes lie on all the box
+    faces and their links across the faces are cut links to the outside of the box.  A seeded
+    elliptic hole carries affine Dirichlet data, the outer surface a constant Neumann traction;
+    ragged box (n, n+3, n+5).  For parity runs of box-face cut links."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n + 3, n + 5) if dim == 3 else (n, n + 3, 1)
+    dx = 1.0 / n
+    ext = [dims[a] * dx for a in range(dim)]
+    ctr = tuple(0.5 * e for e in ext)
+    outer_axes = tuple(0.5 * e - 0.2 * dx for e in ext)
+    inner_axes = tuple(0.5 * min(ext) * rng.uniform(0.25, 0.35) for _ in range(dim))
+    R = rot_z(rng.uniform(0, 90)) @ (rot_y(rng.uniform(0, 90)) if dim == 3 else np.eye(3))
+    p = Problem(name=f"face_touching_{dim}d_{n}_{seed}", dim=dim, n=dims, dx=dx, origin=(0, 0, 0),
+                periodic=(False, False, False), mu=1.0, lam=float(rng.uniform(1.0, 5.0)),
+                options=Options(c=10.0, omega=1.8, gamma=10.0, proj_every=5, proj_iters=20))
+    p.shapes = [Shape("ellipsoid", ctr, outer_axes, boundary_id=1),
+                Shape("ellipsoid", ctr, inner_axes, rot=R, complement=True, boundary_id=0)]
+    A = rng.uniform(-0.2, 0.2, size=(3, 3))
+    if dim == 2:
+        A[2, :] = 0
+        A[:, 2] = 0
+    tr = rng.uniform(-0.05, 0.05, size=3)
+    if dim == 2:
+        tr[2] = 0
+    p.bcs = [BC(0, "dirichlet", "affine", ramp="sin2", t_ramp=0.05, center=ctr, A=A),
+             BC(1, "neumann", "const", ramp="sin2", t_ramp=0.05, vec=tuple(tr))]
+    _rest_fields(p)
+    return p
+

@@ -75,6 +75,23 @@ def test_random_body_ragged_box_fp64(dim, n, seed):
     _check64(errs, sg, so)
 
 
+@pytest.mark.parametrize("dim,n,seed", [(2, 48, 1), (3, 32, 2)])
+def test_face_touching_body_fp64(dim, n, seed):
+    """Body whose surface passes between the outermost nodes and every box face: active nodes on
+    the faces with cut links leaving the box (neighbour indices outside the box are never used)."""
+    p = I.face_touching_box(dim, n, seed)
+    errs, sg, so, *_ = compare(p, 40, "fp64")
+    _check64(errs, sg, so)
+
+
+def test_face_touching_body_fp32():
+    """FP32 form of the box-face case, rows a multiple of 16 (the bulk-copy kernel)."""
+    p = I.face_touching_box(3, 32, 3)
+    errs, sg, so, *_ = compare(p, 40, "fp32")
+    assert sg == 0 and so == 0
+    assert errs["v"] < TOL32 and errs["F"] < TOL32, errs
+
+
 def test_shell_fp64_32():
     """3D thick spherical shell, both surfaces Neumann (mean gauge), 32^3."""
     p = I.shell_3d(32)
