@@ -99,7 +99,9 @@ class Clocks:
 # reported only while those sources are unchanged (null otherwise).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = None  # {"sources_sha256": ..., "bytes_per_launch": ..., "n": 256, "summary": "profiles/..."}
+TRAFFIC_CAPTURE = {"sources_sha256": "5d2f1468508fc905a946fbe6b6ec1883d6e753128212f81c1e7e5775d20a808f",
+                   "bytes_per_launch": 2527481088 + 2094867712, "n": 256,
+                   "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
 
 
 def kernel_sources_hash():
