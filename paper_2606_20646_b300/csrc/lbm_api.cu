@@ -122,7 +122,7 @@ int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes) {
     tmp.grid = *grid;
     long long nz = grid->dim == 3 ? grid->n[2] : 1;
     tmp.box.nbox = (long long)grid->n[0] * grid->n[1] * nz;
-    tmp.box.npad = (tmp.box.nbox + 31) / 32 * 32;
+    tmp.box.npad = (tmp.box.nbox + 31) / 32 * 32 + 32;
     tmp.segs_per_row = (grid->n[0] + kSegAlign - 1) / kSegAlign;
     tmp.nsegmax = (long long)tmp.segs_per_row * grid->n[1] * nz;
     carve_geometry(&tmp, nullptr, bytes);
@@ -213,7 +213,9 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     for (int a = 0; a < 3; ++a) { bx.per[a] = h->grid.periodic[a] != 0; bx.origin[a] = h->grid.origin[a]; }
     bx.dx = h->grid.dx;
     bx.nbox = (long long)bx.nx * bx.ny * bx.nz;
-    bx.npad = (bx.nbox + 31) / 32 * 32;
+    // plane length: the box rounded up to 32 nodes plus one spare window, so that a 32-node window
+    // starting anywhere in the box stays inside every plane
+    bx.npad = (bx.nbox + 31) / 32 * 32 + 32;
     h->segs_per_row = (bx.nx + kSegAlign - 1) / kSegAlign;  // possible window starts per row
     h->nsegmax = (long long)h->segs_per_row * bx.ny * bx.nz;
     h->geo = static_cast<char *>(geometry_storage);
