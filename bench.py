@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
+    ap.add_argument("--batch-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -311,6 +313,47 @@ def run_ours(args, world, rank, local):
         del sim
         torch.cuda.empty_cache()
 
+    # ---- many 2D specimens packed into one body, 1000 steps as one CUDA graph -------------------
+    batch = None
+    if not args.no_batch:
+        packed, specs = I.batch_2d(steps=args.batch_steps)
+        sim = lbm.Simulation(packed, precision="fp32", device=dev)
+        inf_b = sim.info()
+        sim.set_initial()
+        sim.step(W)
+        st_b = sim.sync(raise_on_status=False)
+        Kb = args.batch_steps
+        stream = sim.stream
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        sim.step_graph(Kb)          # stream capture and instantiation on the host, then one launch
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = max_over_ranks(time.perf_counter() - t0, world)
+        ms_g = max_over_ranks(e0.elapsed_time(e1), world)
+        st_b = st_b or sim.sync(raise_on_status=False)
+        # the same steps launched one by one, for the launch overhead the graph removes
+        e0.record(stream)
+        sim.step(Kb // 4)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = max_over_ranks(e0.elapsed_time(e1), world) * 4
+        nb = inf_b["n_active"]
+        batch = {"workload": f"{len(specs)} 2D D2Q4x6 FP32 specimens, sides U{{64..768}}, 1-5 elliptic holes, "
+                             f"per-specimen mu and lambda, packed in a {packed.n[0]}x{packed.n[1]} box; "
+                             "left edge clamped, right edge translated, holes traction-free",
+                 "n_active": nb, "n_cut_links": inf_b["n_cut"], "steps": Kb,
+                 "value": round(world * nb * Kb / (ms_g / 1e3) / 1e6, 2) if st_b == 0 else None, "unit": UNIT,
+                 "graph_ms": round(ms_g, 2), "graph_wall_s": round(wall, 3),
+                 "note": "value over graph_ms: CUDA events around lbm_step_graph, host capture and instantiation included",
+                 "stepwise_ms_per_step": round(ms_s / Kb, 4), "graph_ms_per_step": round(ms_g / Kb, 4),
+                 "device_status": st_b}
+        del sim
+        torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ---------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -331,7 +374,7 @@ def run_ours(args, world, rank, local):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
                 "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
-                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "batch_2d": batch,
                 "cpu_baseline": cpu, "device_status": st}
         print(json.dumps(line), flush=True)
 

@@ -89,6 +89,7 @@ enum lbm_bc_kind { LBM_BC_DIRICHLET = 0, LBM_BC_NEUMANN = 1 };
  *     AFFINE        u_D = s(t) A (X - center)
  *     RADIAL        u_D = amp s(t) (X - center)/|X - center|
  *     TWIST_STRETCH u_D = ((R(s(t) amp) - I) (X_1 - c_1, X_2 - c_2), s(t) vec[2])  (3D)
+ *     CONST         u_D = s(t) vec  (a translation of the boundary part)
  *   Neumann (nominal traction T = P N):
  *     CONST         T = s(t) vec
  *     RADIAL        T = amp s(t) (X - center)/|X - center|                        */
@@ -108,7 +109,8 @@ enum lbm_ramp { LBM_RAMP_ONE = 0, LBM_RAMP_LINEAR = 1, LBM_RAMP_SIN2 = 2, LBM_RA
  * correction of Eqs. (init-general-d, Ut-general-init) */
 enum lbm_init { LBM_INIT_EQUILIBRIUM = 0, LBM_INIT_CHARACTERISTIC = 1 };
 
-#define LBM_MAX_SHAPES 16
+#define LBM_MAX_SHAPES 1024
+#define LBM_MAX_GROUPS 256
 #define LBM_MAX_BCS 16
 #define LBM_LSQ_CAPACITY 160 /* max active nodes within 3 dx of a boundary point */
 
@@ -132,15 +134,29 @@ typedef struct lbm_shape {
     double p;        /* superellipse exponent                                   */
 } lbm_shape;
 
-typedef struct lbm_levelset {
-    int nshapes; /* 0: every box node active (periodic boxes) */
-    const lbm_shape *shapes;
-} lbm_levelset;
-
 typedef struct lbm_material {
     double mu;     /* shear modulus                  */
     double lambda; /* Lame's first parameter          */
 } lbm_material;
+
+/* A body of several disjoint specimens (no counterpart in the paper, which treats one body at a
+ * time): each group is one specimen, phi_g = max over the group's shapes, and the domain is the
+ * union, phi = min over the groups whose box [lo, hi] contains X (phi > 0 outside every box).  A
+ * group's box must contain its body.  Each group carries its own material; cut links take the
+ * shape (and so the boundary id) of the group that defines phi at X_b. */
+typedef struct lbm_group {
+    int first_shape;  /* the group's shapes are shapes[first_shape .. first_shape + nshapes) */
+    int nshapes;
+    double lo[3], hi[3];
+    lbm_material material;
+} lbm_group;
+
+typedef struct lbm_levelset {
+    int nshapes; /* 0: every box node active (periodic boxes) */
+    const lbm_shape *shapes;
+    int ngroups; /* 0: one body, phi = max over all shapes, the material passed to lbm_create */
+    const lbm_group *groups;
+} lbm_levelset;
 
 typedef struct lbm_bc {
     int boundary_id;
@@ -231,6 +247,17 @@ int lbm_set_initial(lbm_handle *h, int mode, const double *v0, const double *F0,
  * proj_every steps).  Enqueued; returns after launching. */
 int lbm_step(lbm_handle *h, int nsteps);
 
+/* The same nsteps steps recorded as one CUDA graph (stream capture of the launches lbm_step
+ * would enqueue) and launched once on the handle's stream; no counterpart in the paper.  The
+ * launches are recorded on a non-blocking stream the library creates for the handle on first use
+ * (the handle's stream may be the legacy default stream, which cannot be captured) and destroys
+ * in lbm_destroy.  The graph's kernel parameters (times, buffers) belong to these steps, so it is
+ * launched once and kept until the next lbm_step_graph call or lbm_destroy.  The handle's stream
+ * must not be capturing and kernel timing must be off.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not
+ * initialised, timing on, or the stream capturing), LBM_ERR_CUDA (stream creation, capture,
+ * instantiation or launch failed). */
+int lbm_step_graph(lbm_handle *h, int nsteps);
+
 /* Writes v, F (from U^num, Eq. state-recovery-general) and u = u* + dt/2 v
  * (Eq. u-recovery-general) at the current time.  Any pointer may be NULL. */
 int lbm_fields(lbm_handle *h, double *v, double *F, double *u);
@@ -277,8 +304,10 @@ const char *lbm_error_string(int code);
  * the counters and rewrites the mask before use.  Work is enqueued on cuda_stream, then the
  * call synchronises that stream to return the counts.  It calls no cudaMalloc, cudaFree or
  * allocating library routine.
- * Errors: LBM_ERR_ARG (invalid grid or level set), LBM_ERR_CAPACITY (more than
- * LBM_CENSUS_MAX_NODES box nodes), LBM_ERR_CUDA. */
+ * Takes single-body level sets of at most LBM_CENSUS_MAX_SHAPES shapes (ngroups must be 0).
+ * Errors: LBM_ERR_ARG (invalid grid or level set, groups, too many shapes), LBM_ERR_CAPACITY
+ * (more than LBM_CENSUS_MAX_NODES box nodes), LBM_ERR_CUDA. */
+#define LBM_CENSUS_MAX_SHAPES 16
 int lbm_census_static(const lbm_grid *grid, const lbm_levelset *levelset, void *cuda_stream, long long *n_active,
                       long long *n_cut, long long *n_segments);
 

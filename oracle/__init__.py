@@ -99,6 +99,8 @@ def _f64(a):
 
 
 def problem_struct(p) -> _Problem:
+    if getattr(p, "groups", None):
+        raise ValueError("the oracle takes one body per problem; run each specimen as its own problem")
     s = _Problem()
     s.dim = p.dim
     for a in range(3):

@@ -422,6 +422,9 @@ static void dirichlet_velocity(const orc_bc *bc, int D, const double *X, double 
         if (D == 3) v[2] = sd * bc->vec[2];
         break;
     }
+    case 4: /* translation u_D = s(t) vec */
+        for (int i = 0; i < D; i++) v[i] = sd * bc->vec[i];
+        break;
     default:
         break;
     }
@@ -451,6 +454,9 @@ static void dirichlet_displacement(const orc_bc *bc, int D, const double *X, dou
         if (D == 3) u[2] = s * bc->vec[2];
         break;
     }
+    case 4: /* translation */
+        for (int i = 0; i < D; i++) u[i] = s * bc->vec[i];
+        break;
     default:
         break;
     }

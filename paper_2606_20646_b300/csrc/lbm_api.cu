@@ -36,6 +36,10 @@ static void carve_geometry(lbm_handle *h, char *base, size_t *bytes) {
     h->scan_scratch = c.take<int>(scan_scratch_ints(std::max<long long>(np, h->nsegmax)));
     h->counters = c.take<unsigned long long>(8);
     h->dshapes = c.take<ShapeD>(kMaxShapes);
+    h->dgroups = c.take<GroupD>(kMaxGroups);
+    h->mtab_d = c.take<double>(2 * kMaxGroups);
+    h->mtab_f = c.take<float>(2 * kMaxGroups);
+    h->gidx = c.take<uint8_t>(np);
     h->dbcs = c.take<BCD>(kMaxBCs);
     h->status = c.take<int>(8);
     *bytes = c.off;
@@ -138,6 +142,15 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         return LBM_ERR_ARG;
     if (ls->nshapes < 0 || ls->nshapes > kMaxShapes || (ls->nshapes > 0 && !ls->shapes)) return LBM_ERR_ARG;
     if (!(mat->mu > 0.0) || !(mat->lambda > -mat->mu)) return LBM_ERR_ARG;
+    if (ls->ngroups < 0 || ls->ngroups > kMaxGroups || (ls->ngroups > 0 && (!ls->groups || ls->nshapes == 0)))
+        return LBM_ERR_ARG;
+    for (int g = 0; g < ls->ngroups; ++g) {
+        const lbm_group &G = ls->groups[g];
+        if (G.first_shape < 0 || G.nshapes < 1 || G.first_shape + G.nshapes > ls->nshapes) return LBM_ERR_ARG;
+        if (!(G.material.mu > 0.0) || !(G.material.lambda > -G.material.mu)) return LBM_ERR_ARG;
+        for (int a = 0; a < grid->dim; ++a)
+            if (!(G.lo[a] <= G.hi[a])) return LBM_ERR_ARG;
+    }
     if (opt->precision != LBM_PREC_FP64 && opt->precision != LBM_PREC_FP32) return LBM_ERR_ARG;
     if (!(opt->c > 0.0) || !(opt->omega > 0.0 && opt->omega <= 2.0) || !(opt->gamma >= 0.0)) return LBM_ERR_ARG;
     if (opt->proj_every < 0 || opt->proj_iters < 0 || !(opt->theta_F > 0.0 && opt->theta_F <= 1.0) ||
@@ -154,7 +167,7 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         if (bc.ramp < 0 || bc.ramp > LBM_RAMP_TIME) return LBM_ERR_ARG;
         if ((bc.ramp == LBM_RAMP_LINEAR || bc.ramp == LBM_RAMP_SIN2 || bc.ramp == LBM_RAMP_COS) && !(bc.t_ramp > 0.0))
             return LBM_ERR_ARG;
-        if (bc.kind == LBM_BC_DIRICHLET && !(bc.profile >= LBM_PROFILE_ZERO && bc.profile <= LBM_PROFILE_TWIST_STRETCH))
+        if (bc.kind == LBM_BC_DIRICHLET && !(bc.profile >= LBM_PROFILE_ZERO && bc.profile <= LBM_PROFILE_CONST))
             return LBM_ERR_ARG;
         if (bc.kind == LBM_BC_NEUMANN && !(bc.profile == LBM_PROFILE_ZERO || bc.profile == LBM_PROFILE_RADIAL ||
                                            bc.profile == LBM_PROFILE_CONST))
@@ -190,6 +203,17 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         for (int a = 0; a < 3; ++a) { d.c[a] = sh.center[a]; d.a[a] = sh.axes[a]; }
         for (int a = 0; a < 9; ++a) d.Q[a] = sh.rot[a];
         d.p = sh.p;
+    }
+    h->ngroups = ls->ngroups;
+    for (int g = 0; g < ls->ngroups; ++g) {
+        const lbm_group &G = ls->groups[g];
+        GroupD &d = h->groups[g];
+        d.first = G.first_shape;
+        d.count = G.nshapes;
+        for (int a = 0; a < 3; ++a) { d.lo[a] = G.lo[a]; d.hi[a] = G.hi[a]; }
+        if (grid->dim == 2) { d.lo[2] = -1.0; d.hi[2] = 1.0; }
+        h->gmat[2 * g] = G.material.mu;
+        h->gmat[2 * g + 1] = G.material.lambda;
     }
     h->nbc = nbc;
     for (int b = 0; b < nbc; ++b) {
@@ -227,8 +251,18 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     if (cudaMemcpyAsync(h->dshapes, h->shapes, sizeof(h->shapes), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(h->dbcs, h->bcs, sizeof(h->bcs), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
-    k_mask<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, h->dshapes, h->nshapes, h->flags);
-    k_cutbits<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, h->dshapes, h->nshapes, h->flags, h->cnt, h->counters,
+    if (h->ngroups > 0) {
+        for (int g = 0; g < 2 * h->ngroups; ++g) h->gmat_f[g] = (float)h->gmat[g];
+        if (cudaMemcpyAsync(h->dgroups, h->groups, sizeof(GroupD) * h->ngroups, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(h->mtab_d, h->gmat, sizeof(double) * 2 * h->ngroups, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(h->mtab_f, h->gmat_f, sizeof(float) * 2 * h->ngroups, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+            return fail(LBM_ERR_CUDA);
+    }
+    k_mask<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, levelset_view(h), h->flags, h->gidx);
+    k_cutbits<<<grid_for(bx.nbox, 256), 256, 0, st>>>(bx, levelset_view(h), h->flags, h->cnt, h->counters,
                                                        h->status);
     if (cudaGetLastError() != cudaSuccess) return fail(LBM_ERR_CUDA);
     if (scan(h->cnt, h->lstart, bx.nbox, h->scan_scratch, st)) return fail(LBM_ERR_CUDA);
@@ -330,6 +364,48 @@ int lbm_step(lbm_handle *h, int nsteps) {
     if (!h || nsteps < 0) return LBM_ERR_ARG;
     if (!h->initialized) return LBM_ERR_STATE;
     return ops(h).step(h, nsteps);
+}
+
+int lbm_step_graph(lbm_handle *h, int nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    if (!h->initialized || h->timing) return LBM_ERR_STATE;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(h->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_STATE;
+    if (h->graph_exec) {  // the previous graph was launched on this stream; its work is ordered before ours
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    // Record on a private non-blocking stream (the caller's may be the legacy default stream,
+    // which cannot be captured); recording executes nothing, and the graph is then launched on
+    // the caller's stream after its earlier work.
+    if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    const cudaStream_t caller = h->stream;
+    h->stream = h->capture_stream;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->stream = caller;
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    const int rc = ops(h).step(h, nsteps);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    h->stream = caller;
+    if (rc != LBM_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != LBM_OK ? rc : LBM_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    h->graph_exec = exec;
+    CK(cudaGraphLaunch(exec, h->stream));
+    return LBM_OK;
 }
 
 int lbm_fields(lbm_handle *h, double *v, double *F, double *u) {
@@ -453,6 +529,11 @@ int lbm_copy_active(lbm_handle *h, unsigned char *mask) {
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
     timing_fold(h);
+    if (h->graph_exec) {
+        cudaStreamSynchronize(h->stream);
+        cudaGraphExecDestroy(h->graph_exec);
+    }
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
 }
 

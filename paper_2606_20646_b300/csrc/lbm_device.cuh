@@ -8,7 +8,8 @@
 
 namespace tlv {
 
-constexpr int kMaxShapes = 16;
+constexpr int kMaxShapes = LBM_MAX_SHAPES;
+constexpr int kMaxGroups = LBM_MAX_GROUPS;
 constexpr int kMaxBCs = 16;
 constexpr int kLsqCap = 160;      // LSQ stencil capacity per link (active nodes within 3 dx)
 constexpr double kLsqRho2 = 9.0;  // squared stencil radius in lattice units
@@ -103,6 +104,43 @@ __device__ inline double levelset(const ShapeD *__restrict__ shapes, int ns, int
     return best;
 }
 
+// a specimen of a multi-specimen body: its shapes and a box containing it
+struct GroupD {
+    int first, count;
+    double lo[3], hi[3];
+};
+
+// the level set a kernel sees: one body (ngroups == 0), or the union of disjoint groups
+struct LevelSetD {
+    const ShapeD *shapes;
+    int nshapes;
+    const GroupD *groups;
+    int ngroups;
+};
+
+// phi(X) and, optionally, the shape defining it and its group: max over the shapes of one body, or
+// min over the groups whose box contains X of the group's max (+1 outside every box)
+__device__ inline double levelset(const LevelSetD &L, int D, const double X[3], int *which, int *group = nullptr) {
+    if (L.ngroups == 0) {
+        if (group) *group = 0;
+        return levelset(L.shapes, L.nshapes, D, X, which);
+    }
+    double best = 1.0;
+    int w = -1, gb = -1;
+    for (int g = 0; g < L.ngroups; ++g) {
+        const GroupD &G = L.groups[g];
+        bool in = true;
+        for (int a = 0; a < D; ++a) in = in && X[a] >= G.lo[a] && X[a] <= G.hi[a];
+        if (!in) continue;
+        int wg;
+        const double v = levelset(L.shapes + G.first, G.count, D, X, &wg);
+        if (gb < 0 || v < best) { best = v; w = G.first + wg; gb = g; }
+    }
+    if (which) *which = w;
+    if (group) *group = gb < 0 ? 0 : gb;
+    return gb < 0 ? 1.0 : best;
+}
+
 // ---------------------------------------------------------------------------------------------
 // boundary data: ramps s(t), Dirichlet displacement/velocity, nominal traction
 // ---------------------------------------------------------------------------------------------
@@ -151,6 +189,9 @@ __device__ inline void dirichlet_eval(const BCD &bc, int D, const double X[3], d
         }
         break;
     }
+    case 4:  // translation u_D = s(t) vec
+        for (int i = 0; i < D; ++i) out[i] = a * bc.vec[i];
+        break;
     default:
         break;
     }

@@ -45,8 +45,11 @@ struct lbm_handle {
     lbm_grid grid{};
     lbm_options opt{};
     lbm_material mat{};
-    int nshapes = 0, nbc = 0;
+    int nshapes = 0, nbc = 0, ngroups = 0;
     ShapeD shapes[kMaxShapes]{};
+    GroupD groups[kMaxGroups]{};
+    double gmat[2 * kMaxGroups]{};  // (mu, lambda) per group
+    float gmat_f[2 * kMaxGroups]{};
     BCD bcs[kMaxBCs]{};
     bool has_neumann_bc = false;
     cudaStream_t stream = nullptr;
@@ -63,9 +66,15 @@ struct lbm_handle {
     int2 *seg = nullptr;
     unsigned long long *counters = nullptr;
     ShapeD *dshapes = nullptr;
+    GroupD *dgroups = nullptr;
+    uint8_t *gidx = nullptr;         // per-node group index
+    double *mtab_d = nullptr;        // (mu, lambda) per group, FP64 and FP32 copies
+    float *mtab_f = nullptr;
     BCD *dbcs = nullptr;
     int *status = nullptr;
     long long n_active = 0, n_cut = 0, nseg = 0;
+    cudaGraphExec_t graph_exec = nullptr;  // the last lbm_step_graph graph
+    cudaStream_t capture_stream = nullptr; // private stream that lbm_step_graph records on
     // solver storage
     char *sto = nullptr;
     size_t sto_bytes = 0;
@@ -240,12 +249,26 @@ inline bool encode_population_maps(void *base, long long npad, int planes, int K
     return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
 }
 
+inline LevelSetD levelset_view(const lbm_handle *h) {
+    LevelSetD L;
+    L.shapes = h->dshapes;
+    L.nshapes = h->nshapes;
+    L.groups = h->dgroups;
+    L.ngroups = h->ngroups;
+    return L;
+}
+
 // =============================================================================================
 // precision- and dimension-specialised operations
 // =============================================================================================
 
 template <typename real, int D> struct Impl {
     static constexpr int K = D + D * D, Q = 2 * D;
+
+    static const real *mtab(lbm_handle *h) {
+        if constexpr (sizeof(real) == 8) return h->mtab_d;
+        else return h->mtab_f;
+    }
 
     static LinkGeom<real> links(lbm_handle *h) {
         LinkGeom<real> L;
@@ -290,6 +313,8 @@ template <typename real, int D> struct Impl {
         a.mu = (real)h->mat.mu;
         a.lam = (real)h->mat.lambda;
         for (int i = 0; i < 3; ++i) a.bf[i] = (real)h->opt.body_force[i];
+        a.mat = h->ngroups > 0 ? h->gidx : nullptr;
+        a.mtab = h->ngroups > 0 ? mtab(h) : nullptr;
         a.status = h->status;
         return a;
     }
@@ -348,7 +373,7 @@ template <typename real, int D> struct Impl {
         setup_tma(h);
         if (h->nseg == 0) return LBM_OK;
         k_link_build<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
-            h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, h->dshapes, h->nshapes, h->dbcs, h->nbc,
+            h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, levelset_view(h), h->dbcs, h->nbc,
             links(h), h->status);
         CKL();
         return LBM_OK;
@@ -358,8 +383,9 @@ template <typename real, int D> struct Impl {
         const double dt = h->grid.dx / h->opt.c;
         k_init<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
             h->box, h->seg, (int)h->nseg, h->flags, v0, F0, u0, dU0, mode == LBM_INIT_CHARACTERISTIC, h->opt.c, dt,
-            h->mat.mu, h->mat.lambda, h->opt.gamma, h->opt.body_force[0], h->opt.body_force[1], h->opt.body_force[2],
-            static_cast<real *>(h->fA), static_cast<real *>(h->ustar));
+            h->mat.mu, h->mat.lambda, h->gidx, h->ngroups > 0 ? h->mtab_d : nullptr, h->opt.gamma,
+            h->opt.body_force[0], h->opt.body_force[1], h->opt.body_force[2], static_cast<real *>(h->fA),
+            static_cast<real *>(h->ustar));
         CKL();
         return LBM_OK;
     }
@@ -379,6 +405,8 @@ template <typename real, int D> struct Impl {
         a.c = h->opt.c;
         a.mu = h->mat.mu;
         a.lam = h->mat.lambda;
+        a.mat = h->ngroups > 0 ? h->gidx : nullptr;
+        a.mtab = h->ngroups > 0 ? mtab(h) : nullptr;
         a.D = D;
         a.status = h->status;
         EventPair ep;

@@ -153,18 +153,22 @@ __device__ __forceinline__ void set_status(int *st, int bits) {
 // geometry pass (FP64)
 // =============================================================================================
 
-static __global__ void k_mask(Box b, const ShapeD *__restrict__ shapes, int nshapes, uint8_t *flags) {
+// active mask, and the group (specimen) of each active node: its material index
+static __global__ void k_mask(Box b, const LevelSetD ls, uint8_t *flags, uint8_t *mat) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= b.nbox) return;
     int x, y, z;
     node_xyz(b, (int)i, x, y, z);
     double X[3];
     node_X(b, x, y, z, X);
-    flags[i] = (levelset(shapes, nshapes, b.D, X, nullptr) <= 0.0) ? kActive : 0;
+    int g;
+    const bool act = levelset(ls, b.D, X, nullptr, &g) <= 0.0;
+    flags[i] = act ? kActive : 0;
+    mat[i] = act ? (uint8_t)g : 0;
 }
 
 // cut bits (link (m,q) cut iff m + e_q is outside the body or outside a non-periodic box)
-static __global__ void k_cutbits(Box b, const ShapeD *__restrict__ shapes, int nshapes, uint8_t *flags, int *cnt,
+static __global__ void k_cutbits(Box b, const LevelSetD ls, uint8_t *flags, int *cnt,
                           unsigned long long *n_active, int *status) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     bool act = false;
@@ -185,7 +189,7 @@ static __global__ void k_cutbits(Box b, const ShapeD *__restrict__ shapes, int n
                     double X[3];
                     node_X(b, x, y, z, X);
                     X[A] += s * b.dx;
-                    if (!(levelset(shapes, nshapes, b.D, X, nullptr) > 0.0)) set_status(status, kStDomain);
+                    if (!(levelset(ls, b.D, X, nullptr) > 0.0)) set_status(status, kStDomain);
                     bits |= (1u << q);
                 } else if (!(flags[nbr(b, node, x, y, z, q)] & kActive)) {
                     bits |= (1u << q);
@@ -345,7 +349,7 @@ __device__ inline void for_stencil(const Box &b, const uint8_t *__restrict__ fla
 
 template <typename real, int D>
 __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint8_t *flags, uint8_t *dmask,
-                             const int *__restrict__ lstart, const ShapeD *__restrict__ shapes, int nshapes,
+                             const int *__restrict__ lstart, const LevelSetD ls,
                              const BCD *__restrict__ bcs, int nbc, LinkGeom<real> L, int *status) {
     int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (sgi >= nseg) return;
@@ -371,18 +375,18 @@ __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint
         for (int it = 0; it < 60; ++it) {
             double mid = 0.5 * (lo + hi), Xt[3] = {Xm[0], Xm[1], Xm[2]};
             Xt[A] = Xm[A] + mid * b.dx * s;
-            if (levelset(shapes, nshapes, D, Xt, nullptr) <= 0.0) lo = mid; else hi = mid;
+            if (levelset(ls, D, Xt, nullptr) <= 0.0) lo = mid; else hi = mid;
         }
         const double eta = 0.5 * (lo + hi);
         double Xb[3] = {Xm[0], Xm[1], Xm[2]};
         Xb[A] = Xm[A] + eta * b.dx * s;
         int which;
-        levelset(shapes, nshapes, D, Xb, &which);
+        levelset(ls, D, Xb, &which);
         double g[3];
-        shape_phi(shapes[which], D, Xb, g);
+        shape_phi(ls.shapes[which], D, Xb, g);
         double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
         double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};  // Eq. (level-set-normal)
-        int bid = shapes[which].bid, bci = -1;
+        int bid = ls.shapes[which].bid, bci = -1;
         for (int j = 0; j < nbc; ++j)
             if (bcs[j].bid == bid) { bci = j; break; }
         int kind = 0;
@@ -534,8 +538,9 @@ template <int D> __device__ inline void dpiola64(const double *F, const double *
 template <typename real, int D>
 __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint8_t *__restrict__ flags,
                        const double *__restrict__ v0, const double *__restrict__ F0, const double *__restrict__ u0,
-                       const double *__restrict__ dU0, int characteristic, double c, double dt, double mu, double lam,
-                       double gamma, double b0, double b1, double b2, real *f, real *ustar) {
+                       const double *__restrict__ dU0, int characteristic, double c, double dt, double mu_, double lam_,
+                       const uint8_t *__restrict__ mat, const double *__restrict__ mtab, double gamma, double b0, double b1,
+                       double b2, real *f, real *ustar) {
     constexpr int K = D + D * D, Q = 2 * D;
     int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (sgi >= nseg) return;
@@ -550,6 +555,7 @@ __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint
     double U0[K];
     for (int i = 0; i < D; ++i) U0[i] = v0[i * N + node];
     for (int k = 0; k < D * D; ++k) U0[D + k] = F0[k * N + node];
+    const double mu = mtab ? mtab[2 * mat[node]] : mu_, lam = mtab ? mtab[2 * mat[node] + 1] : lam_;
     double Pm[D * D];
     piola<double, D>(U0 + D, mu, lam, Pm);
     const double shift = (sizeof(real) == 4) ? 1.0 : 0.0;  // FP32 stores f - f^eq(0, I)
@@ -623,8 +629,23 @@ template <typename real> struct StepArgs {
     real *vst, *Gst;   // projection steps: v^n and G^n = F^n - I (D and D*D planes)
     real *u0;          // projection steps: u^n (displacement-accumulator layout)
     real dt, c, omega, gamma, mu, lam, bf[3];
+    const uint8_t *mat;  // per-node group of a multi-specimen body (with mtab), else null
+    const real *mtab;    // (mu, lambda) per group, or null: mu and lam above for every node
     int *status;
 };
+
+// material of a node: its group's (mu, lambda) for multi-specimen bodies, else the global one
+template <typename real>
+__device__ __forceinline__ void node_material(const StepArgs<real> &a, long long node, real &mu, real &lam) {
+    if (a.mtab) {
+        const int g = a.mat[node];
+        mu = a.mtab[2 * g];
+        lam = a.mtab[2 * g + 1];
+    } else {
+        mu = a.mu;
+        lam = a.lam;
+    }
+}
 
 // N consecutive values at p (aligned to 16 bytes when N*sizeof(real) is a multiple of 16, else to
 // 8 bytes) as 16- or 8-byte vector loads and stores
@@ -830,7 +851,9 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     gather<real, D, MODE>(a, node, x, y, z, cut, f);
     real v[D], G[D * D], F[D * D], Pk[D * D];
     recover<real, D>(a, f, v, G, F);
-    const real J = piola<real, D>(F, a.mu, a.lam, Pk);
+    real mu, lam;
+    node_material(a, node, mu, lam);
+    const real J = piola<real, D>(F, mu, lam, Pk);
     const int st = check_state<real, D>(v, F, J);
     if (st) set_status(a.status, st);
     const long long P = a.b.npad;
@@ -937,6 +960,8 @@ template <typename real> struct CutArgs {
     const real *un;
     long long npad;
     double t, dt, c, mu, lam;
+    const uint8_t *mat;  // per-node group and (mu, lambda) per group of a multi-specimen body, or null
+    const real *mtab;
     int D;
     int *status;
 };
@@ -1010,7 +1035,8 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         }
     } else {
         // nominal-traction Neumann rows (Eqs. neumann-rows-curved, neumann-compact-curved)
-        const real mu = (real)a.mu, lam = (real)a.lam;
+        const real mu = a.mtab ? a.mtab[2 * a.mat[mnode]] : (real)a.mu;
+        const real lam = a.mtab ? a.mtab[2 * a.mat[mnode] + 1] : (real)a.lam;
         real N[D], t[D - 1][D], g[D - 1][D];
         #pragma unroll
         for (int i = 0; i < D; ++i) N[i] = (real)a.L.Nb[3 * l + i];
@@ -1550,8 +1576,10 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
             F[i * D + B] = G[i * D + B] + one;
             Fr[i * D + B] = Gr[i * D + B] + one;
         }
-    piola<real, D>(F, a.mu, a.lam, Pold);
-    const real J = piola<real, D>(Fr, a.mu, a.lam, Pk);
+    real mu, lam;
+    node_material(a, node, mu, lam);
+    piola<real, D>(F, mu, lam, Pold);
+    const real J = piola<real, D>(Fr, mu, lam, Pk);
     const int st = check_state<real, D>(v, Fr, J);
     if (st) set_status(a.status, st);
     const real Dc = real(D) / a.c;

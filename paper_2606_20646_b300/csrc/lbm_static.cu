@@ -36,7 +36,7 @@ unsigned char *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 struct ShapeTable {
-    ShapeD s[kMaxShapes];
+    ShapeD s[LBM_CENSUS_MAX_SHAPES];
 };
 
 __global__ void k_census_mask(Box b, const __grid_constant__ ShapeTable shapes, int nshapes, unsigned char *scratch) {
@@ -114,7 +114,8 @@ extern "C" int lbm_census_static(const lbm_grid *grid, const lbm_levelset *ls, v
                                  long long *n_cut, long long *n_segments) {
     if (!grid || !ls || !n_active || !n_cut || !n_segments) return LBM_ERR_ARG;
     if ((grid->dim != 2 && grid->dim != 3) || !(grid->dx > 0.0)) return LBM_ERR_ARG;
-    if (ls->nshapes < 0 || ls->nshapes > kMaxShapes || (ls->nshapes > 0 && !ls->shapes)) return LBM_ERR_ARG;
+    if (ls->nshapes < 0 || ls->nshapes > LBM_CENSUS_MAX_SHAPES || (ls->nshapes > 0 && !ls->shapes) || ls->ngroups != 0)
+        return LBM_ERR_ARG;
     Box b{};
     b.D = grid->dim;
     b.nx = grid->n[0];

@@ -166,7 +166,7 @@ struct TmaMaps {
 //   f*_q = (1 - omega) f_q + omega f^eq_q + src_q with omega f^eq_q = base_k +- (omega D/(2Dc)) Phi_A,k
 template <int D>
 __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
-                                               const float us[2 * D], long long l0, bool act) {
+                                               const float us[2 * D], long long l0, bool act, float mu, float lam) {
     constexpr int K = D + D * D, Q = 2 * D;
     float S[K];
     #pragma unroll
@@ -185,9 +185,9 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     for (int k = 0; k < D * D; ++k) F[k] = S[D + k] + ((k / D == k % D) ? 1.0f : 0.0f);
     cofactor<float, D>(F, C);
     const float J = det<float, D>(F);
-    const float sJ = (0.5f * a.lam * (J * J - 1.0f) - a.mu) * (1.0f / J);
+    const float sJ = (0.5f * lam * (J * J - 1.0f) - mu) * (1.0f / J);
     #pragma unroll
-    for (int k = 0; k < D * D; ++k) P[k] = a.mu * F[k] + sJ * C[k];
+    for (int k = 0; k < D * D; ++k) P[k] = mu * F[k] + sJ * C[k];
     float chk = J;
     #pragma unroll
     for (int i = 0; i < D; ++i) chk += v[i];
@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_colli
     // flight; lanes past the end of the last row read a clamped index and never use it
     const int node = sg.x + lane;
     const long long l0pre = __ldg(a.lstart + (node < a.b.npad ? node : a.b.npad - 1));
+    const int gpre = a.mtab ? __ldg(a.mat + (node < a.b.npad ? node : a.b.npad - 1)) : 0;
     __syncwarp();
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
         if (lane == 0) set_status(a.status, kStTimeout);
@@ -335,7 +336,8 @@ __global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_colli
     for (int d = 0; d < 2 * D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
     const long long l0 = (fl & kCutMask) ? l0pre : 0;
     if (act) tma_closure<D>(a, cur, node, x, lane, fl & kCutMask, l0);
-    collide_staged<D>(a, cur, node, lane, fl, us, l0, act);
+    const float mu = a.mtab ? a.mtab[2 * gpre] : a.mu, lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
+    collide_staged<D>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 
 // projection steps, part 1, with TMA staging (FP32)

@@ -81,6 +81,7 @@ class BC:
       affine:        u_D = s(t) A (X - center)
       radial:        u_D = amp s(t) e_R,  e_R = (X - center)/|X - center|
       twist_stretch: u_D = ((R_{s(t) amp} - I) X_perp, s(t) vec[2])  (3D, axis X_3)
+      const:         u_D = s(t) vec  (translation)
     neumann profiles (nominal traction T = P N):
       const:         T = s(t) vec
       radial:        T = amp s(t) e_R
@@ -108,6 +109,22 @@ class BC:
 
 
 @dataclass
+class Group:
+    """One specimen of a multi-specimen body: shapes[first_shape : first_shape + nshapes] (their
+    max is the specimen's level set), a box [lo, hi] containing it, and its material."""
+    first_shape: int
+    nshapes: int
+    lo: Sequence[float]
+    hi: Sequence[float]
+    mu: float
+    lam: float
+
+    def __post_init__(self):
+        self.lo = tuple(float(x) for x in self.lo) + (0.0,) * (3 - len(self.lo))
+        self.hi = tuple(float(x) for x in self.hi) + (0.0,) * (3 - len(self.hi))
+
+
+@dataclass
 class Options:
     c: float = 10.0            # lattice speed dx/dt
     omega: float = 1.8         # BGK relaxation, 0 < omega < 2
@@ -132,6 +149,7 @@ class Problem:
     options: Options
     shapes: List[Shape] = field(default_factory=list)
     bcs: List[BC] = field(default_factory=list)
+    groups: List[Group] = field(default_factory=list)   # several disjoint specimens (empty: one body)
     init_mode: str = "equilibrium"          # or "characteristic"
     v0: Optional[np.ndarray] = None         # (D, *box)
     F0: Optional[np.ndarray] = None         # (D*D, *box)
@@ -482,4 +500,93 @@ def face_touching_box(dim: int, n: int, seed: int) -> Problem:
              BC(1, "neumann", "const", ramp="sin2", t_ramp=0.05, vec=tuple(tr))]
     _rest_fields(p)
     return p
+
+
+def batch_2d(n_spec: int = 96, seed: int = 20260646, side: Sequence[int] = (64, 768), dx: float = 1.0 / 256,
+             width: int = 4992, gap: int = 12, steps: int = 1000, margin: int = 8, t_ramp: float = 0.3,
+             stretch: float = 0.02):
+    """Many 2D specimens of uneven size packed into one box and advanced as one body (a level set
+    with one group per specimen, each with its own material).
+
+    Specimen k: a square of s_k ~ U{side} nodes per edge, with 1-5 elliptic holes (semi-axes
+    U[0.05, 0.2] L, random centres and angles, kept apart from each other and from the edges by
+    rejection), mu ~ U[0.5, 2], lambda/mu ~ U[1, 20].  Left edge clamped (Dirichlet zero), right
+    edge translated by (stretch, 0) with a sin^2 ramp over t_ramp (Dirichlet translation), top, bottom and holes
+    traction-free (Neumann zero); omega = 1.8, gamma = 10, projection every 20 steps; lattice speed
+    c = max(10, 2.5 max_k sqrt(lambda_k + 2 mu_k)), shared by all specimens.  Specimens
+    are shelf-packed left to right, `gap` nodes apart (beyond the 3 dx reach of the LSQ stencils),
+    in a box `width` nodes wide.
+
+    Returns (packed problem, [(specimen problem, (i0, j0)) ...]): each specimen problem is the same
+    specimen alone in its own box, whose node (0, 0) is node (i0, j0) of the packed box, so the two
+    runs see identical node coordinates."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side[0], side[1] + 1, size=n_spec)
+    order = np.argsort(-sides, kind="stable")
+    # shelf packing (largest first)
+    place = {}
+    x = y = gap
+    shelf = 0
+    for k in order:
+        s_ = int(sides[k])
+        if x + s_ + gap > width:
+            x, y = gap, y + shelf + gap
+            shelf = 0
+        place[k] = (x, y)
+        x += s_ + gap
+        shelf = max(shelf, s_)
+    height = y + shelf + gap
+    opts = Options(c=10.0, omega=1.8, gamma=10.0, proj_every=20, proj_iters=50)
+    bcs = [BC(0, "dirichlet", "zero"),
+           BC(1, "dirichlet", "const", ramp="sin2", t_ramp=t_ramp, vec=(stretch, 0.0)),
+           BC(2, "neumann", "zero")]
+    shapes, groups, specs = [], [], []
+    for k in range(n_spec):
+        s_ = int(sides[k])
+        i0, j0 = place[k]
+        L = s_ * dx
+        ox, oy = i0 * dx, j0 * dx                      # lower-left corner of the specimen's nodes
+        xl, xr = ox + 0.2 * dx, ox + (s_ - 0.4) * dx   # edges between node centres
+        yb, yt = oy + 0.3 * dx, oy + (s_ - 0.3) * dx
+        mine = [Shape("halfspace", (xl, 0), (-1.0, 0.0), boundary_id=0),
+                Shape("halfspace", (xr, 0), (1.0, 0.0), boundary_id=1),
+                Shape("halfspace", (0, yb), (0.0, -1.0), boundary_id=2),
+                Shape("halfspace", (0, yt), (0.0, 1.0), boundary_id=2)]
+        holes = []
+        for _ in range(int(rng.integers(1, 6))):
+            for _try in range(200):
+                a, b = rng.uniform(0.05, 0.2, size=2) * L
+                th = rng.uniform(0, 180)
+                c = (ox + rng.uniform(0.25, 0.75) * L, oy + rng.uniform(0.25, 0.75) * L)
+                r = max(a, b)
+                if min(c[0] - xl, xr - c[0], c[1] - yb, yt - c[1]) < r + 6 * dx:
+                    continue
+                if any(np.hypot(c[0] - h[0][0], c[1] - h[0][1]) < r + h[1] + 6 * dx for h in holes):
+                    continue
+                holes.append((c, r))
+                mine.append(Shape("ellipsoid", c, (a, b), rot=rot_z(th), complement=True, boundary_id=2))
+                break
+        mu = float(rng.uniform(0.5, 2.0))
+        lam = float(mu * rng.uniform(1.0, 20.0))
+        groups.append(Group(len(shapes), len(mine), (ox - 2 * dx, oy - 2 * dx), (ox + (s_ + 2) * dx, oy + (s_ + 2) * dx),
+                            mu, lam))
+        shapes.extend(mine)
+        nb = s_ + 2 * margin
+        sp = Problem(name=f"batch_specimen_{k}", dim=2, n=(nb, nb, 1), dx=dx,
+                     origin=((i0 - margin) * dx, (j0 - margin) * dx, 0.0), periodic=(False, False, False),
+                     mu=mu, lam=lam, options=opts, shapes=list(mine), bcs=list(bcs))
+        _rest_fields(sp)
+        sp.steps = steps
+        specs.append((sp, (i0 - margin, j0 - margin)))
+    # one lattice speed for the packed run: 2.5 times the largest longitudinal wave speed at rest,
+    # sqrt(lambda + 2 mu) with rho0 = 1, and at least 10.  The stiffest draws (lambda + 2 mu ~ 42)
+    # blow up at c = 10 and, under this loading, still at c = 2 c_L; 2.16 c_L ran stably.
+    opts.c = max(10.0, 2.5 * max(np.sqrt(g.lam + 2.0 * g.mu) for g in groups))
+    packed = Problem(name=f"batch_2d_{n_spec}", dim=2, n=(width, int(-(-height // 16) * 16), 1), dx=dx,
+                     origin=(0.0, 0.0, 0.0), periodic=(False, False, False), mu=1.0, lam=1.0, options=opts,
+                     shapes=shapes, bcs=list(bcs), groups=groups)
+    _rest_fields(packed)
+    packed.steps = steps
+    packed.meta = dict(sides=sides.tolist(), place=[place[k] for k in range(n_spec)])
+    return packed, specs
 

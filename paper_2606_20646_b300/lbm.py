@@ -36,12 +36,18 @@ class lbm_shape(C.Structure):
                 ("center", C.c_double * 3), ("axes", C.c_double * 3), ("rot", C.c_double * 9), ("p", C.c_double)]
 
 
-class lbm_levelset(C.Structure):
-    _fields_ = [("nshapes", C.c_int), ("shapes", C.POINTER(lbm_shape))]
-
-
 class lbm_material(C.Structure):
     _fields_ = [("mu", C.c_double), ("lambda_", C.c_double)]
+
+
+class lbm_group(C.Structure):
+    _fields_ = [("first_shape", C.c_int), ("nshapes", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("material", lbm_material)]
+
+
+class lbm_levelset(C.Structure):
+    _fields_ = [("nshapes", C.c_int), ("shapes", C.POINTER(lbm_shape)), ("ngroups", C.c_int),
+                ("groups", C.POINTER(lbm_group))]
 
 
 class lbm_bc(C.Structure):
@@ -84,6 +90,7 @@ SIGNATURES = {
     "lbm_sync": (C.c_int, [_vp, _i]),
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
     "lbm_enable_timing": (C.c_int, [_vp, C.c_int]),
+    "lbm_step_graph": (C.c_int, [_vp, C.c_int]),
     "lbm_kernel_times": (C.c_int, [_vp, C.POINTER(lbm_kernel_time)]),
     "lbm_copy_links": (C.c_int, [_vp, C.POINTER(C.c_longlong), _i, _d, _d, _d, _i, _i]),
     "lbm_copy_active": (C.c_int, [_vp, C.POINTER(C.c_ubyte)]),
@@ -145,7 +152,15 @@ def descriptors(p, precision="fp32", host_staging=False):
         for a in range(9):
             s.rot[a] = float(sh.rot.reshape(-1)[a])
         s.p = sh.p
-    ls = lbm_levelset(len(p.shapes), shapes)
+    groups = getattr(p, "groups", None) or []
+    gs = (lbm_group * max(1, len(groups)))()
+    for j, gr in enumerate(groups):
+        G = gs[j]
+        G.first_shape, G.nshapes = int(gr.first_shape), int(gr.nshapes)
+        for a in range(3):
+            G.lo[a], G.hi[a] = float(gr.lo[a]), float(gr.hi[a])
+        G.material = lbm_material(gr.mu, gr.lam)
+    ls = lbm_levelset(len(p.shapes), shapes, len(groups), gs)
     mat = lbm_material(p.mu, p.lam)
     bcs = (lbm_bc * max(1, len(p.bcs)))()
     for j, bc in enumerate(p.bcs):
@@ -163,7 +178,7 @@ def descriptors(p, precision="fp32", host_staging=False):
     opt.c, opt.omega, opt.gamma, opt.theta_F, opt.proj_beta = o.c, o.omega, o.gamma, o.theta_F, o.proj_beta
     for a in range(3):
         opt.body_force[a] = float(o.body_force[a])
-    return g, shapes, ls, mat, bcs, opt
+    return g, (shapes, gs), ls, mat, bcs, opt
 
 
 class Simulation:
@@ -221,6 +236,11 @@ class Simulation:
 
     def step(self, n: int = 1):
         _check(load_library().lbm_step(self.h, int(n)), "lbm_step")
+        return self
+
+    def step_graph(self, n: int):
+        """n steps captured as one CUDA graph and launched once (lbm_step_graph)."""
+        _check(load_library().lbm_step_graph(self.h, int(n)), "lbm_step_graph")
         return self
 
     def fields(self, out=None):

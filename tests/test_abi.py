@@ -62,3 +62,27 @@ def test_geometry_bytes_and_validation_without_gpu(lib):
     bcs[0].profile = 1
     assert lib.lbm_create(C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None,
                           C.byref(h)) == -1
+
+
+def test_group_descriptors_validated_without_gpu(lib):
+    """Multi-specimen level sets: group ranges, boxes and materials are checked before any device
+    work; the allocation-free census takes single bodies only."""
+    from paper_2606_20646_b300 import inputs as I, lbm
+    packed, _ = I.batch_2d(n_spec=3, side=(40, 48), width=192, seed=3)
+    g, shapes, ls, mat, bcs, opt = lbm.descriptors(packed)
+    h = C.c_void_p()
+    args = lambda: (C.byref(g), C.byref(ls), C.byref(mat), bcs, len(packed.bcs), C.byref(opt), None, 0, None,
+                    C.byref(h))
+    assert ls.ngroups == 3
+    assert lib.lbm_create(*args()) == -4           # valid descriptors, no storage given
+    gs = shapes[1]
+    gs[1].first_shape = len(packed.shapes)          # group past the shape list
+    assert lib.lbm_create(*args()) == -1
+    gs[1].first_shape = 0
+    gs[2].material.mu = -1.0                        # invalid group material
+    assert lib.lbm_create(*args()) == -1
+    gs[2].material.mu = 1.0
+    gs[0].lo[0], gs[0].hi[0] = 1.0, 0.0             # empty box
+    assert lib.lbm_create(*args()) == -1
+    n = [C.c_longlong(0) for _ in range(3)]
+    assert lib.lbm_census_static(C.byref(g), C.byref(ls), None, *[C.byref(x) for x in n]) == -1
