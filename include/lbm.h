@@ -181,6 +181,9 @@ typedef struct lbm_options {
     double theta_F;   /* F repair weight, 0 < theta_F <= 1 (Eq. projection-F-repair-weight) */
     double proj_beta; /* Jacobi damping, 0 < beta <= 1                                    */
     double body_force[3];
+    int adjoint;      /* non-zero: reserve a per-node shear-modulus field and the reverse-mode
+                         buffers of lbm_adjoint_* (Dirichlet-only bodies)                    */
+    int reserved;
 } lbm_options;
 
 typedef struct lbm_info {
@@ -257,6 +260,46 @@ int lbm_step(lbm_handle *h, int nsteps);
  * initialised, timing on, or the stream capturing), LBM_ERR_CUDA (stream creation, capture,
  * instantiation or launch failed). */
 int lbm_step_graph(lbm_handle *h, int nsteps);
+
+/* ---- parameters, saved states and reverse mode --------------------------------------------
+ * No counterpart in the paper: gradients of a loss on the final displacement with respect to a
+ * per-node shear modulus and the body force, by the discrete adjoint of the steps (reverse
+ * sweep over saved states).  Bodies with Neumann links (whose steps contain the Newton
+ * inversion and the projection) are not supported: lbm_adjoint_begin returns LBM_ERR_STATE. */
+
+/* Per-node shear modulus mu (n_box values in box order, device or host memory; values at
+ * inactive nodes are ignored), replacing the material's mu (lambda is kept).  Needs
+ * options.adjoint.  Takes effect at the next lbm_set_initial or step.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_STATE (no storage or options.adjoint not set), LBM_ERR_CUDA. */
+int lbm_set_mu_field(lbm_handle *h, const double *mu);
+
+/* Body force b (3 values, host memory), replacing options.body_force for later steps. */
+int lbm_set_body_force(lbm_handle *h, const double *b);
+
+/* Bytes of one saved state: populations, u*, u^n, the link reconstruction values and Newton
+ * states, and the step counter.  A saved state restores the simulation exactly. */
+int lbm_state_bytes(const lbm_handle *h, size_t *bytes);
+
+/* Save the current state to / restore it from caller device memory (lbm_state_bytes bytes,
+ * 256-byte aligned).  Enqueued on the handle's stream; lbm_load_state synchronises it to read
+ * the step counter.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not initialised), LBM_ERR_CUDA. */
+int lbm_save_state(lbm_handle *h, void *dst);
+int lbm_load_state(lbm_handle *h, const void *src);
+
+/* Start a reverse sweep at the current state (after N steps): grad_u (D*n_box doubles in device
+ * memory, box order) is dL/du at t_N for u = u* + dt/2 v as lbm_fields reports it.  Clears the
+ * gradient accumulators.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not initialised, options.adjoint
+ * not set, Neumann links present), LBM_ERR_CUDA. */
+int lbm_adjoint_begin(lbm_handle *h, const double *grad_u);
+
+/* Reverse one step: the k-th call after lbm_adjoint_begin reverses step N-k, and `state` must be
+ * the state saved after N-k steps (before that step).  Accumulates the gradients.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_STATE (no sweep in progress, or all steps reversed), LBM_ERR_CUDA. */
+int lbm_adjoint_step(lbm_handle *h, const void *state);
+
+/* Accumulated gradients: dL/dmu per box node (n_box doubles, device memory; zero at inactive
+ * nodes) and dL/db (3 doubles, host memory); either may be null.  Synchronises. */
+int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b);
 
 /* Writes v, F (from U^num, Eq. state-recovery-general) and u = u* + dt/2 v
  * (Eq. u-recovery-general) at the current time.  Any pointer may be NULL. */

@@ -67,6 +67,7 @@ def lib():
         _lib.orc_create.argtypes = [C.POINTER(_Problem), i]
         _lib.orc_destroy.argtypes = [vp]
         _lib.orc_set_initial.argtypes = [vp, C.c_int, d, d, d, d]
+        _lib.orc_set_mu_field.argtypes = [vp, d]
         _lib.orc_step.argtypes = [vp, C.c_int]
         _lib.orc_fields.argtypes = [vp, d, d, d]
         _lib.orc_populations.argtypes = [vp, d]
@@ -161,6 +162,17 @@ class Oracle:
 
     def step(self, n: int) -> int:
         return lib().orc_step(self.h, int(n))
+
+    def set_mu_field(self, mu):
+        """Per-node shear modulus (box-shaped array, box order), replacing p.mu; call before
+        set_initial.  None restores p.mu."""
+        if mu is None:
+            lib().orc_set_mu_field(self.h, None)
+        else:
+            a = _f64(np.asarray(mu).reshape(-1))
+            assert a.size == self.N
+            lib().orc_set_mu_field(self.h, _dp(a))
+        return self
 
     def fields(self):
         D, N = self.D, self.N

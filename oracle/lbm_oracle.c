@@ -96,7 +96,11 @@ typedef struct {
     long step;
     int status;
     double tproj; /* time level of the projection's displacement anchors */
+    double *mu_node; /* per-node shear modulus (N), or NULL: p.mu everywhere */
 } orc_state;
+
+/* shear modulus at node m */
+static double mu_at(const orc_state *s, long m) { return s->mu_node ? s->mu_node[m] : s->p.mu; }
 
 /* ------------------------------------------------------------------------- */
 /* small dense helpers                                                        */
@@ -763,6 +767,20 @@ static int build_stencil(orc_state *s, orc_link *L)
     return r;
 }
 
+/* Per-node shear modulus (N values in box order), replacing p.mu; NULL restores p.mu. */
+int orc_set_mu_field(orc_state *s, const double *mu)
+{
+    if (!mu) {
+        free(s->mu_node);
+        s->mu_node = NULL;
+        return 0;
+    }
+    if (!s->mu_node) s->mu_node = malloc(sizeof(double) * s->N);
+    if (!s->mu_node) return ORC_ENOMEM;
+    memcpy(s->mu_node, mu, sizeof(double) * s->N);
+    return 0;
+}
+
 void orc_destroy(orc_state *s)
 {
     if (!s) return;
@@ -772,6 +790,7 @@ void orc_destroy(orc_state *s)
     }
     free(s->links);
     free(s->active);
+    free(s->mu_node);
     free(s->f);
     free(s->fnew);
     free(s->ustar);
@@ -897,7 +916,7 @@ int orc_set_initial(orc_state *s, int characteristic, const double *v0, const do
         for (int i = 0; i < D; i++) U0[i] = v0[i * N + m];
         for (int k = 0; k < D * D; k++) U0[D + k] = F0[k * N + m];
         double feq[6 * 12];
-        orc_feq(D, c, s->p.mu, s->p.lam, U0, feq);
+        orc_feq(D, c, mu_at(s, m), s->p.lam, U0, feq);
         double *fm = s->f + (size_t)m * Q * K;
         for (int j = 0; j < Q * K; j++) fm[j] = feq[j];
         for (int i = 0; i < D; i++) s->ustar[m * D + i] = u0[i * N + m] - 0.5 * dt * v0[i * N + m];
@@ -922,7 +941,7 @@ int orc_set_initial(orc_state *s, int characteristic, const double *v0, const do
         for (int k = 0; k < K; k++) Ut[k] = 0.0;
         for (int i = 0; i < D; i++) Ut[i] = s->p.b[i] - s->p.gamma * U0[i];
         for (int A = 0; A < D; A++) {
-            flux_jvp(D, s->p.mu, s->p.lam, U0, dU + A * K, dPhi);
+            flux_jvp(D, mu_at(s, m), s->p.lam, U0, dU + A * K, dPhi);
             for (int k = 0; k < K; k++) Ut[k] -= dPhi[A * K + k];
         }
         /* f_q -= dt/2 (f^eq)'(U0)[Z_q],  Z_q = d_t U0 + c e_qA d_A U0 (Eq. feq-derivative-general) */
@@ -933,7 +952,7 @@ int orc_set_initial(orc_state *s, int characteristic, const double *v0, const do
                 for (int A = 0; A < D; A++) Z[k] += c * edir(q, A) * dU[A * K + k];
             }
             double dPz[3 * 12];
-            flux_jvp(D, s->p.mu, s->p.lam, U0, Z, dPz);
+            flux_jvp(D, mu_at(s, m), s->p.lam, U0, Z, dPz);
             for (int k = 0; k < K; k++) {
                 double sacc = 0.0;
                 for (int A = 0; A < D; A++) sacc += edir(q, A) * dPz[A * K + k];
@@ -1050,7 +1069,7 @@ static void one_step(orc_state *s)
 {
     int D = s->D, K = s->K, Q = s->Q;
     long N = s->N;
-    double dt = s->dt, c = s->p.c, mu = s->p.mu, lam = s->p.lam;
+    double dt = s->dt, c = s->p.c, lam = s->p.lam;
     double t = s->step * dt;
     const double *b = s->p.b;
     /* recover U^num,n and u^n */
@@ -1077,8 +1096,8 @@ static void one_step(orc_state *s)
             double Uo[12], Ur[12], fo[6 * 12], fr[6 * 12];
             for (int k = 0; k < K; k++) Uo[k] = Ur[k] = s->U[m * K + k];
             for (int k = 0; k < D * D; k++) Ur[D + k] = Fr[m * D * D + k];
-            orc_feq(D, c, mu, lam, Uo, fo);
-            orc_feq(D, c, mu, lam, Ur, fr);
+            orc_feq(D, c, mu_at(s, m), lam, Uo, fo);
+            orc_feq(D, c, mu_at(s, m), lam, Ur, fr);
             double *fm = s->f + (size_t)m * Q * K;
             for (int j = 0; j < Q * K; j++) fm[j] += fr[j] - fo[j]; /* Eq. projection-population-repair */
             for (int k = 0; k < D * D; k++) s->U[m * K + D + k] = Fr[m * D * D + k];
@@ -1093,7 +1112,7 @@ static void one_step(orc_state *s)
         if (!(J > 0.0)) s->status |= ORC_ST_JACOBIAN;
         for (int k = 0; k < K; k++)
             if (!isfinite(Um[k])) s->status |= ORC_ST_NONFINITE;
-        collide(D, c, s->p.omega, dt, s->p.gamma, b, mu, lam, Um, s->f + (size_t)m * Q * K);
+        collide(D, c, s->p.omega, dt, s->p.gamma, b, mu_at(s, m), lam, Um, s->f + (size_t)m * Q * K);
         for (int i = 0; i < D; i++) s->ustar[m * D + i] = s->u[m * D + i] + 0.5 * dt * Um[i];
     }
     if (proj) {
@@ -1145,11 +1164,11 @@ static void one_step(orc_state *s)
                 }
             neumann_traction(bc, D, L->Xb, th, T);
             double h[3] = {L->h[0], L->h[1], L->h[2]};
-            if (orc_newton(D, mu, lam, L->Nb, &g[0][0], &L->t[0][0], T, h) < 0) s->status |= ORC_ST_NEWTON;
+            if (orc_newton(D, mu_at(s, L->m), lam, L->Nb, &g[0][0], &L->t[0][0], T, h) < 0) s->status |= ORC_ST_NEWTON;
             else for (int i = 0; i < 3; i++) L->h[i] = h[i];
             double Fb[9], Pb[9];
             fb_of_h(D, L->h, L->Nb, &g[0][0], &L->t[0][0], Fb);
-            orc_piola(D, mu, lam, Fb, Pb);
+            orc_piola(D, mu_at(s, L->m), lam, Fb, Pb);
             for (int i = 0; i < D; i++) {
                 double dP = 0.0;
                 for (int B = 0; B < D; B++) dP += ((B == A) ? -sg : 0.0) * Pb[i * D + B];

@@ -87,7 +87,43 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->dA = h->dB = h->resid = h->vst = h->Gst = nullptr;
     }
     h->staging = h->opt.host_staging ? c.take<double>((size_t)(2 * D + D * D + D * K) * h->box.nbox) : nullptr;
+    if (h->opt.adjoint) {
+        h->mu_field = c.take<char>((size_t)np * rs);
+        h->adj_g[0] = c.take<char>((size_t)Q * K * np * rs);
+        h->adj_g[1] = c.take<char>((size_t)Q * K * np * rs);
+        h->adj_mubar = c.take<double>((size_t)np);
+        h->adj_lu = c.take<double>((size_t)D * np);
+        h->adj_bbar = c.take<double>(4);
+    } else {
+        h->mu_field = h->adj_g[0] = h->adj_g[1] = nullptr;
+        h->adj_mubar = h->adj_lu = h->adj_bbar = nullptr;
+    }
     *bytes = c.off;
+}
+
+// saved state: a header (step, phase), the stored populations, u*, u^n, the reconstructed link
+// values and the Newton states of the links
+struct StateLayout {
+    size_t pop, ustar, un, rec, lh, bytes;
+};
+static StateLayout state_layout(const lbm_handle *h) {
+    Carver c{nullptr};
+    const size_t np = (size_t)h->box.npad, nc = (size_t)std::max<long long>(h->n_cut, 1);
+    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
+    StateLayout L;
+    c.take<char>(256);
+    L.pop = c.off;
+    c.take<char>((size_t)Q * K * np * rs);
+    L.ustar = c.off;
+    c.take<char>((size_t)D * np * 8);
+    L.un = c.off;
+    c.take<char>((size_t)(D == 3 ? 32 : 16) * np);
+    L.rec = c.off;
+    c.take<char>((size_t)K * nc * rs);
+    L.lh = c.off;
+    c.take<char>((size_t)3 * nc * rs);
+    L.bytes = c.off;
+    return L;
 }
 
 // =============================================================================================
@@ -405,6 +441,107 @@ int lbm_step_graph(lbm_handle *h, int nsteps) {
     }
     h->graph_exec = exec;
     CK(cudaGraphLaunch(exec, h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_mu_field(lbm_handle *h, const double *mu) {
+    if (!h || !mu) return LBM_ERR_ARG;
+    if (!h->bound || !h->opt.adjoint) return LBM_ERR_STATE;
+    const size_t n = (size_t)h->box.nbox;
+    // stage the FP64 field in the first gradient buffer (n doubles fit in its Q*K*npad values),
+    // then convert into the field in the population precision
+    double *tmp = reinterpret_cast<double *>(h->adj_g[0]);
+    CK(cudaMemcpyAsync(tmp, mu, n * sizeof(double), is_device_ptr(mu) ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyHostToDevice, h->stream));
+    CK(convert_field(tmp, h->mu_field, n, h->real_size, h->stream));
+    h->mu_field_on = true;
+    return LBM_OK;
+}
+
+int lbm_set_body_force(lbm_handle *h, const double *b) {
+    if (!h || !b) return LBM_ERR_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(b[i])) return LBM_ERR_ARG;
+        h->opt.body_force[i] = i < h->D ? b[i] : 0.0;
+    }
+    return LBM_OK;
+}
+
+int lbm_state_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_ERR_ARG;
+    *bytes = state_layout(h).bytes;
+    return LBM_OK;
+}
+
+int lbm_save_state(lbm_handle *h, void *dst) {
+    if (!h || !dst || (reinterpret_cast<uintptr_t>(dst) % kAlign)) return LBM_ERR_ARG;
+    if (!h->initialized) return LBM_ERR_STATE;
+    const StateLayout L = state_layout(h);
+    char *d = static_cast<char *>(dst);
+    const size_t np = (size_t)h->box.npad, nc = (size_t)h->n_cut;
+    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
+    long long hdr[2] = {h->step, h->phase};
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(d, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d + L.pop, h->fA, (size_t)Q * K * np * rs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d + L.ustar, h->ustar, (size_t)D * np * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d + L.un, h->un, (size_t)(D == 3 ? 32 : 16) * np, cudaMemcpyDeviceToDevice, st));
+    if (nc) {
+        CK(cudaMemcpyAsync(d + L.rec, h->l_rec, (size_t)K * nc * rs, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(d + L.lh, h->l_h, (size_t)3 * nc * rs, cudaMemcpyDeviceToDevice, st));
+    }
+    // the header comes from this stack frame: wait until it has been read
+    CK(cudaStreamSynchronize(st));
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_handle *h, const void *src) {
+    if (!h || !src || (reinterpret_cast<uintptr_t>(src) % kAlign)) return LBM_ERR_ARG;
+    if (!h->bound) return LBM_ERR_STATE;
+    const StateLayout L = state_layout(h);
+    const char *s = static_cast<const char *>(src);
+    const size_t np = (size_t)h->box.npad, nc = (size_t)h->n_cut;
+    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
+    long long hdr[2] = {0, 0};
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(hdr, s, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->fA, s + L.pop, (size_t)Q * K * np * rs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->ustar, s + L.ustar, (size_t)D * np * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->un, s + L.un, (size_t)(D == 3 ? 32 : 16) * np, cudaMemcpyDeviceToDevice, st));
+    if (nc) {
+        CK(cudaMemcpyAsync(h->l_rec, s + L.rec, (size_t)K * nc * rs, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->l_h, s + L.lh, (size_t)3 * nc * rs, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (hdr[0] < 0 || (hdr[1] != 0 && hdr[1] != 1)) return LBM_ERR_ARG;
+    h->step = hdr[0];
+    h->phase = (int)hdr[1];
+    h->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_adjoint_begin(lbm_handle *h, const double *grad_u) {
+    if (!h || !grad_u) return LBM_ERR_ARG;
+    if (!h->initialized || !h->opt.adjoint || h->n_neu > 0 || h->step < 1) return LBM_ERR_STATE;
+    return ops(h).adjoint_begin(h, grad_u);
+}
+
+int lbm_adjoint_step(lbm_handle *h, const void *state) {
+    if (!h || !state || (reinterpret_cast<uintptr_t>(state) % kAlign)) return LBM_ERR_ARG;
+    if (!h->opt.adjoint || h->adj_next < 0) return LBM_ERR_STATE;
+    return ops(h).adjoint_step(h, static_cast<const char *>(state) + state_layout(h).pop);
+}
+
+int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->opt.adjoint) return LBM_ERR_STATE;
+    cudaStream_t st = h->stream;
+    if (grad_mu) CK(gather_box(h->adj_mubar, grad_mu, h->box.nbox, st));
+    double b[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(b, h->adj_bbar, sizeof(b), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (grad_b)
+        for (int i = 0; i < 3; ++i) grad_b[i] = b[i];
     return LBM_OK;
 }
 

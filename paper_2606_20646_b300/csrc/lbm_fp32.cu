@@ -17,9 +17,15 @@ int step_any(lbm_handle *h, int n) { return h->D == 2 ? step<2>(h, n) : step<3>(
 int fields_any(lbm_handle *h, double *v, double *F, double *u) {
     return h->D == 2 ? fields<2>(h, v, F, u) : fields<3>(h, v, F, u);
 }
+int adjoint_begin_any(lbm_handle *h, const double *gu) {
+    return h->D == 2 ? Impl<float, 2>::adjoint_begin(h, gu) : Impl<float, 3>::adjoint_begin(h, gu);
+}
+int adjoint_step_any(lbm_handle *h, const void *pop) {
+    return h->D == 2 ? Impl<float, 2>::adjoint_step(h, pop) : Impl<float, 3>::adjoint_step(h, pop);
+}
 }  // namespace
 
 const PrecOps &ops_fp32() {
-    static const PrecOps ops = {link_build_any, init_any, step_any, fields_any};
+    static const PrecOps ops = {link_build_any, init_any, step_any, fields_any, adjoint_begin_any, adjoint_step_any};
     return ops;
 }

@@ -17,9 +17,15 @@ int step_any(lbm_handle *h, int n) { return h->D == 2 ? step<2>(h, n) : step<3>(
 int fields_any(lbm_handle *h, double *v, double *F, double *u) {
     return h->D == 2 ? fields<2>(h, v, F, u) : fields<3>(h, v, F, u);
 }
+int adjoint_begin_any(lbm_handle *h, const double *gu) {
+    return h->D == 2 ? Impl<double, 2>::adjoint_begin(h, gu) : Impl<double, 3>::adjoint_begin(h, gu);
+}
+int adjoint_step_any(lbm_handle *h, const void *pop) {
+    return h->D == 2 ? Impl<double, 2>::adjoint_step(h, pop) : Impl<double, 3>::adjoint_step(h, pop);
+}
 }  // namespace
 
 const PrecOps &ops_fp64() {
-    static const PrecOps ops = {link_build_any, init_any, step_any, fields_any};
+    static const PrecOps ops = {link_build_any, init_any, step_any, fields_any, adjoint_begin_any, adjoint_step_any};
     return ops;
 }

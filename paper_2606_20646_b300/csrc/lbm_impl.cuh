@@ -17,6 +17,7 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
+#include "lbm_adjoint.cuh"
 
 using namespace tlv;
 
@@ -74,6 +75,13 @@ struct lbm_handle {
     int *status = nullptr;
     long long n_active = 0, n_cut = 0, nseg = 0;
     cudaGraphExec_t graph_exec = nullptr;  // the last lbm_step_graph graph
+    // reverse mode (options.adjoint)
+    void *mu_field = nullptr;       // per-node shear modulus (population precision)
+    bool mu_field_on = false;
+    void *adj_g[2] = {nullptr, nullptr};  // gbar of consecutive steps (Q*K planes each)
+    double *adj_mubar = nullptr, *adj_bbar = nullptr, *adj_lu = nullptr;
+    int adj_cur = 0;                // adj_g[adj_cur] holds gbar of the last reversed step
+    long long adj_next = -1;        // step the next lbm_adjoint_step reverses (-1: no sweep)
     cudaStream_t capture_stream = nullptr; // private stream that lbm_step_graph records on
     // solver storage
     char *sto = nullptr;
@@ -121,6 +129,22 @@ struct lbm_handle {
         if (e_ != cudaSuccess) return LBM_ERR_CUDA;        \
     } while (0)
 
+static __global__ void k_convert_field(const double *__restrict__ in, void *out, long long n, int rs) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (rs == 8) static_cast<double *>(out)[i] = in[i];
+    else static_cast<float *>(out)[i] = (float)in[i];
+}
+
+// a box-ordered FP64 field into a field of the population precision (same node indices)
+inline cudaError_t convert_field(const double *in, void *out, long long n, int rs, cudaStream_t st) {
+    k_convert_field<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, rs);
+    return cudaGetLastError();
+}
+
+// the first n values of a node-indexed FP64 array to caller memory (device or host)
+inline cudaError_t gather_box(const double *in, double *out, long long n, cudaStream_t st);
+
 inline bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -129,6 +153,11 @@ inline bool is_device_ptr(const void *p) {
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+inline cudaError_t gather_box(const double *in, double *out, long long n, cudaStream_t st) {
+    return cudaMemcpyAsync(out, in, (size_t)n * sizeof(double),
+                           is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
 }
 
 inline unsigned grid_for(long long n, int per_block) { return (unsigned)((n + per_block - 1) / per_block); }
@@ -315,6 +344,7 @@ template <typename real, int D> struct Impl {
         for (int i = 0; i < 3; ++i) a.bf[i] = (real)h->opt.body_force[i];
         a.mat = h->ngroups > 0 ? h->gidx : nullptr;
         a.mtab = h->ngroups > 0 ? mtab(h) : nullptr;
+        a.mu_field = h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr;
         a.status = h->status;
         return a;
     }
@@ -383,7 +413,8 @@ template <typename real, int D> struct Impl {
         const double dt = h->grid.dx / h->opt.c;
         k_init<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
             h->box, h->seg, (int)h->nseg, h->flags, v0, F0, u0, dU0, mode == LBM_INIT_CHARACTERISTIC, h->opt.c, dt,
-            h->mat.mu, h->mat.lambda, h->gidx, h->ngroups > 0 ? h->mtab_d : nullptr, h->opt.gamma,
+            h->mat.mu, h->mat.lambda, h->gidx, h->ngroups > 0 ? h->mtab_d : nullptr,
+            h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr, h->opt.gamma,
             h->opt.body_force[0], h->opt.body_force[1], h->opt.body_force[2], static_cast<real *>(h->fA),
             static_cast<real *>(h->ustar));
         CKL();
@@ -407,6 +438,7 @@ template <typename real, int D> struct Impl {
         a.lam = h->mat.lambda;
         a.mat = h->ngroups > 0 ? h->gidx : nullptr;
         a.mtab = h->ngroups > 0 ? mtab(h) : nullptr;
+        a.mu_field = h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr;
         a.D = D;
         a.status = h->status;
         EventPair ep;
@@ -511,6 +543,54 @@ template <typename real, int D> struct Impl {
             h->phase = 1;
             h->step++;
         }
+        return LBM_OK;
+    }
+
+    static AdjArgs<real> adj_args(lbm_handle *h, int in, double th) {
+        AdjArgs<real> j;
+        j.g_in = static_cast<const real *>(h->adj_g[in]);
+        j.g_out = static_cast<real *>(h->adj_g[in ^ 1]);
+        j.mubar = h->adj_mubar;
+        j.bbar = h->adj_bbar;
+        j.lu = h->adj_lu;
+        j.grad_u = nullptr;
+        j.nbox = h->box.nbox;
+        j.th = th;
+        j.L = links(h);
+        j.bcs = h->dbcs;
+        return j;
+    }
+
+    // seed of a reverse sweep at the current state (after h->step steps)
+    static int adjoint_begin(lbm_handle *h, const double *grad_u) {
+        const size_t np = (size_t)h->box.npad;
+        CK(cudaMemsetAsync(h->adj_mubar, 0, np * sizeof(double), h->stream));
+        CK(cudaMemsetAsync(h->adj_bbar, 0, 4 * sizeof(double), h->stream));
+        CK(cudaMemsetAsync(h->adj_g[0], 0, (size_t)Q * K * np * sizeof(real), h->stream));
+        CK(cudaMemsetAsync(h->adj_g[1], 0, (size_t)Q * K * np * sizeof(real), h->stream));
+        StepArgs<real> a = step_args(h);
+        AdjArgs<real> j = adj_args(h, 1, 0.0);  // seed writes adj_g[0]
+        j.grad_u = grad_u;
+        k_adj_seed<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(a, j, h->adj_lu);
+        CKL();
+        h->adj_cur = 0;
+        h->adj_next = h->step - 1;
+        return LBM_OK;
+    }
+
+    // reverse of step n = h->adj_next from the state saved before it (populations at `pop`)
+    static int adjoint_step(lbm_handle *h, const void *pop) {
+        const long long n = h->adj_next;
+        const double dt = h->grid.dx / h->opt.c;
+        StepArgs<real> a = step_args(h);
+        a.fsrc = static_cast<const real *>(pop);
+        AdjArgs<real> j = adj_args(h, h->adj_cur, (n - 1) * dt + 0.5 * dt);
+        const unsigned g = grid_for(h->nseg, 4);
+        if (n == 0) k_adj_step<real, D, 0><<<g, 128, 0, h->stream>>>(a, j);
+        else k_adj_step<real, D, 1><<<g, 128, 0, h->stream>>>(a, j);
+        CKL();
+        h->adj_cur ^= 1;
+        h->adj_next = n - 1;
         return LBM_OK;
     }
 

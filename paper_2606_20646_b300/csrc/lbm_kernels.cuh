@@ -539,8 +539,9 @@ template <typename real, int D>
 __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint8_t *__restrict__ flags,
                        const double *__restrict__ v0, const double *__restrict__ F0, const double *__restrict__ u0,
                        const double *__restrict__ dU0, int characteristic, double c, double dt, double mu_, double lam_,
-                       const uint8_t *__restrict__ mat, const double *__restrict__ mtab, double gamma, double b0, double b1,
-                       double b2, real *f, real *ustar) {
+                       const uint8_t *__restrict__ mat, const double *__restrict__ mtab,
+                       const real *__restrict__ mu_field, double gamma, double b0, double b1, double b2, real *f,
+                       real *ustar) {
     constexpr int K = D + D * D, Q = 2 * D;
     int sgi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (sgi >= nseg) return;
@@ -555,7 +556,8 @@ __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint
     double U0[K];
     for (int i = 0; i < D; ++i) U0[i] = v0[i * N + node];
     for (int k = 0; k < D * D; ++k) U0[D + k] = F0[k * N + node];
-    const double mu = mtab ? mtab[2 * mat[node]] : mu_, lam = mtab ? mtab[2 * mat[node] + 1] : lam_;
+    const double mu = mu_field ? (double)mu_field[node] : (mtab ? mtab[2 * mat[node]] : mu_);
+    const double lam = mtab ? mtab[2 * mat[node] + 1] : lam_;
     double Pm[D * D];
     piola<double, D>(U0 + D, mu, lam, Pm);
     const double shift = (sizeof(real) == 4) ? 1.0 : 0.0;  // FP32 stores f - f^eq(0, I)
@@ -631,10 +633,12 @@ template <typename real> struct StepArgs {
     real dt, c, omega, gamma, mu, lam, bf[3];
     const uint8_t *mat;  // per-node group of a multi-specimen body (with mtab), else null
     const real *mtab;    // (mu, lambda) per group, or null: mu and lam above for every node
+    const real *mu_field;  // per-node shear modulus replacing mu, or null
     int *status;
 };
 
-// material of a node: its group's (mu, lambda) for multi-specimen bodies, else the global one
+// material of a node: its group's (mu, lambda) for multi-specimen bodies, else the global one;
+// a per-node shear-modulus field replaces mu
 template <typename real>
 __device__ __forceinline__ void node_material(const StepArgs<real> &a, long long node, real &mu, real &lam) {
     if (a.mtab) {
@@ -645,6 +649,7 @@ __device__ __forceinline__ void node_material(const StepArgs<real> &a, long long
         mu = a.mu;
         lam = a.lam;
     }
+    if (a.mu_field) mu = a.mu_field[node];
 }
 
 // N consecutive values at p (aligned to 16 bytes when N*sizeof(real) is a multiple of 16, else to
@@ -962,6 +967,7 @@ template <typename real> struct CutArgs {
     double t, dt, c, mu, lam;
     const uint8_t *mat;  // per-node group and (mu, lambda) per group of a multi-specimen body, or null
     const real *mtab;
+    const real *mu_field;  // per-node shear modulus, or null
     int D;
     int *status;
 };
@@ -1035,7 +1041,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         }
     } else {
         // nominal-traction Neumann rows (Eqs. neumann-rows-curved, neumann-compact-curved)
-        const real mu = a.mtab ? a.mtab[2 * a.mat[mnode]] : (real)a.mu;
+        const real mu = a.mu_field ? a.mu_field[mnode] : (a.mtab ? a.mtab[2 * a.mat[mnode]] : (real)a.mu);
         const real lam = a.mtab ? a.mtab[2 * a.mat[mnode] + 1] : (real)a.lam;
         real N[D], t[D - 1][D], g[D - 1][D];
         #pragma unroll

@@ -8,6 +8,8 @@ struct PrecOps {
     int (*init)(lbm_handle *, int, const double *, const double *, const double *, const double *);
     int (*step)(lbm_handle *, int);
     int (*fields)(lbm_handle *, double *, double *, double *);
+    int (*adjoint_begin)(lbm_handle *, const double *);
+    int (*adjoint_step)(lbm_handle *, const void *);
 };
 
 const PrecOps &ops_fp64();

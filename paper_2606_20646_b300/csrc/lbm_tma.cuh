@@ -336,7 +336,9 @@ __global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_colli
     for (int d = 0; d < 2 * D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
     const long long l0 = (fl & kCutMask) ? l0pre : 0;
     if (act) tma_closure<D>(a, cur, node, x, lane, fl & kCutMask, l0);
-    const float mu = a.mtab ? a.mtab[2 * gpre] : a.mu, lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
+    float mu = a.mtab ? a.mtab[2 * gpre] : a.mu;
+    const float lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
+    if (a.mu_field) mu = a.mu_field[node];
     collide_staged<D>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 

@@ -590,3 +590,31 @@ def batch_2d(n_spec: int = 96, seed: int = 20260646, side: Sequence[int] = (64, 
     packed.meta = dict(sides=sides.tolist(), place=[place[k] for k in range(n_spec)])
     return packed, specs
 
+
+def inclusion_cube(n: int = 128, steps: int = 3000, lam: float = 2.0, b: Sequence[float] = (0.0, 0.0, -0.1)):
+    """Unit cube whose six faces are clamped (velocity-Dirichlet zero), the body a box inset by
+    0.3 dx so that every box node is active and the links leaving the box are cut links; constant
+    body force b; c = 10, omega = 1.8, gamma = 10.  meta["mu_target"]: shear modulus 2 inside the
+    sphere of radius 0.25 at the centre and 1 outside, blended over one cell (the field a
+    displacement-misfit loss would recover); lambda fixed.  For the reverse-mode runs: the
+    parameter is a per-node mu field (start: 1), the loss a misfit of u(t_N)."""
+    dx = 1.0 / n
+    p = Problem(name=f"inclusion_cube_{n}", dim=3, n=(n, n, n), dx=dx, origin=(0, 0, 0),
+                periodic=(False, False, False), mu=1.0, lam=lam,
+                options=Options(c=10.0, omega=1.8, gamma=10.0, body_force=tuple(b)))
+    e = 0.3 * dx
+    p.shapes = [Shape("halfspace", (e, 0, 0), (-1, 0, 0), boundary_id=0),
+                Shape("halfspace", (1 - e, 0, 0), (1, 0, 0), boundary_id=0),
+                Shape("halfspace", (0, e, 0), (0, -1, 0), boundary_id=0),
+                Shape("halfspace", (0, 1 - e, 0), (0, 1, 0), boundary_id=0),
+                Shape("halfspace", (0, 0, e), (0, 0, -1), boundary_id=0),
+                Shape("halfspace", (0, 0, 1 - e), (0, 0, 1), boundary_id=0)]
+    p.bcs = [BC(0, "dirichlet", "zero")]
+    _rest_fields(p)
+    X = p.coords()
+    r = np.sqrt(sum((X[a] - 0.5) ** 2 for a in range(3)))
+    w = np.clip((0.25 + 0.5 * dx - r) / dx, 0.0, 1.0)
+    p.meta = dict(mu_target=1.0 + w)
+    p.steps = steps
+    return p
+

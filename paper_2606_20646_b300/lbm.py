@@ -59,7 +59,8 @@ class lbm_bc(C.Structure):
 class lbm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("proj_every", C.c_int), ("proj_iters", C.c_int), ("host_staging", C.c_int),
                 ("c", C.c_double), ("omega", C.c_double), ("gamma", C.c_double), ("theta_F", C.c_double),
-                ("proj_beta", C.c_double), ("body_force", C.c_double * 3)]
+                ("proj_beta", C.c_double), ("body_force", C.c_double * 3), ("adjoint", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class lbm_info(C.Structure):
@@ -91,6 +92,14 @@ SIGNATURES = {
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
     "lbm_enable_timing": (C.c_int, [_vp, C.c_int]),
     "lbm_step_graph": (C.c_int, [_vp, C.c_int]),
+    "lbm_set_mu_field": (C.c_int, [_vp, _vp]),
+    "lbm_set_body_force": (C.c_int, [_vp, _d]),
+    "lbm_state_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "lbm_save_state": (C.c_int, [_vp, _vp]),
+    "lbm_load_state": (C.c_int, [_vp, _vp]),
+    "lbm_adjoint_begin": (C.c_int, [_vp, _vp]),
+    "lbm_adjoint_step": (C.c_int, [_vp, _vp]),
+    "lbm_adjoint_gradients": (C.c_int, [_vp, _vp, _d]),
     "lbm_kernel_times": (C.c_int, [_vp, C.POINTER(lbm_kernel_time)]),
     "lbm_copy_links": (C.c_int, [_vp, C.POINTER(C.c_longlong), _i, _d, _d, _d, _i, _i]),
     "lbm_copy_active": (C.c_int, [_vp, C.POINTER(C.c_ubyte)]),
@@ -134,7 +143,7 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def descriptors(p, precision="fp32", host_staging=False):
+def descriptors(p, precision="fp32", host_staging=False, adjoint=False):
     """Translate a problem description into the ABI structs."""
     g = lbm_grid()
     g.dim = p.dim
@@ -178,6 +187,7 @@ def descriptors(p, precision="fp32", host_staging=False):
     opt.c, opt.omega, opt.gamma, opt.theta_F, opt.proj_beta = o.c, o.omega, o.gamma, o.theta_F, o.proj_beta
     for a in range(3):
         opt.body_force[a] = float(o.body_force[a])
+    opt.adjoint = int(bool(adjoint))
     return g, (shapes, gs), ls, mat, bcs, opt
 
 
@@ -185,11 +195,11 @@ class Simulation:
     """One TL vectorial LBM simulation on the current CUDA device, via the C ABI."""
 
     def __init__(self, p, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
-                 host_staging: bool = False, device: str | torch.device = "cuda"):
+                 host_staging: bool = False, device: str | torch.device = "cuda", adjoint: bool = False):
         lib = load_library()
         self.p, self.precision, self.device = p, precision, torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._desc = descriptors(p, precision, host_staging)
+        self._desc = descriptors(p, precision, host_staging, adjoint)
         g, shapes, ls, mat, bcs, opt = self._desc
         nbytes = C.c_size_t(0)
         _check(lib.lbm_geometry_bytes(C.byref(g), C.byref(nbytes)), "lbm_geometry_bytes")
@@ -214,6 +224,52 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    # -- parameters, saved states, reverse mode ------------------------------------------------
+    def set_mu_field(self, mu):
+        """Per-node shear modulus (box-shaped array or tensor); needs adjoint=True."""
+        t = torch.as_tensor(mu, dtype=torch.float64, device=self.device).contiguous()
+        assert t.numel() == self.p.n_box
+        _check(load_library().lbm_set_mu_field(self.h, C.c_void_p(t.data_ptr())), "lbm_set_mu_field")
+        self.stream.synchronize()
+        return self
+
+    def set_body_force(self, b):
+        arr = (C.c_double * 3)(*[float(x) for x in list(b) + [0.0] * (3 - len(b))])
+        _check(load_library().lbm_set_body_force(self.h, arr), "lbm_set_body_force")
+        return self
+
+    def state_bytes(self) -> int:
+        n = C.c_size_t(0)
+        _check(load_library().lbm_state_bytes(self.h, C.byref(n)), "lbm_state_bytes")
+        return n.value
+
+    def save_state(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        buf = out if out is not None else torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        _check(load_library().lbm_save_state(self.h, _ptr(buf)), "lbm_save_state")
+        return buf
+
+    def load_state(self, buf: torch.Tensor):
+        _check(load_library().lbm_load_state(self.h, _ptr(buf)), "lbm_load_state")
+        return self
+
+    def adjoint_begin(self, grad_u: torch.Tensor):
+        g = grad_u.to(device=self.device, dtype=torch.float64).contiguous()
+        assert g.numel() == self.D * self.p.n_box
+        self._grad_u = g
+        _check(load_library().lbm_adjoint_begin(self.h, C.c_void_p(g.data_ptr())), "lbm_adjoint_begin")
+        return self
+
+    def adjoint_step(self, state: torch.Tensor):
+        _check(load_library().lbm_adjoint_step(self.h, _ptr(state)), "lbm_adjoint_step")
+        return self
+
+    def adjoint_gradients(self):
+        """(dL/dmu as a box-shaped float64 tensor on the device, dL/db as 3 floats)."""
+        gm = torch.empty(self.p.box_shape, dtype=torch.float64, device=self.device)
+        gb = (C.c_double * 3)()
+        _check(load_library().lbm_adjoint_gradients(self.h, C.c_void_p(gm.data_ptr()), gb), "lbm_adjoint_gradients")
+        return gm, np.array(list(gb))
 
     # -- state --------------------------------------------------------------------------------
     def set_initial(self, v0=None, F0=None, u0=None, dU0=None, mode=None):

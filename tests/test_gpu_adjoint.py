@@ -1,0 +1,137 @@
+"""Reverse mode: dL/dmu (per node) and dL/db of a displacement-misfit loss,
+L = 1/2 sum over active nodes |u(t_N) - u_target|^2, through DisplacementRun (saved states every
+few steps, recomputation, lbm_adjoint_step), against central finite differences of the forward:
+the CUDA FP64 form and the FP64 oracle.  Clamped cube (velocity-Dirichlet faces), constant body
+force, smooth non-uniform mu.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2606_20646_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N, STEPS, EVERY = 14, 60, 16       # EVERY does not divide STEPS: a short last segment
+B0 = (0.2, -0.3, -1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_20646_b300 import build
+    build.build()
+
+
+def _problem(b=B0):
+    p = I.inclusion_cube(N, STEPS)
+    return p.with_(options=dataclasses.replace(p.options, body_force=tuple(b)))
+
+
+def _mu0(p):
+    X = p.coords()
+    return 1.0 + 0.2 * np.sin(2 * np.pi * X[0]) * np.cos(np.pi * X[1]) + 0.1 * X[2]
+
+
+def _gpu_u(p, mu, precision="fp64"):
+    from paper_2606_20646_b300 import lbm
+    sim = lbm.Simulation(p, precision=precision, adjoint=True)
+    sim.set_mu_field(mu).set_initial().step(STEPS)
+    u = sim.fields()[2].cpu().numpy()
+    assert sim.sync(raise_on_status=False) == 0
+    act = sim.active_mask()
+    sim.close()
+    return u, act
+
+
+def _oracle_u(p, mu):
+    import oracle
+    o = oracle.Oracle(p).set_mu_field(mu).set_initial()
+    o.step(STEPS)
+    return o.fields()[2], o.active_mask()
+
+
+def _loss(u, ut, act):
+    return 0.5 * float((((u - ut) ** 2) * act).sum())
+
+
+@pytest.fixture(scope="module")
+def setup():
+    p = _problem()
+    ut, act = _gpu_u(p, p.meta["mu_target"])       # the displacement of the target modulus
+    rng = np.random.default_rng(5)
+    nodes = [tuple(rng.integers(2, N - 2, size=3)) for _ in range(5)]
+    return p, ut, act, _mu0(p), nodes
+
+
+def _adjoint(p, ut, act, mu0, precision):
+    import torch
+    from paper_2606_20646_b300 import adjoint, lbm
+    sim = lbm.Simulation(p, precision=precision, adjoint=True)
+    mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.tensor(B0, dtype=torch.float64, requires_grad=True)
+    u = adjoint.displacement(mu, b, sim, STEPS, EVERY)
+    utt = torch.as_tensor(ut, device="cuda")
+    actt = torch.as_tensor(act, device="cuda")
+    L = 0.5 * (((u - utt) ** 2) * actt).sum()
+    L.backward()
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
+    return float(L), mu.grad.cpu().numpy(), b.grad.numpy()
+
+
+def _fd_mu(forward, p, ut, mu0, node, act, rel=1e-4):
+    e = rel * mu0[node]
+    mp, mm = mu0.copy(), mu0.copy()
+    mp[node] += e
+    mm[node] -= e
+    return (_loss(forward(p, mp)[0], ut, act) - _loss(forward(p, mm)[0], ut, act)) / (2 * e)
+
+
+def _fd_b(forward, mu0, ut, act, i, h=1e-4):
+    bp, bm = list(B0), list(B0)
+    bp[i] += h
+    bm[i] -= h
+    return (_loss(forward(_problem(bp), mu0)[0], ut, act) - _loss(forward(_problem(bm), mu0)[0], ut, act)) / (2 * h)
+
+
+def test_fp64_adjoint_matches_central_differences(setup):
+    p, ut, act, mu0, nodes = setup
+    L, gmu, gb = _adjoint(p, ut, act, mu0, "fp64")
+    assert L > 0
+    for n in nodes:
+        fd = _fd_mu(_gpu_u, p, ut, mu0, n, act)
+        print(f"dL/dmu{n}: adjoint {gmu[n]:.9e} fd {fd:.9e}")
+        assert abs(gmu[n] - fd) <= 1e-4 * abs(fd), (n, gmu[n], fd)
+    for i in range(3):
+        fd = _fd_b(_gpu_u, mu0, ut, act, i)
+        print(f"dL/db{i}: adjoint {gb[i]:.9e} fd {fd:.9e}")
+        assert abs(gb[i] - fd) <= 1e-4 * abs(fd), (i, gb[i], fd)
+    # inactive-free box: every node carries a gradient; it vanishes nowhere in the interior
+    assert np.isfinite(gmu).all()
+
+
+def test_fp64_adjoint_matches_oracle_differences(setup):
+    """The same gradient against central differences of the FP64 oracle's forward."""
+    p, ut, act, mu0, nodes = setup
+    _, gmu, gb = _adjoint(p, ut, act, mu0, "fp64")
+    for n in nodes[:2]:
+        fd = _fd_mu(_oracle_u, p, ut, mu0, n, act)
+        assert abs(gmu[n] - fd) <= 1e-4 * abs(fd), (n, gmu[n], fd)
+    fd = _fd_b(_oracle_u, mu0, ut, act, 2)
+    assert abs(gb[2] - fd) <= 1e-4 * abs(fd), (gb[2], fd)
+
+
+def test_fp32_adjoint_against_fp64(setup):
+    """FP32 form: the whole gradient field against the FP64 adjoint, and the sampled entries
+    against FP64 central differences."""
+    p, ut, act, mu0, nodes = setup
+    _, g64, gb64 = _adjoint(p, ut, act, mu0, "fp64")
+    _, g32, gb32 = _adjoint(p, ut, act, mu0, "fp32")
+    rel = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    print(f"FP32 vs FP64 adjoint: dL/dmu rel-L2 {rel:.3e}, dL/db {gb32} vs {gb64}")
+    assert rel < 1e-4
+    assert np.abs(gb32 - gb64).max() <= 1e-4 * np.abs(gb64).max()
+    for n in nodes:
+        fd = _fd_mu(_gpu_u, p, ut, mu0, n, act)
+        assert abs(g32[n] - fd) <= 1e-4 * abs(fd) + 1e-4 * np.abs(g64).max(), (n, g32[n], fd)

@@ -491,3 +491,29 @@ def test_newton_reports_nonfinite_traction():
     h, it = oracle.newton(2, 1.0, 1.0, N, [np.array([0.0, 1.0])], [np.array([0.0, 1.0])],
                           np.array([np.nan, 0.0]), N.copy())
     assert it == -1
+
+
+def test_mu_field_is_local_and_reduces_to_scalar():
+    """Per-node shear modulus: a field equal to the scalar mu reproduces the scalar run exactly, and
+    a change of mu at one node reaches, after n steps, only nodes within n links of it (one link
+    per step in the pull streaming), changing the fields at that node itself."""
+    p = I.inclusion_cube(12, 5)
+    runs = {}
+    for name, mu in (("scalar", None), ("same", np.full(p.box_shape, p.mu)), ("bump", None)):
+        o = oracle.Oracle(p)
+        if name == "same":
+            o.set_mu_field(mu)
+        if name == "bump":
+            m = np.full(p.box_shape, p.mu)
+            m[6, 6, 6] = 1.5
+            o.set_mu_field(m)
+        o.set_initial()
+        o.step(5)
+        runs[name] = np.concatenate([a.reshape(-1) for a in o.fields()]).reshape(-1, *p.box_shape)
+    assert np.array_equal(runs["scalar"], runs["same"])
+    d = np.abs(runs["bump"] - runs["scalar"]).max(axis=0)
+    z, y, x = np.indices(p.box_shape)
+    far = (np.abs(z - 6) + np.abs(y - 6) + np.abs(x - 6)) > 5
+    assert d[far].max() == 0.0
+    assert d[6, 6, 6] > 0.0
+
