@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
+    ap.add_argument("--adj-n", type=int, default=128)
+    ap.add_argument("--adj-steps", type=int, default=3000)
+    ap.add_argument("--adj-every", type=int, default=100)
     return ap.parse_args()
 
 
@@ -354,6 +358,60 @@ def run_ours(args, world, rank, local):
         del sim
         torch.cuda.empty_cache()
 
+    # ---- reverse mode: dL/dmu and dL/db of a displacement misfit (clamped cube, inclusion) ------
+    adj = None
+    if not args.no_adjoint:
+        from paper_2606_20646_b300 import adjoint as A
+        pa = I.inclusion_cube(args.adj_n, args.adj_steps)
+        Ka, every = args.adj_steps, args.adj_every
+        sim = lbm.Simulation(pa, precision="fp32", device=dev, adjoint=True)
+        nact_a = sim.info()["n_active"]
+        stream = sim.stream
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        # the target displacement (target modulus), then the plain forward time
+        sim.set_mu_field(pa.meta["mu_target"]).set_initial()
+        sim.step(Ka)
+        u_tgt = sim.fields()[2].clone()
+        act_t = torch.as_tensor(sim.active_mask(), device=dev)
+        sim.set_initial()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        sim.step(Ka)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = max_over_ranks(e0.elapsed_time(e1), world)
+
+        def run(steps):
+            mu = torch.ones(pa.box_shape, dtype=torch.float64, device=dev, requires_grad=True)
+            b = torch.tensor(pa.options.body_force, dtype=torch.float64, requires_grad=True)
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record(stream)
+            u = A.displacement(mu, b, sim, steps, every)
+            e1.record(stream)
+            loss = 0.5 * (((u - u_tgt) ** 2) * act_t).sum()
+            loss.backward()
+            e2.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), e1.elapsed_time(e2), float(loss.detach()), mu.grad, b.grad
+
+        for _ in range(max(W, 3)):   # warm-up sweeps (and the recorded-F ring) of one segment
+            run(every)
+        ms_fwd, ms_bwd, loss, gmu, gb = run(Ka)
+        ms_fwd, ms_bwd = max_over_ranks(ms_fwd, world), max_over_ranks(ms_bwd, world)
+        adj = {"workload": f"inclusion_cube_{args.adj_n}: D3Q6x12 FP32, clamped unit cube, target mu 2 inside "
+                           "r = 0.25, parameter mu field (start 1) and body force, loss 1/2 |u(T) - u_target|^2",
+               "n_active": nact_a, "steps": Ka, "checkpoint_every": every,
+               "forward_MLUPS": round(nact_a * Ka / (ms_plain / 1e3) / 1e6, 2),
+               "forward_ms": round(ms_plain, 2), "forward_with_saves_ms": round(ms_fwd, 2),
+               "backward_ms": round(ms_bwd, 2), "adjoint_over_forward": round(ms_bwd / ms_plain, 3),
+               "loss": loss, "grad_mu_norm": float(gmu.norm()), "grad_b": [float(x) for x in gb],
+               "device_status": sim.sync(raise_on_status=False),
+               "note": "backward = recomputation from saved states recording F, then the reverse steps; "
+                       "ratio over the plain forward of the same steps"}
+        del sim
+        torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ---------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -375,6 +433,7 @@ def run_ours(args, world, rank, local):
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
                 "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "batch_2d": batch,
+                "adjoint": adj,
                 "cpu_baseline": cpu, "device_status": st}
         print(json.dumps(line), flush=True)
 

@@ -281,10 +281,20 @@ int lbm_set_body_force(lbm_handle *h, const double *b);
 int lbm_state_bytes(const lbm_handle *h, size_t *bytes);
 
 /* Save the current state to / restore it from caller device memory (lbm_state_bytes bytes,
- * 256-byte aligned).  Enqueued on the handle's stream; lbm_load_state synchronises it to read
- * the step counter.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not initialised), LBM_ERR_CUDA. */
+ * 256-byte aligned).  Enqueued on the handle's stream (a kernel writes the step counter);
+ * lbm_load_state synchronises the stream to read the counter back.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_STATE (not initialised), LBM_ERR_CUDA. */
 int lbm_save_state(lbm_handle *h, void *dst);
 int lbm_load_state(lbm_handle *h, const void *src);
+
+/* Bytes of one step's recorded moments (lbm_step_moments): the D*D components of F recovered in
+ * that step (F - I in the FP32 form), one plane each over the padded box. */
+int lbm_moments_bytes(const lbm_handle *h, size_t *bytes);
+
+/* One step that also records its recovered F into `dst` (lbm_moments_bytes bytes, 256-byte
+ * aligned, device memory) for lbm_adjoint_step.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not
+ * initialised, or Neumann links present), LBM_ERR_CUDA. */
+int lbm_step_moments(lbm_handle *h, void *dst);
 
 /* Start a reverse sweep at the current state (after N steps): grad_u (D*n_box doubles in device
  * memory, box order) is dL/du at t_N for u = u* + dt/2 v as lbm_fields reports it.  Clears the
@@ -292,10 +302,11 @@ int lbm_load_state(lbm_handle *h, const void *src);
  * not set, Neumann links present), LBM_ERR_CUDA. */
 int lbm_adjoint_begin(lbm_handle *h, const double *grad_u);
 
-/* Reverse one step: the k-th call after lbm_adjoint_begin reverses step N-k, and `state` must be
- * the state saved after N-k steps (before that step).  Accumulates the gradients.  Errors:
- * LBM_ERR_ARG, LBM_ERR_STATE (no sweep in progress, or all steps reversed), LBM_ERR_CUDA. */
-int lbm_adjoint_step(lbm_handle *h, const void *state);
+/* Reverse one step: the k-th call after lbm_adjoint_begin reverses step N-k, and `moments` must
+ * hold what lbm_step_moments recorded for that step (a recomputation from a saved state provides
+ * it).  Accumulates the gradients.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (no sweep in progress, or
+ * all steps reversed), LBM_ERR_CUDA. */
+int lbm_adjoint_step(lbm_handle *h, const void *moments);
 
 /* Accumulated gradients: dL/dmu per box node (n_box doubles, device memory; zero at inactive
  * nodes) and dL/db (3 doubles, host memory); either may be null.  Synchronises. */

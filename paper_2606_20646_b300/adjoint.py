@@ -3,15 +3,26 @@ body force, as a torch.autograd.Function over a simulation.
 
 The forward pass runs the steps, saving the state every `every` steps.  The backward pass seeds
 the reverse sweep with dL/du(t_N), then walks the saved states from the last to the first: it
-restores one, recomputes the steps up to the next saved state (saving each), and reverses those
-steps in the opposite order (lbm_adjoint_step).  Memory: ceil(N/every) saved states plus `every`
-recomputed ones.  All arithmetic runs in the library's kernels; this module orders the calls.
+restores one, recomputes the steps up to the next saved state, each recording the F it recovers
+(lbm_step_moments: D*D values per node), and reverses those steps in the opposite order
+(lbm_adjoint_step).  Memory: ceil(N/every) saved states plus `every` recorded F fields, the
+latter kept on the simulation for later sweeps.  All arithmetic runs in the library's kernels;
+this module orders the calls.
 """
 from __future__ import annotations
 
 import torch
 
 from . import lbm
+
+
+def _ring(sim: "lbm.Simulation", every: int):
+    ring = getattr(sim, "_adj_ring", None)
+    if ring is None or len(ring) < every:
+        nb = sim.moments_bytes()
+        ring = [torch.empty(nb, dtype=torch.uint8, device=sim.device) for _ in range(every)]
+        sim._adj_ring = ring
+    return ring
 
 
 class DisplacementRun(torch.autograd.Function):
@@ -39,17 +50,15 @@ class DisplacementRun(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_u: torch.Tensor):
         sim, saved, nsteps, every = ctx.sim, ctx.saved, ctx.nsteps, ctx.every
+        ring = _ring(sim, every)
         sim.load_state(ctx.final)
         sim.adjoint_begin(grad_u)
-        ring = [torch.empty(sim.state_bytes(), dtype=torch.uint8, device=sim.device) for _ in range(every)]
         for s in reversed(range(len(saved))):
             n0 = s * every
             n1 = min(n0 + every, nsteps)
             sim.load_state(saved[s])
-            ring[0].copy_(saved[s])
-            for i in range(1, n1 - n0):
-                sim.step(1)
-                sim.save_state(ring[i])
+            for i in range(n1 - n0):
+                sim.step_moments(ring[i])
             for i in reversed(range(n1 - n0)):
                 sim.adjoint_step(ring[i])
         gm, gb = sim.adjoint_gradients()

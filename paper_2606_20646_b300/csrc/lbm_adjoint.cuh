@@ -14,15 +14,20 @@
 // Given lambda* = dL/df*^n and lambda_u = dL/du*^{n+1} (constant over the sweep, since u* enters
 // additively), the reverse step forms gbar = dL/dg^n at every node, and dL/dS = dL/df*^{n-1} is
 // the transpose of the gather: a pull of gbar over the same links, which the next reverse step
-// (n-1) evaluates at its own node before its local product.  The stress derivative uses the
-// tangent's major symmetry: the product with C^T equals the directional derivative along Pbar.
+// (n-1) evaluates at its own node before its local product.  f*_q is linear in g, v and X except
+// through P(F), so the local product needs only F of step n: the recomputation of the forward
+// records it (lbm_step_moments) and the reverse step reads it instead of gathering the state.  The
+// stress derivative uses the tangent's major symmetry: the product with C^T equals the directional
+// derivative along Pbar.
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace tlv {
 
 template <typename real> struct AdjArgs {
+    const real *mom;     // X = F (or F - I when shifted) of the step being reversed (D*D planes)
     const real *g_in;    // gbar of the step after this one (Q*K planes)
     real *g_out;         // gbar of this step
     double *mubar;       // dL/dmu per node
@@ -30,7 +35,6 @@ template <typename real> struct AdjArgs {
     const double *lu;    // dL/du* (D planes, box order over npad)
     const double *grad_u;  // seed: dL/du(t_N), D * nbox values
     long long nbox;
-    double th;           // time of the closure data used by this step's gather
     LinkGeom<real> L;
     const BCD *bcs;
 };
@@ -140,64 +144,6 @@ __device__ __forceinline__ void adjoint_pull(const StepArgs<real> &a, const AdjA
     }
 }
 
-// forward gather of step n recomputed from the saved state (a.fsrc), with the Dirichlet closure
-// data at time j.th (the values the link kernel formed after step n-1)
-template <typename real, int D, int MODE>
-__device__ __forceinline__ void gather_recompute(const StepArgs<real> &a, const AdjArgs<real> &j, int node, int x,
-                                                 int y, int z, unsigned cut, real (&f)[2 * D * (D + D * D)]) {
-    constexpr int K = D + D * D, Q = 2 * D;
-    const long long P = a.b.npad;
-    const real *__restrict__ fs = a.fsrc;
-    if constexpr (MODE == 0) {
-        #pragma unroll
-        for (int q = 0; q < Q; ++q)
-            #pragma unroll
-            for (int k = 0; k < K; ++k) f[q * K + k] = fs[(long long)(q * K + k) * P + node];
-        return;
-    } else {
-        const real c = a.c;
-        #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int co = q ^ 1;  // cut direction whose closure supplies g_q
-            if (!((cut >> co) & 1)) {
-                const int src = nbr(a.b, node, x, y, z, co);
-                #pragma unroll
-                for (int k = 0; k < K; ++k) f[q * K + k] = fs[(long long)(q * K + k) * P + src];
-            } else {
-                const long long l = link_of(__ldg(a.lstart + node), cut, co);
-                const BCD &bc = j.bcs[j.L.bc[l]];
-                const int A = co >> 1;
-                const real s = (co & 1) ? real(-1) : real(1);
-                const double Xb[3] = {j.L.Xb[3 * l], j.L.Xb[3 * l + 1], j.L.Xb[3 * l + 2]};
-                double vb[3];
-                dirichlet_eval(bc, D, Xb, j.th, false, vb);
-                real S[K];
-                #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    S[i] = (real)vb[i] / real(D);
-                    #pragma unroll
-                    for (int B = 0; B < D; ++B) S[D + i * D + B] = (B == A) ? s * (real)vb[i] / c : real(0);
-                }
-                const real eta = (real)j.L.eta[l];
-                const bool up = !((cut >> q) & 1);
-                const int mu_ = up ? nbr(a.b, node, x, y, z, q) : node;
-                #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const real Dk = (k < D) ? real(-1) : real(1);  // D_D = diag(-I, I)
-                    const real fo = fs[(long long)(co * K + k) * P + node];
-                    const real fi = fs[(long long)(q * K + k) * P + node];
-                    if (eta >= real(0.5)) {
-                        f[q * K + k] = (Dk * fo + S[k]) / (real(2) * eta) + (real(1) - real(1) / (real(2) * eta)) * fi;
-                    } else {
-                        const real fu = up ? fs[(long long)(co * K + k) * P + mu_] : fo;
-                        f[q * K + k] = Dk * (real(2) * eta * fo + (real(1) - real(2) * eta) * fu) + S[k];
-                    }
-                }
-            }
-        }
-    }
-}
-
 // block sum of a per-thread 3-vector into bbar (one atomic per warp and component)
 __device__ __forceinline__ void add_bbar(double *bbar, double b0, double b1, double b2) {
     #pragma unroll
@@ -249,10 +195,59 @@ __global__ void __launch_bounds__(128) k_adj_seed(const StepArgs<real> a, const 
     add_bbar(j.bbar, bb[0], bb[1], D == 3 ? bb[2] : 0.0);
 }
 
-// Reverse of step n: lambda* = pull of gbar(n+1) (the adjoint of step n+1's gather), the forward
-// quantities of step n recomputed from the saved state before it, then gbar(n) (MODE 1 only: the
-// first step has no gather to reverse) and the mu and b gradients.
-template <typename real, int D, int MODE>
+// the local product of the reverse step at one node: lambda* through the accessor L(q, k), F of
+// the step; writes gbar of the step to gout and accumulates the mu and b gradients
+template <typename real, int D, typename Lam>
+__device__ __forceinline__ void adjoint_local(const StepArgs<real> &a, const AdjArgs<real> &j, long long node, Lam L,
+                                              const real F[D * D], real mu, real lm, const double lu[D], double bb[3],
+                                              real *gout) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    const real hdt = real(0.5) * a.dt;
+    const real inv_damp = real(1) / (real(1) + hdt * a.gamma);
+    const real Dc = real(D) / a.c;
+    const real w = a.omega / real(2 * D);
+    const real src = a.dt * (real(2) - a.omega) / real(4 * D);
+    real vbar[D], Pbar[D * D], Xbar[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        real sv = 0, sF = 0;
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const real sq = (q & 1) ? real(-1) : real(1);
+            sv += L(q, i);
+            sF += sq * L(q, D + i * D + (q >> 1));
+        }
+        vbar[i] = (real)(a.dt * lu[i]) + (w - src * a.gamma) * sv - w * Dc * sF;
+        bb[i] = (double)(src * sv + vbar[i] * hdt * inv_damp);
+        #pragma unroll
+        for (int A = 0; A < D; ++A) Pbar[i * D + A] = -w * Dc * (L(2 * A, i) - L(2 * A + 1, i));
+    }
+    dpiola_t<real, D>(F, Pbar, mu, lm, Xbar);
+    real C[D * D];
+    cofactor<real, D>(F, C);
+    const real J = det<real, D>(F);
+    real dmu = 0;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) {
+        real s = 0;
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) s += L(q, D + k);
+        Xbar[k] += w * s;
+        dmu += Pbar[k] * (F[k] - C[k] / J);  // dP/dmu = F - F^-T
+    }
+    j.mubar[node] += (double)dmu;
+    const real om1 = real(1) - a.omega;
+    const long long P = a.b.npad;
+    #pragma unroll
+    for (int q = 0; q < Q; ++q)
+        #pragma unroll
+        for (int k = 0; k < K; ++k)
+            gout[(long long)(q * K + k) * P + node] = om1 * L(q, k) + (k < D ? vbar[k] * inv_damp : Xbar[k - D]);
+}
+
+// Reverse of step n: lambda* = pull of gbar(n+1) (the adjoint of step n+1's gather), then gbar(n)
+// and the mu and b gradients from the recorded F of step n
+template <typename real, int D>
 __global__ void __launch_bounds__(128) k_adj_step(const StepArgs<real> a, const AdjArgs<real> j) {
     constexpr int K = D + D * D, Q = 2 * D;
     const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -265,72 +260,147 @@ __global__ void __launch_bounds__(128) k_adj_step(const StepArgs<real> a, const 
         const uint8_t fl = x < a.b.nx ? __ldg(a.flags + node) : (uint8_t)0;
         if (fl & kActive) {
             const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
-            const unsigned cut = fl & kCutMask;
             const long long P = a.b.npad;
-            real lam[Q * K], f[Q * K];
-            adjoint_pull<real, D>(a, j, node, x, y, z, cut, lam);
-            gather_recompute<real, D, MODE>(a, j, node, x, y, z, cut, f);
-            // forward recovery and stress
-            const real hdt = real(0.5) * a.dt;
-            const real inv_damp = real(1) / (real(1) + hdt * a.gamma);
-            real v[D], X[D * D], F[D * D], Pk[D * D];
+            real lam[Q * K], F[D * D];
+            adjoint_pull<real, D>(a, j, node, x, y, z, fl & kCutMask, lam);
             #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                real s = f[k];
-                #pragma unroll
-                for (int q = 1; q < Q; ++q) s += f[q * K + k];
-                if (k < D) v[k] = (s + hdt * a.bf[k]) * inv_damp;
-                else X[k - D] = s;
-            }
-            #pragma unroll
-            for (int k = 0; k < D * D; ++k) F[k] = X[k] + ((kShifted<real> && (k / D == k % D)) ? real(1) : real(0));
+            for (int k = 0; k < D * D; ++k)
+                F[k] = j.mom[(long long)k * P + node] + ((kShifted<real> && (k / D == k % D)) ? real(1) : real(0));
             real mu, lm;
             node_material(a, node, mu, lm);
-            piola<real, D>(F, mu, lm, Pk);
-            // reverse of collision, equilibrium and quadrature
-            const real Dc = real(D) / a.c;
-            const real w = a.omega / real(2 * D);
-            const real src = a.dt * (real(2) - a.omega) / real(4 * D);
-            real vbar[D], Pbar[D * D], Xbar[D * D];
+            double lu[D];
             #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                real sv = 0, sF = 0;
-                #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const real sq = (q & 1) ? real(-1) : real(1);
-                    sv += lam[q * K + i];
-                    sF += sq * lam[q * K + D + i * D + (q >> 1)];
-                }
-                vbar[i] = (real)(a.dt * j.lu[i * P + node]) + (w - src * a.gamma) * sv - w * Dc * sF;
-                bb[i] = (double)(src * sv + vbar[i] * hdt * inv_damp);
-                #pragma unroll
-                for (int A = 0; A < D; ++A)
-                    Pbar[i * D + A] = -w * Dc * (lam[(2 * A) * K + i] - lam[(2 * A + 1) * K + i]);
+            for (int i = 0; i < D; ++i) lu[i] = j.lu[i * P + node];
+            adjoint_local<real, D>(a, j, node, [&](int q, int k) { return lam[q * K + k]; }, F, mu, lm, lu, bb,
+                                   j.g_out);
+        }
+    }
+    add_bbar(j.bbar, bb[0], bb[1], D == 3 ? bb[2] : 0.0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32 reverse step with bulk-copy staging (rows a multiple of 16): per warp one 32-node window;
+// the stage holds the pulled gbar of the next step, g(q, m + e_q) (the forward's boxes one link the
+// other way), and the flag bytes.  Cut links are applied from global memory by the lanes that
+// have them, as in the plain kernel.
+// ---------------------------------------------------------------------------------------------
+
+template <int D> struct AdjLayout {
+    using L = TmaLayout<D>;
+    static constexpr int fl_off = L::warp_bytes;
+    static constexpr int bytes = fl_off + 128;
+    static constexpr int tx = L::tx_bytes + 32;
+    // element of lane 0 inside the pulled boxes of +-x: g(q, m + e_q)
+    __device__ static constexpr int g_lane0(int q) { return q == 0 ? 5 : (q == 1 ? 3 : 0); }
+};
+
+template <int D> __device__ __forceinline__ float &stG(char *w, int q, int k, int lane) {
+    using L = TmaLayout<D>;
+    return reinterpret_cast<float *>(w + L::slot(q))[k * L::width(q) + AdjLayout<D>::g_lane0(q) + lane];
+}
+
+template <int D>
+__global__ void __launch_bounds__(32, 16) k_adj_step_tma(const StepArgs<float> a, const AdjArgs<float> j,
+                                                        const __grid_constant__ TmaMaps maps) {
+    using L = TmaLayout<D>;
+    using AL = AdjLayout<D>;
+    constexpr int K = D + D * D, Q = 2 * D;
+    extern __shared__ __align__(128) char smem[];
+    const int lane = threadIdx.x;
+    const int sgi = blockIdx.x;
+    if (sgi >= a.nseg) return;
+    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + AL::bytes);
+    const int2 sg = __ldg(&a.seg[sgi]);
+    const int y = sg.y % a.b.ny, z = sg.y / a.b.ny, x0 = sg.x - sg.y * a.b.nx;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(bar, AL::tx);
+        tma_load_2d(smem + AL::fl_off, &maps.flags, bar, x0, sg.y);
+        #pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int A = q >> 1, s = (q & 1) ? -1 : 1;
+            int st;  // the window of gbar at m + s e_A
+            if (A == 0) {
+                st = sg.x - 4;
+            } else {
+                const int n = A == 1 ? a.b.ny : a.b.nz;
+                int cg = (A == 1 ? y : z) + s;
+                if (a.b.per[A]) cg = cg < 0 ? cg + n : (cg >= n ? cg - n : cg);
+                st = A == 1 ? (z * a.b.ny + cg) * a.b.nx + x0 : (cg * a.b.ny + y) * a.b.nx + x0;
             }
-            dpiola_t<real, D>(F, Pbar, mu, lm, Xbar);
-            real C[D * D];
-            cofactor<real, D>(F, C);
-            const real J = det<real, D>(F);
-            real dmu = 0;
-            #pragma unroll
-            for (int k = 0; k < D * D; ++k) {
-                real s = 0;
-                #pragma unroll
-                for (int q = 0; q < Q; ++q) s += lam[q * K + D + k];
-                Xbar[k] += w * s;
-                dmu += Pbar[k] * (F[k] - C[k] / J);  // dP/dmu = F - F^-T
-            }
-            j.mubar[node] += (double)dmu;
-            if constexpr (MODE == 1) {
-                const real om1 = real(1) - a.omega;
-                #pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    #pragma unroll
+            tma_load_2d(smem + L::slot(q), A == 0 ? &maps.wide : &maps.narrow, bar, st, q * K);
+        }
+    }
+    const int x = x0 + lane;
+    const int node = sg.x + lane;
+    const long long P = a.b.npad;
+    const bool inrow = x < a.b.nx;
+    // per-node inputs fetched while the copies are in flight (planes hold a spare window past the
+    // box, so every lane's index is in range)
+    double lu[D];
+    float F[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) lu[i] = inrow ? j.lu[i * P + node] : 0.0;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) F[k] = j.mom[(long long)k * P + node] + ((k / D == k % D) ? 1.0f : 0.0f);
+    float mu = a.mu, lm = a.lam;
+    if (inrow) node_material(a, node, mu, lm);
+    const bool per_ = a.b.per[0] | a.b.per[1] | a.b.per[2];
+    const int yy = per_ ? y : 0, zz = per_ ? z : 0;
+    unsigned ncut[Q];  // cut masks of the axis neighbours
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long mt = nbr(a.b, node, x, yy, zz, q);
+        mt = mt < 0 ? 0 : (mt >= P ? P - 1 : mt);
+        ncut[q] = inrow ? (__ldg(a.flags + mt) & kCutMask) : 0u;
+    }
+    __syncwarp();
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
+        if (lane == 0) set_status(a.status, kStTimeout);
+        mbar_wait_bounded(bar, 0);  // let the copies in flight land before the warp exits
+        return;
+    }
+    // lanes past the row end belong to the next row: they only join the warp's sum at the end
+    const uint8_t fl = inrow ? reinterpret_cast<const uint8_t *>(smem + AL::fl_off)[lane] : (uint8_t)0;
+    double bb[3] = {0.0, 0.0, 0.0};
+    if (fl & kActive) {
+        const unsigned cut = fl & kCutMask;
+        const float *__restrict__ gin = j.g_in;
+        if (a.b.per[0]) {  // periodic x ends: the aligned boxes do not wrap
+            if (x == a.b.nx - 1 && !(cut & 1))
+                for (int k = 0; k < K; ++k) stG<D>(smem, 0, k, lane) = gin[(long long)(0 * K + k) * P + node - (a.b.nx - 1)];
+            if (x == 0 && !((cut >> 1) & 1))
+                for (int k = 0; k < K; ++k) stG<D>(smem, 1, k, lane) = gin[(long long)(1 * K + k) * P + node + a.b.nx - 1];
+        }
+        // transposed gather: the staged g(q, m + e_q) is right across interior links; fix the rest
+        #pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            float al_v, al_F, be, ga_v, ga_F;
+            if ((cut >> q) & 1) {
+                link_coeffs<float>(a, j, node, cut, q, al_v, al_F, be, ga_v, ga_F);
+                for (int k = 0; k < K; ++k)
+                    stG<D>(smem, q, k, lane) = (k < D ? al_v : al_F) * gin[(long long)((q ^ 1) * K + k) * P + node];
+            } else if ((ncut[q] >> q) & 1) {
+                const int mt = nbr(a.b, node, x, yy, zz, q);
+                link_coeffs<float>(a, j, mt, ncut[q], q, al_v, al_F, be, ga_v, ga_F);
+                if (ga_v != 0.0f || ga_F != 0.0f)
                     for (int k = 0; k < K; ++k)
-                        j.g_out[(long long)(q * K + k) * P + node] =
-                            om1 * lam[q * K + k] + (k < D ? vbar[k] * inv_damp : Xbar[k - D]);
+                        stG<D>(smem, q, k, lane) += (k < D ? ga_v : ga_F) * gin[(long long)((q ^ 1) * K + k) * P + mt];
+            }
+            if ((cut >> (q ^ 1)) & 1) {
+                link_coeffs<float>(a, j, node, cut, q ^ 1, al_v, al_F, be, ga_v, ga_F);
+                if (be != 0.0f)
+                    for (int k = 0; k < K; ++k) stG<D>(smem, q, k, lane) += be * gin[(long long)(q * K + k) * P + node];
             }
         }
+        adjoint_local<float, D>(a, j, node, [&](int q, int k) { return stG<D>(smem, q, k, lane); }, F, mu, lm, lu, bb,
+                                j.g_out);
+    } else if (inrow) {  // whole sectors: inactive nodes of the window get zeros
+        #pragma unroll
+        for (int q = 0; q < Q; ++q)
+            #pragma unroll
+            for (int k = 0; k < K; ++k) j.g_out[(long long)(q * K + k) * P + node] = 0.0f;
     }
     add_bbar(j.bbar, bb[0], bb[1], D == 3 ? bb[2] : 0.0);
 }

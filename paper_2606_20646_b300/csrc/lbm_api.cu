@@ -473,6 +473,11 @@ int lbm_state_bytes(const lbm_handle *h, size_t *bytes) {
     return LBM_OK;
 }
 
+static __global__ void k_state_header(long long *dst, long long step, long long phase) {
+    dst[0] = step;
+    dst[1] = phase;
+}
+
 int lbm_save_state(lbm_handle *h, void *dst) {
     if (!h || !dst || (reinterpret_cast<uintptr_t>(dst) % kAlign)) return LBM_ERR_ARG;
     if (!h->initialized) return LBM_ERR_STATE;
@@ -480,9 +485,9 @@ int lbm_save_state(lbm_handle *h, void *dst) {
     char *d = static_cast<char *>(dst);
     const size_t np = (size_t)h->box.npad, nc = (size_t)h->n_cut;
     const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
-    long long hdr[2] = {h->step, h->phase};
     cudaStream_t st = h->stream;
-    CK(cudaMemcpyAsync(d, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
+    k_state_header<<<1, 1, 0, st>>>(reinterpret_cast<long long *>(d), h->step, h->phase);
+    CKL();
     CK(cudaMemcpyAsync(d + L.pop, h->fA, (size_t)Q * K * np * rs, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d + L.ustar, h->ustar, (size_t)D * np * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d + L.un, h->un, (size_t)(D == 3 ? 32 : 16) * np, cudaMemcpyDeviceToDevice, st));
@@ -490,8 +495,6 @@ int lbm_save_state(lbm_handle *h, void *dst) {
         CK(cudaMemcpyAsync(d + L.rec, h->l_rec, (size_t)K * nc * rs, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(d + L.lh, h->l_h, (size_t)3 * nc * rs, cudaMemcpyDeviceToDevice, st));
     }
-    // the header comes from this stack frame: wait until it has been read
-    CK(cudaStreamSynchronize(st));
     return LBM_OK;
 }
 
@@ -520,16 +523,31 @@ int lbm_load_state(lbm_handle *h, const void *src) {
     return LBM_OK;
 }
 
+int lbm_moments_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_ERR_ARG;
+    *bytes = (size_t)h->D * h->D * h->box.npad * h->real_size;
+    return LBM_OK;
+}
+
+int lbm_step_moments(lbm_handle *h, void *dst) {
+    if (!h || !dst || (reinterpret_cast<uintptr_t>(dst) % kAlign)) return LBM_ERR_ARG;
+    if (!h->initialized || h->n_neu > 0) return LBM_ERR_STATE;
+    h->mom_out = dst;
+    const int rc = ops(h).step(h, 1);
+    h->mom_out = nullptr;
+    return rc;
+}
+
 int lbm_adjoint_begin(lbm_handle *h, const double *grad_u) {
     if (!h || !grad_u) return LBM_ERR_ARG;
     if (!h->initialized || !h->opt.adjoint || h->n_neu > 0 || h->step < 1) return LBM_ERR_STATE;
     return ops(h).adjoint_begin(h, grad_u);
 }
 
-int lbm_adjoint_step(lbm_handle *h, const void *state) {
-    if (!h || !state || (reinterpret_cast<uintptr_t>(state) % kAlign)) return LBM_ERR_ARG;
+int lbm_adjoint_step(lbm_handle *h, const void *moments) {
+    if (!h || !moments || (reinterpret_cast<uintptr_t>(moments) % kAlign)) return LBM_ERR_ARG;
     if (!h->opt.adjoint || h->adj_next < 0) return LBM_ERR_STATE;
-    return ops(h).adjoint_step(h, static_cast<const char *>(state) + state_layout(h).pop);
+    return ops(h).adjoint_step(h, moments);
 }
 
 int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b) {

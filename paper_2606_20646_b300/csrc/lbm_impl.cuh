@@ -82,6 +82,9 @@ struct lbm_handle {
     double *adj_mubar = nullptr, *adj_bbar = nullptr, *adj_lu = nullptr;
     int adj_cur = 0;                // adj_g[adj_cur] holds gbar of the last reversed step
     long long adj_next = -1;        // step the next lbm_adjoint_step reverses (-1: no sweep)
+    TmaMaps adj_maps[2];            // bulk-copy maps of adj_g[0], adj_g[1] (FP32)
+    bool adj_maps_ok = false;
+    void *mom_out = nullptr;        // lbm_step_moments: where this step records F
     cudaStream_t capture_stream = nullptr; // private stream that lbm_step_graph records on
     // solver storage
     char *sto = nullptr;
@@ -345,6 +348,7 @@ template <typename real, int D> struct Impl {
         a.mat = h->ngroups > 0 ? h->gidx : nullptr;
         a.mtab = h->ngroups > 0 ? mtab(h) : nullptr;
         a.mu_field = h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr;
+        a.mom_out = static_cast<real *>(h->mom_out);
         a.status = h->status;
         return a;
     }
@@ -370,6 +374,7 @@ template <typename real, int D> struct Impl {
     // FP32 only: tensor maps for the TMA-staged gather (needs node rows aligned to 4 floats)
     static void setup_tma(lbm_handle *h) {
         h->tma_ok = false;
+        h->adj_maps_ok = false;
         if constexpr (sizeof(real) == 4) {
             const char *off = std::getenv("LBM_B300_NO_TMA");
             // population boxes need rows aligned to 4 floats; the flag box needs rows of 16 bytes
@@ -389,6 +394,17 @@ template <typename real, int D> struct Impl {
                          cudaSuccess &&
                      cudaFuncSetAttribute(k_gather_moments_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess;
+            }
+            if (ok && h->opt.adjoint) {
+                h->adj_maps_ok = true;
+                for (int j = 0; j < 2; ++j) {
+                    h->adj_maps[j] = h->tma_maps[0];  // flags and u* maps; population maps replaced
+                    h->adj_maps_ok = h->adj_maps_ok &&
+                                     encode_population_maps(h->adj_g[j], h->box.npad, Q * K, K, &h->adj_maps[j]);
+                }
+                h->adj_maps_ok = h->adj_maps_ok &&
+                                 cudaFuncSetAttribute(k_adj_step_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                      100) == cudaSuccess;
             }
             cudaGetLastError();
             h->tma_ok = ok;
@@ -546,8 +562,9 @@ template <typename real, int D> struct Impl {
         return LBM_OK;
     }
 
-    static AdjArgs<real> adj_args(lbm_handle *h, int in, double th) {
+    static AdjArgs<real> adj_args(lbm_handle *h, int in) {
         AdjArgs<real> j;
+        j.mom = nullptr;
         j.g_in = static_cast<const real *>(h->adj_g[in]);
         j.g_out = static_cast<real *>(h->adj_g[in ^ 1]);
         j.mubar = h->adj_mubar;
@@ -555,7 +572,6 @@ template <typename real, int D> struct Impl {
         j.lu = h->adj_lu;
         j.grad_u = nullptr;
         j.nbox = h->box.nbox;
-        j.th = th;
         j.L = links(h);
         j.bcs = h->dbcs;
         return j;
@@ -569,7 +585,7 @@ template <typename real, int D> struct Impl {
         CK(cudaMemsetAsync(h->adj_g[0], 0, (size_t)Q * K * np * sizeof(real), h->stream));
         CK(cudaMemsetAsync(h->adj_g[1], 0, (size_t)Q * K * np * sizeof(real), h->stream));
         StepArgs<real> a = step_args(h);
-        AdjArgs<real> j = adj_args(h, 1, 0.0);  // seed writes adj_g[0]
+        AdjArgs<real> j = adj_args(h, 1);  // seed writes adj_g[0]
         j.grad_u = grad_u;
         k_adj_seed<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(a, j, h->adj_lu);
         CKL();
@@ -578,16 +594,21 @@ template <typename real, int D> struct Impl {
         return LBM_OK;
     }
 
-    // reverse of step n = h->adj_next from the state saved before it (populations at `pop`)
-    static int adjoint_step(lbm_handle *h, const void *pop) {
+    // reverse of step n = h->adj_next, given F of that step as lbm_step_moments recorded it
+    static int adjoint_step(lbm_handle *h, const void *moments) {
         const long long n = h->adj_next;
-        const double dt = h->grid.dx / h->opt.c;
         StepArgs<real> a = step_args(h);
-        a.fsrc = static_cast<const real *>(pop);
-        AdjArgs<real> j = adj_args(h, h->adj_cur, (n - 1) * dt + 0.5 * dt);
-        const unsigned g = grid_for(h->nseg, 4);
-        if (n == 0) k_adj_step<real, D, 0><<<g, 128, 0, h->stream>>>(a, j);
-        else k_adj_step<real, D, 1><<<g, 128, 0, h->stream>>>(a, j);
+        AdjArgs<real> j = adj_args(h, h->adj_cur);
+        j.mom = static_cast<const real *>(moments);
+        bool staged = false;
+        if constexpr (sizeof(real) == 4) {
+            if (h->tma_ok && h->adj_maps_ok) {
+                k_adj_step_tma<D><<<(unsigned)h->nseg, 32, AdjLayout<D>::bytes + 8, h->stream>>>(
+                    a, j, h->adj_maps[h->adj_cur]);
+                staged = true;
+            }
+        }
+        if (!staged) k_adj_step<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(a, j);
         CKL();
         h->adj_cur ^= 1;
         h->adj_next = n - 1;

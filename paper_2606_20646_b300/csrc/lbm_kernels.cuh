@@ -634,6 +634,7 @@ template <typename real> struct StepArgs {
     const uint8_t *mat;  // per-node group of a multi-specimen body (with mtab), else null
     const real *mtab;    // (mu, lambda) per group, or null: mu and lam above for every node
     const real *mu_field;  // per-node shear modulus replacing mu, or null
+    real *mom_out;         // the step's recovered F (or F - I when shifted): D*D planes, or null
     int *status;
 };
 
@@ -858,6 +859,9 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     recover<real, D>(a, f, v, G, F);
     real mu, lam;
     node_material(a, node, mu, lam);
+    if (a.mom_out)
+        #pragma unroll
+        for (int k = 0; k < D * D; ++k) a.mom_out[(long long)k * a.b.npad + node] = kShifted<real> ? G[k] : F[k];
     const real J = piola<real, D>(F, mu, lam, Pk);
     const int st = check_state<real, D>(v, F, J);
     if (st) set_status(a.status, st);

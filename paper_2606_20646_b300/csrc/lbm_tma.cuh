@@ -183,6 +183,9 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     for (int i = 0; i < D; ++i) v[i] = (S[i] + hdt * a.bf[i]) * inv_damp;
     #pragma unroll
     for (int k = 0; k < D * D; ++k) F[k] = S[D + k] + ((k / D == k % D) ? 1.0f : 0.0f);
+    if (a.mom_out && act)
+        #pragma unroll
+        for (int k = 0; k < D * D; ++k) a.mom_out[(long long)k * a.b.npad + node] = S[D + k];
     cofactor<float, D>(F, C);
     const float J = det<float, D>(F);
     const float sJ = (0.5f * lam * (J * J - 1.0f) - mu) * (1.0f / J);

@@ -97,6 +97,8 @@ SIGNATURES = {
     "lbm_state_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "lbm_save_state": (C.c_int, [_vp, _vp]),
     "lbm_load_state": (C.c_int, [_vp, _vp]),
+    "lbm_moments_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "lbm_step_moments": (C.c_int, [_vp, _vp]),
     "lbm_adjoint_begin": (C.c_int, [_vp, _vp]),
     "lbm_adjoint_step": (C.c_int, [_vp, _vp]),
     "lbm_adjoint_gradients": (C.c_int, [_vp, _vp, _d]),
@@ -260,8 +262,19 @@ class Simulation:
         _check(load_library().lbm_adjoint_begin(self.h, C.c_void_p(g.data_ptr())), "lbm_adjoint_begin")
         return self
 
-    def adjoint_step(self, state: torch.Tensor):
-        _check(load_library().lbm_adjoint_step(self.h, _ptr(state)), "lbm_adjoint_step")
+    def moments_bytes(self) -> int:
+        n = C.c_size_t(0)
+        _check(load_library().lbm_moments_bytes(self.h, C.byref(n)), "lbm_moments_bytes")
+        return n.value
+
+    def step_moments(self, buf: torch.Tensor):
+        """One step recording its recovered F into `buf` (moments_bytes() bytes, device)."""
+        _check(load_library().lbm_step_moments(self.h, _ptr(buf)), "lbm_step_moments")
+        return self
+
+    def adjoint_step(self, moments: torch.Tensor):
+        """Reverse the next step of the sweep, given its recorded moments."""
+        _check(load_library().lbm_adjoint_step(self.h, _ptr(moments)), "lbm_adjoint_step")
         return self
 
     def adjoint_gradients(self):
