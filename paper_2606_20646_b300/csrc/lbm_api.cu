@@ -92,11 +92,14 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->adj_g[0] = c.take<char>((size_t)Q * K * np * rs);
         h->adj_g[1] = c.take<char>((size_t)Q * K * np * rs);
         h->adj_mubar = c.take<double>((size_t)np);
-        h->adj_lu = c.take<double>((size_t)D * np);
-        h->adj_bbar = c.take<double>(4);
+        h->adj_bslot = c.take<double>((size_t)4 * kAdjSlots);
+        h->adj_lu = c.take<char>((size_t)D * np * rs);
+        h->adj_coef = c.take<char>((size_t)4 * nc * rs);
+        h->adj_side = c.take<char>((size_t)K * nc * rs);
     } else {
         h->mu_field = h->adj_g[0] = h->adj_g[1] = nullptr;
-        h->adj_mubar = h->adj_lu = h->adj_bbar = nullptr;
+        h->adj_mubar = h->adj_bslot = nullptr;
+        h->adj_lu = h->adj_coef = h->adj_side = nullptr;
     }
     *bytes = c.off;
 }
@@ -555,11 +558,16 @@ int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b) {
     if (!h->opt.adjoint) return LBM_ERR_STATE;
     cudaStream_t st = h->stream;
     if (grad_mu) CK(gather_box(h->adj_mubar, grad_mu, h->box.nbox, st));
-    double b[4] = {0, 0, 0, 0};
-    CK(cudaMemcpyAsync(b, h->adj_bbar, sizeof(b), cudaMemcpyDeviceToHost, st));
+    // dL/db: the sum of the windows' slots
+    std::vector<double> slots((size_t)4 * tlv::kAdjSlots);
+    CK(cudaMemcpyAsync(slots.data(), h->adj_bslot, slots.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (grad_b)
-        for (int i = 0; i < 3; ++i) grad_b[i] = b[i];
+        for (int i = 0; i < 3; ++i) {
+            double b = 0.0;
+            for (int s = 0; s < tlv::kAdjSlots; ++s) b += slots[(size_t)4 * s + i];
+            grad_b[i] = b;
+        }
     return LBM_OK;
 }
 

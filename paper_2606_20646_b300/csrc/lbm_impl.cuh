@@ -79,7 +79,9 @@ struct lbm_handle {
     void *mu_field = nullptr;       // per-node shear modulus (population precision)
     bool mu_field_on = false;
     void *adj_g[2] = {nullptr, nullptr};  // gbar of consecutive steps (Q*K planes each)
-    double *adj_mubar = nullptr, *adj_bbar = nullptr, *adj_lu = nullptr;
+    double *adj_mubar = nullptr, *adj_bslot = nullptr;  // dL/dmu per node; dL/db slots (kAdjSlots x 4)
+    void *adj_lu = nullptr;         // dL/du* (D planes, population precision)
+    void *adj_coef = nullptr, *adj_side = nullptr;  // per cut link: closure derivatives; side rows
     int adj_cur = 0;                // adj_g[adj_cur] holds gbar of the last reversed step
     long long adj_next = -1;        // step the next lbm_adjoint_step reverses (-1: no sweep)
     TmaMaps adj_maps[2];            // bulk-copy maps of adj_g[0], adj_g[1] (FP32)
@@ -568,12 +570,12 @@ template <typename real, int D> struct Impl {
         j.g_in = static_cast<const real *>(h->adj_g[in]);
         j.g_out = static_cast<real *>(h->adj_g[in ^ 1]);
         j.mubar = h->adj_mubar;
-        j.bbar = h->adj_bbar;
-        j.lu = h->adj_lu;
+        j.bslot = h->adj_bslot;
+        j.lu = static_cast<const real *>(h->adj_lu);
         j.grad_u = nullptr;
+        j.coef = static_cast<const real *>(h->adj_coef);
+        j.side = static_cast<real *>(h->adj_side);
         j.nbox = h->box.nbox;
-        j.L = links(h);
-        j.bcs = h->dbcs;
         return j;
     }
 
@@ -581,13 +583,18 @@ template <typename real, int D> struct Impl {
     static int adjoint_begin(lbm_handle *h, const double *grad_u) {
         const size_t np = (size_t)h->box.npad;
         CK(cudaMemsetAsync(h->adj_mubar, 0, np * sizeof(double), h->stream));
-        CK(cudaMemsetAsync(h->adj_bbar, 0, 4 * sizeof(double), h->stream));
+        CK(cudaMemsetAsync(h->adj_bslot, 0, 4 * kAdjSlots * sizeof(double), h->stream));
         CK(cudaMemsetAsync(h->adj_g[0], 0, (size_t)Q * K * np * sizeof(real), h->stream));
         CK(cudaMemsetAsync(h->adj_g[1], 0, (size_t)Q * K * np * sizeof(real), h->stream));
+        if (h->n_cut > 0) {
+            k_adj_coef<real><<<grid_for(h->n_cut, 256), 256, 0, h->stream>>>(
+                h->flags, h->l_node, h->l_q, h->l_bc, h->l_eta, h->dbcs, h->n_cut, static_cast<real *>(h->adj_coef));
+            CKL();
+        }
         StepArgs<real> a = step_args(h);
         AdjArgs<real> j = adj_args(h, 1);  // seed writes adj_g[0]
         j.grad_u = grad_u;
-        k_adj_seed<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(a, j, h->adj_lu);
+        k_adj_seed<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(a, j, static_cast<real *>(h->adj_lu));
         CKL();
         h->adj_cur = 0;
         h->adj_next = h->step - 1;
