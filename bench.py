@@ -105,23 +105,28 @@ class Clocks:
 # reported only while those sources are unchanged (null otherwise).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = {"sources_sha256": "5d2f1468508fc905a946fbe6b6ec1883d6e753128212f81c1e7e5775d20a808f",
-                   "bytes_per_launch": 2527481088 + 2094867712, "n": 256,
+TRAFFIC_CAPTURE = {"sources_sha256": "b04e68ac44a6a69182fc3914f096a6025a81498be2b9038c6e467c7af56575f8",
+                   "bytes_per_launch": 2527437056 + 2096242688, "n": 256,
                    "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
+# the same for the reverse step on the clamped cube (128^3)
+ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
+               "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
+ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "de261bedf582e11c624c21edb4c8e105f5a103dc2b357652ffa40d957ff9d87c",
+                       "bytes_per_launch": 741809152 + 573622272, "n": 128,
+                       "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(sources=KERNEL_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def captured_traffic(n):
-    cap = TRAFFIC_CAPTURE
-    if not cap or cap.get("n") != n or cap.get("sources_sha256") != kernel_sources_hash():
+def captured_traffic(n, cap=TRAFFIC_CAPTURE, sources=KERNEL_SOURCES):
+    if not cap or cap.get("n") != n or cap.get("sources_sha256") != kernel_sources_hash(sources):
         return None
     return cap["bytes_per_launch"]
 
@@ -140,6 +145,21 @@ def jacobi_bytes_per_node(D, real_size):
     sweep weight) and its flag byte; neighbour reads hit in cache."""
     dv = 4 if D == 3 else 2
     return 2 * dv * real_size + 4 * real_size + 1
+
+
+def adjoint_bytes_per_node(D, real_size):
+    """Algorithmic HBM bytes per active node of one reverse step: the next step's gbar read once
+    and this step's written once (Q*K values each), the recorded F (D*D values) and dL/du* (D
+    values) read, dL/dmu (FP64) read and written, one flag byte.  Cut links add their coefficient
+    and side rows (below 0.3 % of the nodes' bytes on a clamped cube)."""
+    K, Q = D + D * D, 2 * D
+    return 2 * Q * K * real_size + D * D * real_size + D * real_size + 2 * 8 + 1
+
+
+def recompute_bytes_per_node(D, real_size):
+    """The forward step of the backward's recomputation: the fused kernel's bytes plus the D*D
+    recorded F values written."""
+    return bytes_per_node(D, real_size) + D * D * real_size
 
 
 def dist_setup(args):
@@ -399,6 +419,35 @@ def run_ours(args, world, rank, local):
             run(every)
         ms_fwd, ms_bwd, loss, gmu, gb = run(Ka)
         ms_fwd, ms_bwd = max_over_ranks(ms_fwd, world), max_over_ranks(ms_bwd, world)
+        # the backward's two kernels alone: `every` recomputed steps recording F (one fused launch
+        # each), then the reverse steps over them (one k_adj_step_tma launch each)
+        ring = A._ring(sim, every)
+        seed = ((sim.fields()[2] - u_tgt) * act_t).contiguous()
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        for i in range(every):
+            sim.step_moments(ring[i])
+        e1.record(stream)
+        sim.adjoint_begin(seed)
+        e2.record(stream)
+        for i in reversed(range(every)):
+            sim.adjoint_step(ring[i])
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ms_rec = max_over_ranks(e0.elapsed_time(e1), world) / every
+        ms_rev = max_over_ranks(e2.elapsed_time(e3), world) / every
+        brev, brec = adjoint_bytes_per_node(3, 4), recompute_bytes_per_node(3, 4)
+        gb_rev = nact_a * brev / (ms_rev / 1e3) / 1e9
+        gb_rec = nact_a * brec / (ms_rec / 1e3) / 1e9
+        kernels = {"reverse": {"kernel": "k_adj_step_tma<3>", "ms_per_launch": round(ms_rev, 4),
+                               "bytes_per_node": brev, "achieved_GBps": round(gb_rev, 1),
+                               "frac": round(gb_rev / peak, 4),
+                               "traffic": captured_traffic(args.adj_n, ADJ_TRAFFIC_CAPTURE, ADJ_SOURCES)},
+                   "recompute": {"kernel": "k_stream_collide_tma<3> recording F", "ms_per_launch": round(ms_rec, 4),
+                                 "bytes_per_node": brec, "achieved_GBps": round(gb_rec, 1),
+                                 "frac": round(gb_rec / peak, 4)},
+                   "peak": peak, "peak_kind": peak_kind,
+                   "note": f"CUDA events around {every} launches of each on the solver's stream"}
         adj = {"workload": f"inclusion_cube_{args.adj_n}: D3Q6x12 FP32, clamped unit cube, target mu 2 inside "
                            "r = 0.25, parameter mu field (start 1) and body force, loss 1/2 |u(T) - u_target|^2",
                "n_active": nact_a, "steps": Ka, "checkpoint_every": every,
@@ -406,6 +455,7 @@ def run_ours(args, world, rank, local):
                "forward_ms": round(ms_plain, 2), "forward_with_saves_ms": round(ms_fwd, 2),
                "backward_ms": round(ms_bwd, 2), "adjoint_over_forward": round(ms_bwd / ms_plain, 3),
                "loss": loss, "grad_mu_norm": float(gmu.norm()), "grad_b": [float(x) for x in gb],
+               "kernels": kernels,
                "device_status": sim.sync(raise_on_status=False),
                "note": "backward = recomputation from saved states recording F, then the reverse steps; "
                        "ratio over the plain forward of the same steps"}
