@@ -86,6 +86,7 @@ def lib():
         _lib.orc_newton.restype = C.c_int
         _lib.orc_newton.argtypes = [C.c_int, C.c_double, C.c_double, d, d, d, d, d]
         _lib.orc_project.argtypes = [vp, d, d, C.c_double, d]
+        _lib.orc_adjoint.argtypes = [vp, C.c_int, d, d, d]
         _lib.orc_levelset.restype = C.c_double
         _lib.orc_levelset.argtypes = [C.POINTER(_Problem), d, i]
     return _lib
@@ -173,6 +174,19 @@ class Oracle:
             assert a.size == self.N
             lib().orc_set_mu_field(self.h, _dp(a))
         return self
+
+    def adjoint(self, nsteps: int, grad_u):
+        """Runs nsteps steps from the current state and returns the discrete adjoint of a loss
+        on u after them: (dL/dmu, box-shaped; dL/db, 3 values), given grad_u = dL/du (D x box).
+        Velocity-Dirichlet bodies only."""
+        g = _f64(np.asarray(grad_u).reshape(self.D, -1))
+        assert g.shape[1] == self.N
+        mubar = np.zeros(self.N)
+        bbar = np.zeros(3)
+        rc = lib().orc_adjoint(self.h, int(nsteps), _dp(g), _dp(mubar), _dp(bbar))
+        if rc < 0:
+            raise ValueError(f"oracle adjoint refused (code {rc})")
+        return mubar.reshape(self.p.box_shape), bbar
 
     def fields(self):
         D, N = self.D, self.N

@@ -29,6 +29,10 @@
  * boundary edges to the prescribed displacement u_D(X_b), or a mean gauge; projection every proj_every steps; after
  * the second projection u*^{n+1} = u^c + dt/2 v^n.
  *
+ * Reverse mode (orc_adjoint): the discrete adjoint of the step for velocity-Dirichlet bodies, a
+ * plain reverse accumulation over stored states; pinned by central differences of this file's
+ * forward (single-node moduli, body force, a random direction of the whole modulus field).
+ *
  * Parity status: every function is pinned by tests except the projection
  * solver constants (sweep count, damping, gauge), which the paper does not
  * fix -- parity unpinned for those constants; the projection is pinned only
@@ -1308,4 +1312,142 @@ int orc_project(orc_state *s, const double *F, double *u, double t, double *Fc)
     free(U);
     free(uu);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* reverse mode                                                               */
+/* ------------------------------------------------------------------------- */
+/*
+ * The discrete adjoint of `nsteps` calls of one_step from the current state, for bodies whose cut
+ * links are all velocity-Dirichlet (no projection, no Newton inversion).  Parameters: the shear
+ * modulus of every node (the per-node field, or p.mu everywhere) and the body force b, constant
+ * in time.  The loss L enters through grad_u = dL/du(t_N) (box SoA, D*N values) with
+ * u(t_N) = u*^N + dt/2 v^N (orc_fields).  Outputs dL/dmu (N values, zero off the body) and dL/db
+ * (3 values).  The state advances by nsteps.
+ *
+ * Plain reverse accumulation.  Every pre-collision state f^n is kept.  Going backwards, step n
+ * maps fbar (= dL/df^{n+1}) to dL/df*^n by transposing the streaming (each streamed value sends
+ * its adjoint back along its link) and the BFL reconstruction (Eqs. bfl-eta-ge-half,
+ * bfl-eta-lt-half; the Dirichlet S_b does not depend on the parameters), then to dL/df^n through
+ * the collision of Eq. collision-general-d with the recovery of Eq. state-recovery-general.  The
+ * Jacobian of f^eq with respect to U is formed column by column with the flux JVP (Eq.
+ * flux-jvp-general-d) and applied transposed as an explicit sum; d f^eq / d mu comes from
+ * P(F; mu = 1, lambda = 0) = F - F^{-T}, the part of P proportional to mu.  u*^{n+1} = u*^n + dt v^n
+ * makes dL/du* = dL/du at every step and adds dt dL/du to dL/dv^n.
+ */
+int orc_adjoint(orc_state *s, int nsteps, const double *grad_u, double *mubar, double *bbar)
+{
+    if (!s->f || nsteps < 1 || !grad_u || !mubar || !bbar) return ORC_EARG;
+    if (s->nneu > 0) return ORC_EARG;
+    int D = s->D, K = s->K, Q = s->Q;
+    long N = s->N;
+    size_t nf = (size_t)N * Q * K;
+    double dt = s->dt, c = s->p.c, lam = s->p.lam, om = s->p.omega, ga = s->p.gamma;
+    double damp = 1.0 + 0.5 * dt * ga, wq = 1.0 / (4.0 * D);
+    double *hist = malloc(sizeof(double) * nf * (size_t)(nsteps + 1));
+    double *fbar = calloc(nf, sizeof(double)), *fsbar = calloc(nf, sizeof(double));
+    if (!hist || !fbar || !fsbar) {
+        free(hist);
+        free(fbar);
+        free(fsbar);
+        return ORC_ENOMEM;
+    }
+    memcpy(hist, s->f, sizeof(double) * nf);
+    for (int n = 0; n < nsteps; n++) {
+        one_step(s);
+        memcpy(hist + nf * (size_t)(n + 1), s->f, sizeof(double) * nf);
+    }
+    for (long m = 0; m < N; m++) mubar[m] = 0.0;
+    for (int i = 0; i < 3; i++) bbar[i] = 0.0;
+    /* seed: u(t_N) = u*^N + dt/2 v^N with v^N recovered from f^N */
+    for (long m = 0; m < N; m++) {
+        if (!s->active[m]) continue;
+        for (int i = 0; i < D; i++) {
+            double vbar = 0.5 * dt * grad_u[i * N + m];
+            for (int q = 0; q < Q; q++) fbar[((size_t)m * Q + q) * K + i] = vbar / damp;
+            bbar[i] += vbar * 0.5 * dt / damp;
+        }
+    }
+    for (int n = nsteps - 1; n >= 0; n--) {
+        const double *fn = hist + nf * (size_t)n;
+        /* transpose of streaming and cut-link reconstruction: fsbar = dL/df*^n */
+        memset(fsbar, 0, sizeof(double) * nf);
+        for (long m = 0; m < N; m++) {
+            if (!s->active[m]) continue;
+            for (int q = 0; q < Q; q++) {
+                long l = nbr_q(s, m, q);
+                if (l < 0 || !s->active[l]) continue;
+                for (int k = 0; k < K; k++)
+                    fsbar[((size_t)m * Q + q) * K + k] += fbar[((size_t)l * Q + q) * K + k];
+            }
+        }
+        for (long li = 0; li < s->ncut; li++) {
+            const orc_link *L = &s->links[li];
+            int q = L->q, qin = q ^ 1;
+            double eta = L->eta;
+            const double *g = fbar + ((size_t)L->m * Q + qin) * K;
+            double *bo = fsbar + ((size_t)L->m * Q + q) * K;
+            double *bi = fsbar + ((size_t)L->m * Q + qin) * K;
+            double *bu = fsbar + ((size_t)L->mminus * Q + q) * K;
+            for (int k = 0; k < K; k++) {
+                double Dp = (k < D) ? -1.0 : 1.0; /* velocity-Dirichlet rows */
+                if (eta >= 0.5) {
+                    bo[k] += Dp / (2.0 * eta) * g[k];
+                    bi[k] += (1.0 - 1.0 / (2.0 * eta)) * g[k];
+                } else {
+                    bo[k] += Dp * 2.0 * eta * g[k];
+                    bu[k] += Dp * (1.0 - 2.0 * eta) * g[k];
+                }
+            }
+        }
+        /* transpose of recovery + collision + u* update at every node: fbar = dL/df^n */
+        for (long m = 0; m < N; m++) {
+            if (!s->active[m]) continue;
+            const double *f = fn + (size_t)m * Q * K;
+            const double *gs = fsbar + (size_t)m * Q * K;
+            double *fb = fbar + (size_t)m * Q * K;
+            double U[12], Ubar[12], mu = mu_at(s, m);
+            recover(D, dt, ga, s->p.b, f, U);
+            for (int j = 0; j < K; j++) {
+                /* column j of d f^eq / dU */
+                double Z[12] = {0}, dPhi[3 * 12];
+                Z[j] = 1.0;
+                flux_jvp(D, mu, lam, U, Z, dPhi);
+                double acc = 0.0;
+                for (int q = 0; q < Q; q++)
+                    for (int k = 0; k < K; k++) {
+                        double col = (k == j) ? 1.0 : 0.0;
+                        double sA = 0.0;
+                        for (int A = 0; A < D; A++) sA += edir(q, A) * dPhi[A * K + k];
+                        col = (col + (D / c) * sA) / (2.0 * D);
+                        acc += gs[q * K + k] * col;
+                    }
+                Ubar[j] = om * acc;
+            }
+            for (int i = 0; i < D; i++) {
+                double sg = 0.0;
+                for (int q = 0; q < Q; q++) sg += gs[q * K + i];
+                Ubar[i] += dt * (2.0 - om) * wq * (-ga) * sg + dt * grad_u[i * N + m];
+                bbar[i] += dt * (2.0 - om) * wq * sg;
+            }
+            /* d f^eq / d mu: the fluxes' velocity rows hold -P, and dP/dmu = P(F; 1, 0) */
+            double dPm[9], dmu = 0.0;
+            orc_piola(D, 1.0, 0.0, U + D, dPm);
+            for (int q = 0; q < Q; q++)
+                for (int i = 0; i < D; i++) {
+                    double sA = 0.0;
+                    for (int A = 0; A < D; A++) sA += edir(q, A) * (-dPm[i * D + A]);
+                    dmu += gs[q * K + i] * (D / c) * sA / (2.0 * D);
+                }
+            mubar[m] += om * dmu;
+            for (int q = 0; q < Q; q++)
+                for (int k = 0; k < K; k++)
+                    fb[q * K + k] = (1.0 - om) * gs[q * K + k] + ((k < D) ? Ubar[k] / damp : Ubar[k]);
+            for (int i = 0; i < D; i++) bbar[i] += Ubar[i] * 0.5 * dt / damp;
+        }
+    }
+    free(hist);
+    free(fbar);
+    free(fsbar);
+    return s->status;
 }

@@ -2,7 +2,9 @@
 L = 1/2 sum over active nodes |u(t_N) - u_target|^2, through DisplacementRun (saved states every
 few steps, recomputation, lbm_adjoint_step), against central finite differences of the forward:
 the CUDA FP64 form and the FP64 oracle.  Clamped cube (velocity-Dirichlet faces), constant body
-force, smooth non-uniform mu.
+force, smooth non-uniform mu.  Then the whole gradient field against the oracle's own discrete
+adjoint (itself pinned to central differences of the oracle's forward on CPU), on the cube and on a
+rotated ellipsoid whose cut links take every branch of the interpolated bounce-back.
 """
 import dataclasses
 
@@ -135,3 +137,86 @@ def test_fp32_adjoint_against_fp64(setup):
     for n in nodes:
         fd = _fd_mu(_gpu_u, p, ut, mu0, n, act)
         assert abs(g32[n] - fd) <= 1e-4 * abs(fd) + 1e-4 * np.abs(g64).max(), (n, g32[n], fd)
+
+
+# ---- against the oracle's discrete adjoint (the whole gradient field) ---------------------------
+
+def _gpu_grad(p, mu0, ut, act, precision, steps, every):
+    import torch
+    from paper_2606_20646_b300 import adjoint, lbm
+    sim = lbm.Simulation(p, precision=precision, adjoint=True)
+    mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.tensor(p.options.body_force, dtype=torch.float64, requires_grad=True)
+    u = adjoint.displacement(mu, b, sim, steps, every)
+    L = 0.5 * (((u - torch.as_tensor(ut, device="cuda")) ** 2) * torch.as_tensor(act, device="cuda")).sum()
+    L.backward()
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
+    return mu.grad.cpu().numpy(), b.grad.numpy()
+
+
+def _oracle_grad(p, mu0, ut, act, steps):
+    import oracle
+    o = oracle.Oracle(p).set_mu_field(mu0).set_initial()
+    o.step(steps)
+    u = o.fields()[2]
+    o = oracle.Oracle(p).set_mu_field(mu0).set_initial()
+    return o.adjoint(steps, (u - ut) * act)
+
+
+def _ellipsoid_from_rest(N):
+    """The rotated ellipsoid started from rest with F = I (initial populations independent of mu
+    and b), driven by its prescribed surface velocity, with a body force: its links take both
+    eta branches and the upstream fallback."""
+    p = I.ellipsoid_3d(N)
+    D = p.dim
+    return p.with_(init_mode="equilibrium", dU0=None, v0=np.zeros((D,) + p.box_shape),
+                   u0=np.zeros((D,) + p.box_shape),
+                   F0=np.broadcast_to(np.eye(D).reshape(-1, 1, 1, 1), (D * D,) + p.box_shape).copy(),
+                   options=dataclasses.replace(p.options, body_force=(0.3, 0.1, -0.5)))
+
+
+@pytest.fixture(scope="module")
+def ellipsoid_case():
+    import oracle
+    p = _ellipsoid_from_rest(16)
+    mu0 = _mu0(p)
+    steps = 40
+    o = oracle.Oracle(p).set_mu_field(1.3 * mu0).set_initial()
+    o.step(steps)
+    ut = o.fields()[2]
+    act = o.active_mask().reshape(p.box_shape)
+    return p, mu0, ut, act, steps
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_fp64_adjoint_equals_oracle_adjoint_cube(setup):
+    p, ut, act, mu0, _ = setup
+    g, gb = _gpu_grad(p, mu0, ut, act, "fp64", STEPS, EVERY)
+    go, gbo = _oracle_grad(p, mu0, ut, act, STEPS)
+    print(f"cube: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
+    assert _rel(g, go) < 1e-10
+    assert np.abs(gb - gbo).max() <= 1e-10 * np.abs(gbo).max()
+
+
+def test_fp64_adjoint_equals_oracle_adjoint_ellipsoid(ellipsoid_case):
+    p, mu0, ut, act, steps = ellipsoid_case
+    g, gb = _gpu_grad(p, mu0, ut, act, "fp64", steps, 16)
+    go, gbo = _oracle_grad(p, mu0, ut, act, steps)
+    print(f"ellipsoid: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
+    assert _rel(g, go) < 1e-10
+    assert np.abs(gb - gbo).max() <= 1e-10 * np.abs(gbo).max()
+    assert not g[~act.astype(bool)].any()
+
+
+def test_fp32_adjoint_ellipsoid_against_oracle(ellipsoid_case):
+    """FP32 form (staged reverse kernel: rows of 16) on the body with every closure branch."""
+    p, mu0, ut, act, steps = ellipsoid_case
+    g, gb = _gpu_grad(p, mu0, ut, act, "fp32", steps, 16)
+    go, gbo = _oracle_grad(p, mu0, ut, act, steps)
+    print(f"ellipsoid FP32: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
+    assert _rel(g, go) < 1e-4
+    assert np.abs(gb - gbo).max() <= 1e-4 * np.abs(gbo).max()
