@@ -198,8 +198,8 @@ def test_fp64_adjoint_equals_oracle_adjoint_cube(setup):
     g, gb = _gpu_grad(p, mu0, ut, act, "fp64", STEPS, EVERY)
     go, gbo = _oracle_grad(p, mu0, ut, act, STEPS)
     print(f"cube: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
-    assert _rel(g, go) < 1e-10
-    assert np.abs(gb - gbo).max() <= 1e-10 * np.abs(gbo).max()
+    assert _rel(g, go) < 1e-12
+    assert np.abs(gb - gbo).max() <= 1e-12 * np.abs(gbo).max()
 
 
 def test_fp64_adjoint_equals_oracle_adjoint_ellipsoid(ellipsoid_case):
@@ -207,8 +207,8 @@ def test_fp64_adjoint_equals_oracle_adjoint_ellipsoid(ellipsoid_case):
     g, gb = _gpu_grad(p, mu0, ut, act, "fp64", steps, 16)
     go, gbo = _oracle_grad(p, mu0, ut, act, steps)
     print(f"ellipsoid: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
-    assert _rel(g, go) < 1e-10
-    assert np.abs(gb - gbo).max() <= 1e-10 * np.abs(gbo).max()
+    assert _rel(g, go) < 1e-12
+    assert np.abs(gb - gbo).max() <= 1e-12 * np.abs(gbo).max()
     assert not g[~act.astype(bool)].any()
 
 
