@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="box nodes per axis of the shell workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
     ap.add_argument("--batch-steps", type=int, default=1000)
@@ -309,6 +310,43 @@ def run_ours(args, world, rank, local):
         del sim
         torch.cuda.empty_cache()
 
+    # ---- BF16 population storage on the same workload; its error at t = 1 on the 128^3 copy --------
+    bf16 = None
+    if not args.no_bf16:
+        sim = lbm.Simulation(p, precision="bf16s", device=dev)
+        sim.set_initial()
+        sim.step(W)
+        msb, _, ktb, _ = timed(sim, K, True)
+        avgb = ktb["stream_collide_ms"] / max(ktb["stream_collide_launches"], 1)
+        bpn = bytes_per_node(3, 2)
+        gbb = nact * bpn / (avgb / 1e3) / 1e9
+        stb = sim.sync(raise_on_status=False)
+        del sim
+        torch.cuda.empty_cache()
+        pe, ne = I.shell_3d(128), 640
+        res = {}
+        for prec in ("fp64", "bf16s"):
+            s2 = lbm.Simulation(pe, precision=prec, device=dev)
+            s2.set_initial().step(ne)
+            res[prec] = [t.double() for t in s2.fields()]
+            acte = torch.as_tensor(s2.active_mask(), device=dev)
+            s2.close()
+        eye = torch.eye(3, dtype=torch.float64, device=dev).reshape(9, 1, 1, 1)
+
+        def rel(a, b):
+            return float(torch.linalg.norm((a - b)[:, acte]) / torch.linalg.norm(b[:, acte]))
+
+        (vb, Fb, ub), (vd, Fd, ud) = res["bf16s"], res["fp64"]
+        bf16 = {"value": round(nact * K / (msb / 1e3) / 1e6, 2), "unit": UNIT, "steps": K,
+                "ms_per_step": round(msb / K, 4), "dtype": "bf16 storage, f32 arithmetic",
+                "stream_collide_ms": round(avgb, 4), "bytes_per_node": bpn,
+                "stream_collide_GBps": round(gbb, 1), "frac": round(gbb / peak, 4), "peak_kind": peak_kind,
+                "error_vs_fp64": {"workload": "shell_3d_128 at t = 1 (640 steps)", "v": rel(vb, vd),
+                                  "F_minus_I": rel(Fb - eye, Fd - eye), "u": rel(ub, ud)},
+                "device_status": stb}
+        del res
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers ---------------------------------------
     e2e = None
     if not args.no_e2e:
@@ -482,7 +520,7 @@ def run_ours(args, world, rank, local):
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
                 "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
-                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "batch_2d": batch,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "bf16": bf16, "batch_2d": batch,
                 "adjoint": adj,
                 "cpu_baseline": cpu, "device_status": st}
         print(json.dumps(line), flush=True)

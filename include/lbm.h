@@ -64,7 +64,12 @@ enum lbm_device_status {
     LBM_DEV_TIMEOUT = 128  /* a bounded wait for a TMA copy ran out; that step is invalid */
 };
 
-enum lbm_precision { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1 };
+/* FP64: populations and arithmetic in FP64.  FP32: both in FP32, populations stored shifted
+ * (f - f^eq(0, I)).  BF16S: the FP32 form with the shifted populations stored as BF16 (rounded to
+ * nearest even on store; every other array, the cut links' kept and reconstructed values and the
+ * displacement accumulators keep their FP32 form); half the population bytes of FP32.  Not with
+ * options.adjoint. */
+enum lbm_precision { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_BF16S = 2 };
 
 /* level-set primitives; local coordinates xi = rot^T (X - center), rot row-major 3x3
  *   SPHERE        phi = |X - center| - axes[0]                (circle in 2D)
@@ -171,7 +176,7 @@ typedef struct lbm_bc {
 } lbm_bc;
 
 typedef struct lbm_options {
-    int precision;    /* enum lbm_precision: population storage and collision arithmetic */
+    int precision;    /* enum lbm_precision: population storage and arithmetic              */
     int proj_every;   /* compatibility projection cadence in steps (0: never)            */
     int proj_iters;   /* damped-Jacobi sweeps per projection solve                        */
     int host_staging; /* non-zero: reserve a staging area so field calls accept host memory */

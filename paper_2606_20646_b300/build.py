@@ -13,6 +13,7 @@ LIB = os.path.join(HERE, "liblbm_b300.so")
 SOURCES = [(os.path.join(HERE, "csrc", "lbm_api.cu"), []),
            (os.path.join(HERE, "csrc", "lbm_fp32.cu"), []),
            (os.path.join(HERE, "csrc", "lbm_fp64.cu"), ["-fmad=false"]),
+           (os.path.join(HERE, "csrc", "lbm_bf16s.cu"), []),
            (os.path.join(HERE, "csrc", "lbm_static.cu"), [])]
 DEPENDS = glob.glob(os.path.join(HERE, "csrc", "*")) + [os.path.join(ROOT, "include", "lbm.h")]
 

@@ -18,7 +18,9 @@
 
 #include "lbm_ops.cuh"
 
-static const PrecOps &ops(const lbm_handle *h) { return h->real_size == 8 ? ops_fp64() : ops_fp32(); }
+static const PrecOps &ops(const lbm_handle *h) {
+    return h->real_size == 8 ? ops_fp64() : (h->pop_size == 2 ? ops_bf16s() : ops_fp32());
+}
 
 // =============================================================================================
 // storage layouts
@@ -48,9 +50,9 @@ static void carve_geometry(lbm_handle *h, char *base, size_t *bytes) {
 static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     Carver c{base};
     const long long np = h->box.npad, nc = std::max<long long>(h->n_cut, 1);
-    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size;
-    h->fA = c.take<char>((size_t)Q * K * np * rs);
-    h->fB = c.take<char>((size_t)Q * K * np * rs);
+    const int D = h->D, K = h->K, Q = h->Q, rs = h->real_size, ps = h->pop_size;
+    h->fA = c.take<char>((size_t)Q * K * np * ps);
+    h->fB = c.take<char>((size_t)Q * K * np * ps);
     // displacement accumulators: one FP64 plane per component, or a (hi, lo) pair of FP32 planes
     h->ustar = c.take<char>((size_t)D * np * 8);
     h->un = c.take<char>((size_t)(D == 3 ? 32 : 16) * np);  // node-major u^n (see kUnStride)
@@ -116,7 +118,7 @@ static StateLayout state_layout(const lbm_handle *h) {
     StateLayout L;
     c.take<char>(256);
     L.pop = c.off;
-    c.take<char>((size_t)Q * K * np * rs);
+    c.take<char>((size_t)Q * K * np * h->pop_size);
     L.ustar = c.off;
     c.take<char>((size_t)D * np * 8);
     L.un = c.off;
@@ -190,7 +192,9 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         for (int a = 0; a < grid->dim; ++a)
             if (!(G.lo[a] <= G.hi[a])) return LBM_ERR_ARG;
     }
-    if (opt->precision != LBM_PREC_FP64 && opt->precision != LBM_PREC_FP32) return LBM_ERR_ARG;
+    if (opt->precision != LBM_PREC_FP64 && opt->precision != LBM_PREC_FP32 && opt->precision != LBM_PREC_BF16S)
+        return LBM_ERR_ARG;
+    if (opt->precision == LBM_PREC_BF16S && opt->adjoint) return LBM_ERR_ARG;
     if (!(opt->c > 0.0) || !(opt->omega > 0.0 && opt->omega <= 2.0) || !(opt->gamma >= 0.0)) return LBM_ERR_ARG;
     if (opt->proj_every < 0 || opt->proj_iters < 0 || !(opt->theta_F > 0.0 && opt->theta_F <= 1.0) ||
         !(opt->proj_beta > 0.0 && opt->proj_beta <= 1.0))
@@ -232,6 +236,7 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     h->K = h->D + h->D * h->D;
     h->Q = 2 * h->D;
     h->real_size = opt->precision == LBM_PREC_FP64 ? 8 : 4;
+    h->pop_size = opt->precision == LBM_PREC_BF16S ? 2 : h->real_size;
     h->nshapes = ls->nshapes;
     for (int s = 0; s < ls->nshapes; ++s) {
         const lbm_shape &sh = ls->shapes[s];
@@ -491,7 +496,7 @@ int lbm_save_state(lbm_handle *h, void *dst) {
     cudaStream_t st = h->stream;
     k_state_header<<<1, 1, 0, st>>>(reinterpret_cast<long long *>(d), h->step, h->phase);
     CKL();
-    CK(cudaMemcpyAsync(d + L.pop, h->fA, (size_t)Q * K * np * rs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d + L.pop, h->fA, (size_t)Q * K * np * h->pop_size, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d + L.ustar, h->ustar, (size_t)D * np * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d + L.un, h->un, (size_t)(D == 3 ? 32 : 16) * np, cudaMemcpyDeviceToDevice, st));
     if (nc) {
@@ -511,7 +516,7 @@ int lbm_load_state(lbm_handle *h, const void *src) {
     long long hdr[2] = {0, 0};
     cudaStream_t st = h->stream;
     CK(cudaMemcpyAsync(hdr, s, sizeof(hdr), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h->fA, s + L.pop, (size_t)Q * K * np * rs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->fA, s + L.pop, (size_t)Q * K * np * h->pop_size, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->ustar, s + L.ustar, (size_t)D * np * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->un, s + L.un, (size_t)(D == 3 ? 32 : 16) * np, cudaMemcpyDeviceToDevice, st));
     if (nc) {

@@ -1,5 +1,6 @@
 // Host-side orchestration shared by the precision-specific translation units: the handle,
-// storage carving helpers, and Impl<real, D> which launches the kernels of one update.
+// storage carving helpers, and Impl<real, D, pop> which launches the kernels of one update (real:
+// arithmetic type; pop: population storage type, real itself or BF16 with FP32 arithmetic).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,6 +10,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -55,7 +57,8 @@ struct lbm_handle {
     bool has_neumann_bc = false;
     cudaStream_t stream = nullptr;
     int D = 0, K = 0, Q = 0;
-    int real_size = 8;
+    int real_size = 8;  // bytes of the arithmetic type
+    int pop_size = 8;   // bytes of a stored population value (2 for BF16 storage)
     Box box{};
     int segs_per_row = 0;
     long long nsegmax = 0;
@@ -257,7 +260,9 @@ inline bool encode_meta_maps(void *ustar, long long npad, int D, void *flags, in
     return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
 }
 
-inline bool encode_population_maps(void *base, long long npad, int planes, int K, TmaMaps *out) {
+// population planes as a 2D tensor (node index, plane) of E-byte elements (4: FP32, 2: BF16): boxes of
+// (32 + 2*16/E, K) for the +-x pulls and (32, K) otherwise
+inline bool encode_population_maps(void *base, long long npad, int planes, int K, TmaMaps *out, int E = 4) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -271,13 +276,16 @@ inline bool encode_population_maps(void *base, long long npad, int planes, int K
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)planes};
-    const cuuint64_t strides[1] = {(cuuint64_t)npad * 4};
+    if (E != 4 && E != 2) return false;
+    const CUtensorMapDataType ty = E == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t strides[1] = {(cuuint64_t)npad * E};
     const cuuint32_t es[2] = {1, 1};
-    const cuuint32_t wide[2] = {(cuuint32_t)kTmaWide, (cuuint32_t)K}, narrow[2] = {(cuuint32_t)kTmaNarrow, (cuuint32_t)K};
-    CUresult r1 = encode(&out->wide, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, wide, es,
+    const cuuint32_t wide[2] = {(cuuint32_t)(32 + 2 * (16 / E)), (cuuint32_t)K};
+    const cuuint32_t narrow[2] = {(cuuint32_t)kTmaNarrow, (cuuint32_t)K};
+    CUresult r1 = encode(&out->wide, ty, 2, base, dims, strides, wide, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r2 = encode(&out->narrow, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, narrow, es,
+    CUresult r2 = encode(&out->narrow, ty, 2, base, dims, strides, narrow, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
@@ -296,7 +304,8 @@ inline LevelSetD levelset_view(const lbm_handle *h) {
 // precision- and dimension-specialised operations
 // =============================================================================================
 
-template <typename real, int D> struct Impl {
+template <typename real, int D, typename pop = real> struct Impl {
+    static constexpr bool kPlainPop = std::is_same<real, pop>::value;
     static constexpr int K = D + D * D, Q = 2 * D;
 
     static const real *mtab(lbm_handle *h) {
@@ -384,20 +393,20 @@ template <typename real, int D> struct Impl {
             bool ok = true;
             for (int j = 0; j < 2; ++j) {
                 h->tma_buf[j] = j == 0 ? h->fA : h->fB;
-                ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j]) &&
+                ok = ok && encode_population_maps(h->tma_buf[j], h->box.npad, Q * K, K, &h->tma_maps[j], (int)sizeof(pop)) &&
                      encode_meta_maps(h->ustar, h->box.npad, D, h->flags, h->box.nx,
                                       (long long)h->box.ny * h->box.nz, &h->tma_maps[j]);
             }
             if (ok) {
-                h->tma_smem = kTmaWarps * (TmaLayout<D>::stage_bytes + 8);
-                ok = cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                h->tma_smem = kTmaWindows<pop> * (TmaLayout<D, sizeof(pop)>::stage_bytes + 8);
+                ok = cudaFuncSetAttribute(k_stream_collide_tma<D, pop>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           h->tma_smem) == cudaSuccess &&
-                     cudaFuncSetAttribute(k_stream_collide_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                     cudaFuncSetAttribute(k_stream_collide_tma<D, pop>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess &&
-                     cudaFuncSetAttribute(k_gather_moments_tma<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                     cudaFuncSetAttribute(k_gather_moments_tma<D, pop>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess;
             }
-            if (ok && h->opt.adjoint) {
+            if (ok && h->opt.adjoint && kPlainPop) {
                 h->adj_maps_ok = true;
                 for (int j = 0; j < 2; ++j) {
                     h->adj_maps[j] = h->tma_maps[0];  // flags and u* maps; population maps replaced
@@ -429,7 +438,7 @@ template <typename real, int D> struct Impl {
 
     static int init(lbm_handle *h, int mode, const double *v0, const double *F0, const double *u0, const double *dU0) {
         const double dt = h->grid.dx / h->opt.c;
-        k_init<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
+        k_init<real, D, pop><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
             h->box, h->seg, (int)h->nseg, h->flags, v0, F0, u0, dU0, mode == LBM_INIT_CHARACTERISTIC, h->opt.c, dt,
             h->mat.mu, h->mat.lambda, h->gidx, h->ngroups > 0 ? h->mtab_d : nullptr,
             h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr, h->opt.gamma,
@@ -461,7 +470,7 @@ template <typename real, int D> struct Impl {
         a.status = h->status;
         EventPair ep;
         if (h->timing) timing_begin(h, ep, 1);
-        k_cutlinks<real, D><<<grid_for(h->n_cut, 128), 128, 0, h->stream>>>(a);
+        k_cutlinks<real, D, pop><<<grid_for(h->n_cut, 128), 128, 0, h->stream>>>(a);
         if (h->timing) timing_end(h, ep);
         h->launches++;
         CKL();
@@ -518,33 +527,34 @@ template <typename real, int D> struct Impl {
             if (!proj) {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 0);
-                if (h->phase == 0) k_stream_collide<real, D, 0><<<g, 128, 0, h->stream>>>(a);
+                if (h->phase == 0) k_stream_collide<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
                     if (h->tma_ok)
-                        k_stream_collide_tma<D><<<grid_for(h->nseg, kTmaWarps), 32 * kTmaWarps, h->tma_smem, h->stream>>>(
+                        k_stream_collide_tma<D, pop><<<grid_for(h->nseg, kTmaWindows<pop>), 32, h->tma_smem, h->stream>>>(
                             a, *maps_of(h, h->fA));
                     else
-                        k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
-                } else k_stream_collide<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                        k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
+                } else k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
                 if (h->timing) timing_end(h, ep);
                 h->launches++;
                 CKL();
             } else {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 2);
-                if (h->phase == 0) k_gather_moments<real, D, 0><<<g, 128, 0, h->stream>>>(a);
+                if (h->phase == 0) k_gather_moments<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
                     if (h->tma_ok)
-                        k_gather_moments_tma<D><<<g, 128, TmaLayout<D>::block_bytes(4), h->stream>>>(a, *maps_of(h, h->fA));
+                        k_gather_moments_tma<D, pop><<<g, 128, TmaLayout<D, sizeof(pop)>::block_bytes(4), h->stream>>>(
+                            a, *maps_of(h, h->fA));
                     else
-                        k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
-                } else k_gather_moments<real, D, 1><<<g, 128, 0, h->stream>>>(a);
+                        k_gather_moments<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
+                } else k_gather_moments<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
                 h->launches++;
                 CKL();
                 real *d = nullptr;
                 int rc = solve(h, t, static_cast<const real *>(h->u0), &d);
                 if (rc) return rc;
-                k_repair_collide<real, D><<<g, 128, 0, h->stream>>>(a, static_cast<const real *>(h->u0), d, h->mean,
+                k_repair_collide<real, D, pop><<<g, 128, 0, h->stream>>>(a, static_cast<const real *>(h->u0), d, h->mean,
                                                                      h->opt.theta_F, static_cast<real *>(h->u1));
                 h->launches++;
                 CKL();
@@ -625,8 +635,8 @@ template <typename real, int D> struct Impl {
     static int fields(lbm_handle *h, double *v, double *F, double *u) {
         StepArgs<real> a = step_args(h);
         const unsigned g = grid_for(h->nseg, 4);
-        if (h->phase == 0) k_fields<real, D, 0><<<g, 128, 0, h->stream>>>(a, v, F, u);
-        else k_fields<real, D, 1><<<g, 128, 0, h->stream>>>(a, v, F, u);
+        if (h->phase == 0) k_fields<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a, v, F, u);
+        else k_fields<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a, v, F, u);
         CKL();
         return LBM_OK;
     }

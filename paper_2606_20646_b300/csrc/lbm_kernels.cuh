@@ -11,6 +11,8 @@
 // reconstruction (Eqs. bfl-eta-ge-half, bfl-eta-lt-half) before recovering U^num.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "lbm_device.cuh"
 
 namespace tlv {
@@ -19,6 +21,34 @@ namespace tlv {
 // arithmetic follows the FP64 oracle operation for operation (its translation unit is built
 // without FMA contraction), so the FP64 form reproduces the oracle to rounding.
 template <typename real> constexpr bool kShifted = sizeof(real) == 4;
+
+// Population storage.  The planes hold the arithmetic type itself, or BF16 with FP32 arithmetic
+// (rounded to nearest even on store, widened exactly on load).  StepArgs carries the population
+// pointers typed by the arithmetic type; kernels instantiated for BF16 storage reinterpret them.
+// pop_ld reads through the read-only path (arrays the kernel does not write); pop_ld_rw reads an
+// array the kernel updates in place.
+template <typename pop> struct PopIO {
+    static __device__ __forceinline__ pop ld(const pop *p) { return __ldg(p); }
+    static __device__ __forceinline__ pop ld_rw(const pop *p) { return *p; }
+    static __device__ __forceinline__ void st(pop *p, pop v) { *p = v; }
+};
+template <> struct PopIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_rw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <typename real, typename pop>
+__device__ __forceinline__ real pop_ld(const real *base, long long i) {
+    return (real)PopIO<pop>::ld(reinterpret_cast<const pop *>(base) + i);
+}
+template <typename real, typename pop>
+__device__ __forceinline__ real pop_ld_rw(const real *base, long long i) {
+    return (real)PopIO<pop>::ld_rw(reinterpret_cast<const pop *>(base) + i);
+}
+template <typename real, typename pop>
+__device__ __forceinline__ void pop_st(real *base, long long i, real v) {
+    PopIO<pop>::st(reinterpret_cast<pop *>(base) + i, v);
+}
 
 template <typename real, int D> __device__ __forceinline__ real div2D(real x) {
     if constexpr (kShifted<real>) return x * (real(1) / real(2 * D));
@@ -535,7 +565,7 @@ template <int D> __device__ inline void dpiola64(const double *F, const double *
         }
 }
 
-template <typename real, int D>
+template <typename real, int D, typename pop = real>
 __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint8_t *__restrict__ flags,
                        const double *__restrict__ v0, const double *__restrict__ F0, const double *__restrict__ u0,
                        const double *__restrict__ dU0, int characteristic, double c, double dt, double mu_, double lam_,
@@ -607,7 +637,7 @@ __global__ void k_init(Box b, const int2 *__restrict__ seg, int nseg, const uint
                 for (int B = 0; B < D; ++B)
                     fq[D + i * D + B] -= 0.5 * dt * (Zq[D + i * D + B] - s * (D / c) * (A == B ? Zq[i] : 0.0)) / (2.0 * D);
         }
-        for (int k = 0; k < K; ++k) f[(long long)(q * K + k) * P + node] = (real)fq[k];
+        for (int k = 0; k < K; ++k) pop_st<real, pop>(f, (long long)(q * K + k) * P + node, (real)fq[k]);
     }
     for (int i = 0; i < D; ++i) disp_set<real>(ustar, P, D, i, node, u0[i * N + node] - 0.5 * dt * v0[i * N + node]);
 }
@@ -710,7 +740,7 @@ __device__ __forceinline__ void keep_link_values(real *lfo, long long l0, unsign
 }
 
 // MODE 0: state is pre-collision f^0 (first step, no streaming); MODE 1: state is f*^{n-1}
-template <typename real, int D, int MODE>
+template <typename real, int D, int MODE, typename pop = real>
 __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x, int y, int z, unsigned cut,
                                        real (&f)[2 * D * (D + D * D)]) {
     constexpr int K = D + D * D, Q = 2 * D;
@@ -720,7 +750,7 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
         #pragma unroll
         for (int q = 0; q < Q; ++q)
             #pragma unroll
-            for (int k = 0; k < K; ++k) f[q * K + k] = __ldg(fs + (long long)(q * K + k) * P + node);
+            for (int k = 0; k < K; ++k) f[q * K + k] = pop_ld<real, pop>(fs, (long long)(q * K + k) * P + node);
         return;
     } else {
     #pragma unroll
@@ -728,7 +758,7 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
         if (!((cut >> (q ^ 1)) & 1)) {  // source m - e_q = m + e_{q^1} is active
             const int src = nbr(a.b, node, x, y, z, q ^ 1);
             #pragma unroll
-            for (int k = 0; k < K; ++k) f[q * K + k] = __ldg(fs + (long long)(q * K + k) * P + src);
+            for (int k = 0; k < K; ++k) f[q * K + k] = pop_ld<real, pop>(fs, (long long)(q * K + k) * P + src);
         }
     }
     if (cut) {
@@ -783,7 +813,7 @@ __device__ __forceinline__ void equilibrium(const real v[D], const real X[D * D]
     }
 }
 
-template <typename real, int D>
+template <typename real, int D, typename pop = real>
 __device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node, unsigned cut,
                                               real (&f)[2 * D * (D + D * D)], const real v[D], const real G[D * D],
                                               const real F[D * D], const real Pk[D * D]) {
@@ -818,7 +848,7 @@ __device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node,
                 out[k] = fv + a.omega * (feq - fv);
             }
         #pragma unroll
-        for (int k = 0; k < K; ++k) a.fdst[(long long)(q * K + k) * P + node] = out[k];
+        for (int k = 0; k < K; ++k) pop_st<real, pop>(a.fdst, (long long)(q * K + k) * P + node, out[k]);
         if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
     }
 }
@@ -839,7 +869,7 @@ __device__ __forceinline__ int check_state(const real v[D], const real F[D * D],
 // ---------------------------------------------------------------------------------------------
 // K3: fused gather + closure + recovery + collision (+ u quadrature), one thread per node
 // ---------------------------------------------------------------------------------------------
-template <typename real, int D, int MODE>
+template <typename real, int D, int MODE, typename pop = real>
 __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) {
     constexpr int K = D + D * D, Q = 2 * D;
     const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -854,7 +884,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
     const unsigned cut = fl & kCutMask;
     real f[Q * K];
-    gather<real, D, MODE>(a, node, x, y, z, cut, f);
+    gather<real, D, MODE, pop>(a, node, x, y, z, cut, f);
     real v[D], G[D * D], F[D * D], Pk[D * D];
     recover<real, D>(a, f, v, G, F);
     real mu, lam;
@@ -886,11 +916,11 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
         }
     }
     if (fl & kNeedU) un_store<real, D>(a.un, node, unh, unl);
-    collide_store<real, D>(a, node, cut, f, v, G, F, Pk);
+    collide_store<real, D, pop>(a, node, cut, f, v, G, F, Pk);
 }
 
 // projection steps, part 1: gather + recovery; stores f^n (pre-collision), v^n, G^n, u^n (FP64)
-template <typename real, int D, int MODE>
+template <typename real, int D, int MODE, typename pop = real>
 __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) {
     constexpr int K = D + D * D, Q = 2 * D;
     const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -904,12 +934,12 @@ __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) 
     if (!(fl & kActive)) return;
     const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
     real f[Q * K];
-    gather<real, D, MODE>(a, node, x, y, z, fl & kCutMask, f);
+    gather<real, D, MODE, pop>(a, node, x, y, z, fl & kCutMask, f);
     real v[D], G[D * D], F[D * D];
     recover<real, D>(a, f, v, G, F);
     const long long P = a.b.npad;
     #pragma unroll
-    for (int j = 0; j < Q * K; ++j) a.fdst[(long long)j * P + node] = f[j];
+    for (int j = 0; j < Q * K; ++j) pop_st<real, pop>(a.fdst, (long long)j * P + node, f[j]);
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         a.vst[i * P + node] = v[i];
@@ -927,7 +957,7 @@ __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) 
 }
 
 // field output: v, F, u at the current time (FP64, box planes)
-template <typename real, int D, int MODE>
+template <typename real, int D, int MODE, typename pop = real>
 __global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *vout, double *Fout, double *uout) {
     constexpr int K = D + D * D, Q = 2 * D;
     const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -941,7 +971,7 @@ __global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *
     if (!(fl & kActive)) return;
     const int y = sg.y % a.b.ny, z = sg.y / a.b.ny;
     real f[Q * K];
-    gather<real, D, MODE>(a, node, x, y, z, fl & kCutMask, f);
+    gather<real, D, MODE, pop>(a, node, x, y, z, fl & kCutMask, f);
     real v[D], G[D * D], F[D * D];
     recover<real, D>(a, f, v, G, F);
     const long long N = a.b.nbox, P = a.b.npad;
@@ -1002,7 +1032,7 @@ __device__ __forceinline__ bool traction_residual(const real h[D], const real N[
     return true;
 }
 
-template <typename real, int D>
+template <typename real, int D, typename pop = real>
 __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
     constexpr int K = D + D * D;
     const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1024,7 +1054,7 @@ __global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
         node_xyz(a.b, mnode, x, y, z);
         const int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
         #pragma unroll
-        for (int k = 0; k < K; ++k) fu[k] = a.fstar[(long long)(q * K + k) * a.b.npad + mup];
+        for (int k = 0; k < K; ++k) fu[k] = pop_ld<real, pop>(a.fstar, (long long)(q * K + k) * a.b.npad + mup);
     } else {
         #pragma unroll
         for (int k = 0; k < K; ++k) fu[k] = fo[k];
@@ -1520,7 +1550,7 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__
 // after the first solve: u^n = u0 + d - mean (written to u1), F^c (Eq. projection-compatible-F), F^r
 // (Eq. projection-F-repair-weight), population repair (Eq. projection-population-repair),
 // collision and u*^{n+1}.  f^n is read from and f*^n written to fdst (in place).
-template <typename real, int D>
+template <typename real, int D, typename pop = real>
 __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, const real *__restrict__ u0,
                                                         const real *__restrict__ dc, const double *__restrict__ mean,
                                                         double theta, real *u1) {
@@ -1536,7 +1566,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     real fpre[kPre];
     if constexpr (kPre == Q * K) {
         #pragma unroll
-        for (int j = 0; j < Q * K; ++j) fpre[j] = a.fdst[(long long)j * P + node];
+        for (int j = 0; j < Q * K; ++j) fpre[j] = pop_ld_rw<real, pop>(a.fdst, (long long)j * P + node);
     }
     real v[D], G[D * D], F[D * D], Pold[D * D], Fr[D * D], Gr[D * D], Pk[D * D];
     #pragma unroll
@@ -1605,7 +1635,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         real out[K];
         if constexpr (kPre == K) {
             #pragma unroll
-            for (int k = 0; k < K; ++k) fpre[k] = a.fdst[(long long)(q * K + k) * P + node];
+            for (int k = 0; k < K; ++k) fpre[k] = pop_ld_rw<real, pop>(a.fdst, (long long)(q * K + k) * P + node);
         }
         #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -1630,7 +1660,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
             out[k] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : real(0));
         }
         #pragma unroll
-        for (int k = 0; k < K; ++k) a.fdst[(long long)(q * K + k) * P + node] = out[k];
+        for (int k = 0; k < K; ++k) pop_st<real, pop>(a.fdst, (long long)(q * K + k) * P + node, out[k]);
         if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
     }
     #pragma unroll

@@ -1,5 +1,6 @@
 // Entry points of one precision: defined in lbm_fp64.cu (built with -fmad=false so its
-// arithmetic matches the FP64 oracle operation for operation) and lbm_fp32.cu.
+// arithmetic matches the FP64 oracle operation for operation), lbm_fp32.cu and lbm_bf16s.cu (FP32
+// arithmetic, BF16 population storage).
 #pragma once
 #include "lbm_impl.cuh"
 
@@ -14,3 +15,4 @@ struct PrecOps {
 
 const PrecOps &ops_fp64();
 const PrecOps &ops_fp32();
+const PrecOps &ops_bf16s();

@@ -1,12 +1,14 @@
-// TMA-staged gather for the FP32 fused collide-stream kernel (sm_103a).
+// TMA-staged gather for the fused collide-stream kernel with FP32 arithmetic (sm_103a), for
+// populations stored in FP32 or in BF16.
 //
 // The pull gather of one 32-node x-segment reads, for every direction q, the K component
 // planes of f* at the segment shifted by -e_q.  Population planes are consecutive in a
 // 2D tensor (dim 0: node index, npad; dim 1: plane q*K + k), so the K planes of one
 // direction are one box of (width, K).  One elected lane per warp issues Q bulk tensor
 // copies into the warp's shared-memory slots, completed on a per-warp mbarrier:
-//   +-x: box (40, K) starting 4 nodes before the segment (a TMA start coordinate must be a
-//        multiple of 4 floats, so the +-1 shifted windows are read from an aligned wider box)
+//   +-x: box (40, K) starting 4 nodes before the segment for FP32, (48, K) starting 8 nodes
+//        before it for BF16 (a TMA start coordinate must fall on a 16-byte boundary, so the
+//        +-1 shifted windows are read from an aligned wider box)
 //   +-y, +-z: box (32, K) at the source row (periodic rows wrapped).
 // The wait is bounded; on timeout the kernel latches a status bit, waits once more (bounded)
 // for its copies in flight and returns without writing.
@@ -20,19 +22,24 @@ namespace tlv {
 
 constexpr int kStTimeout = 128;        // device status bit: a TMA wait ran out
 constexpr int kTmaSpin = 1 << 20;      // try_wait polls before giving up
-constexpr int kTmaWide = 40, kTmaNarrow = 32;
+constexpr int kTmaNarrow = 32;
 
-template <int D> struct TmaLayout {
+// stage layout of one warp for population elements of E bytes (4: FP32, 2: BF16).  The +-x boxes
+// start `halo` elements before the segment, since a bulk copy's start coordinate must fall on a
+// 16-byte boundary: 4 floats or 8 BF16 values, so the +-x boxes are 40 or 48 elements wide.
+template <int D, int E = 4> struct TmaLayout {
     static constexpr int K = D + D * D, Q = 2 * D;
-    static constexpr int wide_bytes = ((kTmaWide * K * 4 + 127) / 128) * 128;
-    static constexpr int narrow_bytes = ((kTmaNarrow * K * 4 + 127) / 128) * 128;
+    static constexpr int halo = 16 / E;
+    static constexpr int wide = 32 + 2 * halo;
+    static constexpr int wide_bytes = ((wide * K * E + 127) / 128) * 128;
+    static constexpr int narrow_bytes = ((kTmaNarrow * K * E + 127) / 128) * 128;
     static constexpr int warp_bytes = 2 * wide_bytes + (Q - 2) * narrow_bytes;
-    static constexpr int tx_bytes = 2 * kTmaWide * K * 4 + (Q - 2) * kTmaNarrow * K * 4;
+    static constexpr int tx_bytes = 2 * wide * K * E + (Q - 2) * kTmaNarrow * K * E;
     // byte offset of direction q's slot in a warp region
     __device__ static constexpr int slot(int q) { return q < 2 ? q * wide_bytes : 2 * wide_bytes + (q - 2) * narrow_bytes; }
-    __device__ static constexpr int width(int q) { return q < 2 ? kTmaWide : kTmaNarrow; }
-    // element offset of lane 0's source inside the box row
-    __device__ static constexpr int lane0(int q) { return q == 0 ? 3 : (q == 1 ? 5 : 0); }
+    __device__ static constexpr int width(int q) { return q < 2 ? wide : kTmaNarrow; }
+    // element offset of lane 0's source inside the box row: m - e_x for q = 0, m + e_x for q = 1
+    __device__ static constexpr int lane0(int q) { return q == 0 ? halo - 1 : (q == 1 ? halo + 1 : 0); }
     static constexpr int block_bytes(int warps) { return warps * warp_bytes + warps * 8; }
     // fused-kernel stage: population slots, then u* (hi and lo planes: 2D x 32 floats), flags (32 bytes)
     static constexpr int us_off = warp_bytes;
@@ -81,10 +88,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // Issue the Q bulk copies of segment sg into the warp's slots and wait for them.  Returns false
 // (status latched) if the wait ran out.  Every lane of the warp must call it.
-template <int D>
+template <int D, typename pop = float>
 __device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorMap *wide, const CUtensorMap *narrow,
                                                    char *wsm, uint64_t *bar, int2 sg, int lane, int *status) {
-    using L = TmaLayout<D>;
+    using L = TmaLayout<D, sizeof(pop)>;
     constexpr int K = L::K, Q = L::Q;
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -99,7 +106,7 @@ __device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorM
             const int A = q >> 1, s = (q & 1) ? -1 : 1;  // pull source of direction q is m - s e_A
             int start;
             if (A == 0) {
-                start = sg.x - 4;
+                start = sg.x - L::halo;
             } else if (A == 1) {
                 int yy = y - s;
                 if (b.per[1]) yy = yy < 0 ? yy + b.ny : (yy >= b.ny ? yy - b.ny : yy);
@@ -120,15 +127,21 @@ __device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorM
     return __all_sync(0xffffffffu, ok);
 }
 
-// value of direction q, component k for this lane from the staged slots
-template <int D> __device__ __forceinline__ float &staged(char *wsm, int q, int k, int lane) {
-    using L = TmaLayout<D>;
-    return reinterpret_cast<float *>(wsm + L::slot(q))[k * L::width(q) + L::lane0(q) + lane];
+// value of direction q, component k for this lane in the staged slots (as FP32), and its update
+template <int D, typename pop = float> __device__ __forceinline__ float staged(const char *wsm, int q, int k, int lane) {
+    using L = TmaLayout<D, sizeof(pop)>;
+    const pop v = reinterpret_cast<const pop *>(wsm + L::slot(q))[k * L::width(q) + L::lane0(q) + lane];
+    return (float)v;
+}
+template <int D, typename pop = float>
+__device__ __forceinline__ void stage_put(char *wsm, int q, int k, int lane, float v) {
+    using L = TmaLayout<D, sizeof(pop)>;
+    reinterpret_cast<pop *>(wsm + L::slot(q))[k * L::width(q) + L::lane0(q) + lane] = (pop)v;
 }
 
 // closure with TMA staging: the populations that cut links leave unknown arrive reconstructed by the
 // link kernel (first link of the node l0); the gathered values stay in shared memory
-template <int D>
+template <int D, typename pop = float>
 __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm, int node, int x, int lane,
                                             unsigned cut, long long l0) {
     constexpr int K = D + D * D, Q = 2 * D;
@@ -137,10 +150,12 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
     if (a.b.per[0]) {  // the aligned x windows do not wrap: patch the periodic ends
         if (x == 0 && !((cut >> 1) & 1))
             #pragma unroll
-            for (int k = 0; k < K; ++k) staged<D>(wsm, 0, k, lane) = __ldg(fs + (long long)(0 * K + k) * P + node + a.b.nx - 1);
+            for (int k = 0; k < K; ++k)
+                stage_put<D, pop>(wsm, 0, k, lane, pop_ld<float, pop>(fs, (long long)(0 * K + k) * P + node + a.b.nx - 1));
         if (x == a.b.nx - 1 && !(cut & 1))
             #pragma unroll
-            for (int k = 0; k < K; ++k) staged<D>(wsm, 1, k, lane) = __ldg(fs + (long long)(1 * K + k) * P + node - (a.b.nx - 1));
+            for (int k = 0; k < K; ++k)
+                stage_put<D, pop>(wsm, 1, k, lane, pop_ld<float, pop>(fs, (long long)(1 * K + k) * P + node - (a.b.nx - 1)));
     }
     if (!cut) return;
     #pragma unroll
@@ -149,13 +164,13 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
             float r[K];
             vload<K>(a.lrec + link_of(l0, cut, q ^ 1) * K, r);
             #pragma unroll
-            for (int k = 0; k < K; ++k) staged<D>(wsm, q, k, lane) = r[k];
+            for (int k = 0; k < K; ++k) stage_put<D, pop>(wsm, q, k, lane, r[k]);
         }
     }
 }
 
 struct TmaMaps {
-    CUtensorMap wide, narrow;  // population planes of the source buffer: (40, K) and (32, K) boxes
+    CUtensorMap wide, narrow;  // population planes of the source buffer: (40 or 48, K) and (32, K) boxes
     CUtensorMap ustar;         // u* planes: (32, D) boxes
     CUtensorMap flags;         // flag bytes as (nx, ny*nz): (32, 1) boxes
 };
@@ -164,16 +179,16 @@ struct TmaMaps {
 // Arithmetic is arranged to avoid divisions in the per-node path:
 //   v = (sum f_v + dt/2 b) * 1/(1 + gamma dt/2),  F^{-T} = cof(F) * (1/J),
 //   f*_q = (1 - omega) f_q + omega f^eq_q + src_q with omega f^eq_q = base_k +- (omega D/(2Dc)) Phi_A,k
-template <int D>
+template <int D, typename pop = float>
 __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
                                                const float us[2 * D], long long l0, bool act, float mu, float lam) {
     constexpr int K = D + D * D, Q = 2 * D;
     float S[K];
     #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float s = staged<D>(wsm, 0, k, lane);
+        float s = staged<D, pop>(wsm, 0, k, lane);
         #pragma unroll
-        for (int q = 1; q < Q; ++q) s += staged<D>(wsm, q, k, lane);
+        for (int q = 1; q < Q; ++q) s += staged<D, pop>(wsm, q, k, lane);
         S[k] = s;
     }
     const float hdt = 0.5f * a.dt;
@@ -224,7 +239,6 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     float wv[D];
     #pragma unroll
     for (int i = 0; i < D; ++i) wv[i] = wc * v[i];
-    float *out = a.fdst + node;
     const unsigned cut = fl & kCutMask;
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -243,8 +257,8 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
             } else {
                 t = base[k];
             }
-            o[k] = act ? fmaf(om1, staged<D>(wsm, q, k, lane), t) : 0.0f;
-            out[(long long)(q * K + k) * Pn] = o[k];
+            o[k] = act ? fmaf(om1, staged<D, pop>(wsm, q, k, lane), t) : 0.0f;
+            pop_st<float, pop>(a.fdst, (long long)(q * K + k) * Pn + node, o[k]);
         }
         if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, o);
     }
@@ -257,7 +271,7 @@ struct SegStarts {
     int start[6];
 };
 
-template <int D> __device__ __forceinline__ SegStarts seg_starts(const Box &b, int2 sg) {
+template <int D, int halo> __device__ __forceinline__ SegStarts seg_starts(const Box &b, int2 sg) {
     SegStarts r;
     r.sg = sg;
     const int y = sg.y % b.ny, z = sg.y / b.ny;
@@ -269,7 +283,7 @@ template <int D> __device__ __forceinline__ SegStarts seg_starts(const Box &b, i
         int start = 0;
         if (q < 2 * D) {
             if (A == 0) {
-                start = sg.x - 4;
+                start = sg.x - halo;
             } else if (A == 1) {
                 int yy = y - s;
                 if (b.per[1]) yy = yy < 0 ? yy + b.ny : (yy >= b.ny ? yy - b.ny : yy);
@@ -285,71 +299,105 @@ template <int D> __device__ __forceinline__ SegStarts seg_starts(const Box &b, i
     return r;
 }
 
-// warps (segments) per block of the fused kernel: one, so that a warp's slot frees as soon as that
-// warp is done rather than when the slowest warp of its block is
-constexpr int kTmaWarps = 1;
+// Windows (segments) per warp of the fused kernel.  A warp waits for its copies before it computes,
+// so the bytes an SM has in flight are its resident warps times one warp's staged bytes.  An FP32
+// stage (10 KB in 3D) keeps HBM busy with one window per warp; a BF16 stage is half that, so each
+// warp stages two windows at once, each on its own single-use barrier, and computes them in turn.
+template <typename pop> constexpr int kTmaWindows = sizeof(pop) == 2 ? 2 : 1;
 
-// K3 with TMA staging (FP32): one warp per 32-node segment.  Lane 0 issues the bulk copies of the
-// segment's population boxes, u* box and flag bytes into the warp's stage; every lane waits on the
-// warp's mbarrier (bounded), so no warp can leave while one of its copies is still in flight.
-template <int D>
-__global__ void __launch_bounds__(32 * kTmaWarps, 16 / kTmaWarps) k_stream_collide_tma(const StepArgs<float> a,
-                                                                        const __grid_constant__ TmaMaps maps) {
-    using L = TmaLayout<D>;
+// lane 0: issue the bulk copies of one window (population boxes, u* box, flag bytes) on `bar`
+template <int D, typename pop>
+__device__ __forceinline__ void issue_window(const StepArgs<float> &a, const TmaMaps &maps, char *cur, uint64_t *bar,
+                                             int2 sg) {
+    using L = TmaLayout<D, sizeof(pop)>;
     constexpr int K = L::K, Q = L::Q;
-    extern __shared__ __align__(128) char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sgi = blockIdx.x * kTmaWarps + warp;
-    if (sgi >= a.nseg) return;
-    char *const cur = smem + warp * L::stage_bytes;
-    uint64_t *const bar = reinterpret_cast<uint64_t *>(smem + kTmaWarps * L::stage_bytes) + warp;
-    const int2 sg = __ldg(&a.seg[sgi]);
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        mbar_fence_init();
-        const SegStarts st = seg_starts<D>(a.b, sg);
-        mbar_arrive_expect_tx(bar, L::stage_tx);
-        tma_load_2d(cur + L::us_off, &maps.ustar, bar, st.sg.x, 0);
-        tma_load_2d(cur + L::fl_off, &maps.flags, bar, st.x0, st.sg.y);
-        #pragma unroll
-        for (int q = 0; q < Q; ++q)
-            tma_load_2d(cur + L::slot(q), (q >> 1) == 0 ? &maps.wide : &maps.narrow, bar, st.start[q], q * K);
-    }
-    // first cut link of each node (used by boundary nodes only), fetched while the copies are in
-    // flight; lanes past the end of the last row read a clamped index and never use it
-    const int node = sg.x + lane;
-    const long long l0pre = __ldg(a.lstart + (node < a.b.npad ? node : a.b.npad - 1));
-    const int gpre = a.mtab ? __ldg(a.mat + (node < a.b.npad ? node : a.b.npad - 1)) : 0;
-    __syncwarp();
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
-        if (lane == 0) set_status(a.status, kStTimeout);
-        mbar_wait_bounded(bar, 0);  // let the copies in flight land before the warp exits
-        return;
-    }
-    // Every lane inside the row stores: inactive nodes receive zeros, so each warp writes whole
-    // 32-byte sectors of every plane (a partly written sector costs the memory system a read of
-    // the rest).  Nothing reads an inactive node's populations or u*: pulls across cut links are
-    // replaced by the closure.  Lanes past the row end belong to the next row and store nothing.
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    const SegStarts st = seg_starts<D, L::halo>(a.b, sg);
+    mbar_arrive_expect_tx(bar, L::stage_tx);
+    tma_load_2d(cur + L::us_off, &maps.ustar, bar, st.sg.x, 0);
+    tma_load_2d(cur + L::fl_off, &maps.flags, bar, st.x0, st.sg.y);
+    #pragma unroll
+    for (int q = 0; q < Q; ++q)
+        tma_load_2d(cur + L::slot(q), (q >> 1) == 0 ? &maps.wide : &maps.narrow, bar, st.start[q], q * K);
+}
+
+// one staged window: closure, recovery, collision, stores.  Every lane inside the row stores:
+// inactive nodes receive zeros, so each warp writes whole 32-byte sectors of every plane (a partly
+// written sector costs the memory system a read of the rest).  Nothing reads an inactive node's
+// populations or u*: pulls across cut links are replaced by the closure.  Lanes past the row end
+// belong to the next row and store nothing.
+template <int D, typename pop>
+__device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *cur, int2 sg, int lane, long long l0pre,
+                                               int gpre) {
+    using L = TmaLayout<D, sizeof(pop)>;
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
+    const int node = sg.x + lane;
     const uint8_t fl = reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane];
     const bool act = fl & kActive;
     float us[2 * D];
     #pragma unroll
     for (int d = 0; d < 2 * D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
     const long long l0 = (fl & kCutMask) ? l0pre : 0;
-    if (act) tma_closure<D>(a, cur, node, x, lane, fl & kCutMask, l0);
+    if (act) tma_closure<D, pop>(a, cur, node, x, lane, fl & kCutMask, l0);
     float mu = a.mtab ? a.mtab[2 * gpre] : a.mu;
     const float lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
     if (a.mu_field) mu = a.mu_field[node];
-    collide_staged<D>(a, cur, node, lane, fl, us, l0, act, mu, lam);
+    collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
+}
+
+// K3 with TMA staging (FP32 arithmetic): one warp per block, kTmaWindows<pop> 32-node windows per
+// warp.  Lane 0 issues the bulk copies of the warp's windows; every lane waits on each window's
+// barrier (bounded) before computing it, so no warp can leave while one of its copies is in flight.
+template <int D, typename pop = float>
+__global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<float> a,
+                                                              const __grid_constant__ TmaMaps maps) {
+    using L = TmaLayout<D, sizeof(pop)>;
+    constexpr int NW = kTmaWindows<pop>;
+    extern __shared__ __align__(128) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int sg0 = blockIdx.x * NW;
+    if (sg0 >= a.nseg) return;
+    const int nw = min(NW, a.nseg - sg0);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(smem + NW * L::stage_bytes);
+    int2 sg[NW];
+    #pragma unroll
+    for (int w = 0; w < NW; ++w) sg[w] = w < nw ? __ldg(&a.seg[sg0 + w]) : make_int2(0, 0);
+    if (lane == 0)
+        #pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (w < nw) issue_window<D, pop>(a, maps, smem + w * L::stage_bytes, bars + w, sg[w]);
+    // first cut link and group of each node (used by boundary nodes and multi-specimen bodies),
+    // fetched while the copies are in flight; lanes past the end of the last row read a clamped
+    // index and never use it
+    long long l0pre[NW];
+    int gpre[NW];
+    #pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int node = sg[w].x + lane;
+        const int nc = node < a.b.npad ? node : a.b.npad - 1;
+        l0pre[w] = __ldg(a.lstart + nc);
+        gpre[w] = a.mtab ? __ldg(a.mat + nc) : 0;
+    }
+    __syncwarp();
+    #pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (w >= nw) break;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + w, 0))) {
+            if (lane == 0) set_status(a.status, kStTimeout);
+            for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
+            return;
+        }
+        collide_window<D, pop>(a, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w]);
+    }
 }
 
 // projection steps, part 1, with TMA staging (FP32)
-template <int D>
+template <int D, typename pop = float>
 __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
     constexpr int K = D + D * D, Q = 2 * D;
-    using L = TmaLayout<D>;
+    using L = TmaLayout<D, sizeof(pop)>;
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sgi = blockIdx.x * 4 + warp;
@@ -357,23 +405,23 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     char *wsm = smem + warp * L::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
     const int2 sg = __ldg(&a.seg[sgi]);
-    if (!tma_gather_segment<D>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
+    if (!tma_gather_segment<D, pop>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
     const int node = sg.x + lane;
     const uint8_t fl = __ldg(a.flags + node);
     if (!(fl & kActive)) return;
-    tma_closure<D>(a, wsm, node, x, lane, fl & kCutMask, (fl & kCutMask) ? __ldg(a.lstart + node) : 0);
+    tma_closure<D, pop>(a, wsm, node, x, lane, fl & kCutMask, (fl & kCutMask) ? __ldg(a.lstart + node) : 0);
     const long long P = a.b.npad;
     float v[D];
     #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float s = staged<D>(wsm, 0, k, lane);
-        a.fdst[(long long)(0 * K + k) * P + node] = s;
+        float s = staged<D, pop>(wsm, 0, k, lane);
+        pop_st<float, pop>(a.fdst, (long long)(0 * K + k) * P + node, s);
         #pragma unroll
         for (int q = 1; q < Q; ++q) {
-            const float fq = staged<D>(wsm, q, k, lane);
-            a.fdst[(long long)(q * K + k) * P + node] = fq;
+            const float fq = staged<D, pop>(wsm, q, k, lane);
+            pop_st<float, pop>(a.fdst, (long long)(q * K + k) * P + node, fq);
             s += fq;
         }
         if (k < D) v[k] = (s + 0.5f * a.dt * a.bf[k]) / (1.0f + 0.5f * a.dt * a.gamma);

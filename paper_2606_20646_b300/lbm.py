@@ -20,7 +20,7 @@ _SHAPE = {"sphere": 0, "ellipsoid": 1, "superellipse": 2, "cylinder": 3, "halfsp
 _BCKIND = {"dirichlet": 0, "neumann": 1}
 _PROFILE = {"zero": 0, "affine": 1, "radial": 2, "twist_stretch": 3, "const": 4}
 _RAMP = {"one": 0, "linear": 1, "sin2": 2, "cos": 3, "time": 4}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "bf16s": 2}
 DEV_STATUS = {1: "nonfinite", 2: "jacobian", 4: "newton", 8: "lsq", 16: "capacity", 128: "timeout"}
 MAX_SHAPES = 16
 MAX_BCS = 16

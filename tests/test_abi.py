@@ -86,3 +86,20 @@ def test_group_descriptors_validated_without_gpu(lib):
     assert lib.lbm_create(*args()) == -1
     n = [C.c_longlong(0) for _ in range(3)]
     assert lib.lbm_census_static(C.byref(g), C.byref(ls), None, *[C.byref(x) for x in n]) == -1
+
+
+def test_bf16_storage_descriptors_without_gpu(lib):
+    """The BF16-storage form is a valid precision; it does not take the reverse mode; unknown
+    precisions are refused.  All checked before any device work."""
+    from paper_2606_20646_b300 import inputs as I, lbm
+    p = I.shell_3d(32)
+    g, shapes, ls, mat, bcs, opt = lbm.descriptors(p, precision="bf16s")
+    h = C.c_void_p()
+    args = lambda: (C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None, C.byref(h))
+    assert opt.precision == 2
+    assert lib.lbm_create(*args()) == -4           # valid descriptors, no storage given
+    opt.adjoint = 1
+    assert lib.lbm_create(*args()) == -1
+    opt.adjoint = 0
+    opt.precision = 3
+    assert lib.lbm_create(*args()) == -1

@@ -1,0 +1,88 @@
+"""BF16 population storage (precision "bf16s"): FP32 arithmetic, the shifted populations
+f - f^eq(0, I) stored as BF16, against the FP64 form (itself equal to the FP64 oracle to 1e-12).
+
+BF16 keeps 8 significant bits: each stored population carries a relative rounding error of at most
+2^-9 (1.95e-3) of its shifted value, every step.  The moments sum 2D such values and the collision
+conserves v and F, so the moments keep the accumulated rounding: the measured relative L2 errors
+sit at one to six times 2^-9 (v 4.4e-3, F - I 2.5e-3, u 2.3e-4 on the shell at t = 1).  The bounds
+below are twice the measured errors, rounded up.  Every other array (cut-link values, u*, the
+projection) keeps its FP32 form, so the FP32 form's parity is untouched by this option.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_20646_b300 import inputs as I
+from parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_20646_b300 import build
+    build.build()
+
+
+def _run(p, precision, steps):
+    from paper_2606_20646_b300 import lbm
+    sim = lbm.Simulation(p, precision=precision)
+    sim.set_initial().step(steps)
+    v, F, u = [t.cpu().numpy().astype(np.float64) for t in sim.fields()]
+    act = sim.active_mask()
+    info = sim.info()
+    nbytes = sim.state_bytes()
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
+    return v, F, u, act, info, nbytes
+
+
+def _errors(p, a, b):
+    D = p.dim
+    eye = np.eye(D).reshape((D * D,) + (1,) * D)
+    act = b[3]
+    return (rel_l2(a[0], b[0], act), rel_l2(a[1] - eye, b[1] - eye, act), rel_l2(a[2], b[2], act))
+
+
+@pytest.mark.parametrize("n,steps,bounds", [(64, 320, (1e-2, 6e-3, 5e-4))])
+def test_shell_bf16_storage_against_fp64(n, steps, bounds):
+    """The 3D shell (Neumann links, projection every 20 steps, TMA-staged kernels with two windows
+    per warp) at t = 1."""
+    p = I.shell_3d(n)
+    ref = _run(p, "fp64", steps)
+    b16 = _run(p, "bf16s", steps)
+    ev, eF, eu = _errors(p, b16, ref)
+    print(f"shell {n}^3 BF16 storage vs FP64 at t=1: v {ev:.3e}, F-I {eF:.3e}, u {eu:.3e}")
+    assert ev < bounds[0] and eF < bounds[1] and eu < bounds[2]
+    assert b16[4]["n_active"] == ref[4]["n_active"]
+
+
+def test_periodic_bf16_storage_against_fp64():
+    """Periodic 2D box, 2000 steps: the periodic x ends of the staged windows in BF16."""
+    p = I.random_periodic(2, 64, 1)
+    ref = _run(p, "fp64", 2000)
+    b16 = _run(p, "bf16s", 2000)
+    ev, eF, eu = _errors(p, b16, ref)
+    print(f"periodic 64^2 BF16 storage vs FP64, 2000 steps: v {ev:.3e}, F-I {eF:.3e}, u {eu:.3e}")
+    assert ev < 3e-2 and eF < 3e-2 and eu < 1e-2
+
+
+def test_ragged_box_bf16_storage_against_fp64():
+    """Ragged box (48 x 51 x 53) with mixed Dirichlet/Neumann links and three projection steps;
+    an odd or even number of windows leaves the last warp one window or two."""
+    p = I.random_box(3, 48, 2)
+    ref = _run(p, "fp64", 60)
+    b16 = _run(p, "bf16s", 60)
+    ev, eF, eu = _errors(p, b16, ref)
+    print(f"random box BF16 storage vs FP64, 60 steps: v {ev:.3e}, F-I {eF:.3e}, u {eu:.3e}")
+    assert ev < 2e-2 and eF < 2e-2 and eu < 2e-2
+
+
+def test_bf16_storage_halves_the_population_bytes():
+    p = I.shell_3d(32)
+    nbytes = {prec: _run(p, prec, 1)[5] for prec in ("fp32", "bf16s")}
+    # saved state = header + populations + u* + u^n + link values: the populations halve
+    from paper_2606_20646_b300 import lbm
+    sim = lbm.Simulation(p, precision="fp32")
+    npad = sim.info()["n_box"]
+    sim.close()
+    assert nbytes["fp32"] - nbytes["bf16s"] >= 72 * 2 * npad
