@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
     ap.add_argument("--batch-steps", type=int, default=1000)
@@ -273,6 +274,8 @@ def run_ours(args, world, rank, local):
     st_warm = sim.sync(raise_on_status=False)
     if st_warm:
         raise SystemExit(f"device status {st_warm} after warm-up; not timing a failing step")
+    # tile shapes by the library's autotuner (timed from the warm state, which it restores)
+    tuning = sim.autotune(steps=20) if not args.no_autotune else sim.get_tuning()
     ms, launches, kt, clocks = timed(sim, K, True)
     st = sim.sync(raise_on_status=False)
     info = sim.info()
@@ -316,6 +319,7 @@ def run_ours(args, world, rank, local):
         sim = lbm.Simulation(p, precision="bf16s", device=dev)
         sim.set_initial()
         sim.step(W)
+        tune_b = sim.autotune(steps=20) if not args.no_autotune else sim.get_tuning()
         msb, _, ktb, _ = timed(sim, K, True)
         avgb = ktb["stream_collide_ms"] / max(ktb["stream_collide_launches"], 1)
         bpn = bytes_per_node(3, 2)
@@ -343,7 +347,7 @@ def run_ours(args, world, rank, local):
                 "stream_collide_GBps": round(gbb, 1), "frac": round(gbb / peak, 4), "peak_kind": peak_kind,
                 "error_vs_fp64": {"workload": "shell_3d_128 at t = 1 (640 steps)", "v": rel(vb, vd),
                                   "F_minus_I": rel(Fb - eye, Fd - eye), "u": rel(ub, ud)},
-                "device_status": stb}
+                "tuning": tune_b, "device_status": stb}
         del res
         torch.cuda.empty_cache()
 
@@ -384,6 +388,7 @@ def run_ours(args, world, rank, local):
         sim.set_initial()
         sim.step(W)
         st_b = sim.sync(raise_on_status=False)
+        tune_g = sim.autotune(steps=20) if not args.no_autotune else sim.get_tuning()
         Kb = args.batch_steps
         stream = sim.stream
         torch.cuda.synchronize()
@@ -412,7 +417,7 @@ def run_ours(args, world, rank, local):
                  "graph_ms": round(ms_g, 2), "graph_wall_s": round(wall, 3),
                  "note": "value over graph_ms: CUDA events around lbm_step_graph, host capture and instantiation included",
                  "stepwise_ms_per_step": round(ms_s / Kb, 4), "graph_ms_per_step": round(ms_g / Kb, 4),
-                 "device_status": st_b}
+                 "tuning": tune_g, "device_status": st_b}
         del sim
         torch.cuda.empty_cache()
 
@@ -517,7 +522,7 @@ def run_ours(args, world, rank, local):
                                        "projection every 20 steps",
                            "n_active": nact, "n_cut_links": info["n_cut"], "lsq_entries": info["lsq_entries"],
                            "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}", "tuning": tuning},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
                 "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "bf16": bf16, "batch_2d": batch,

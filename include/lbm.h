@@ -266,6 +266,35 @@ int lbm_step(lbm_handle *h, int nsteps);
  * instantiation or launch failed). */
 int lbm_step_graph(lbm_handle *h, int nsteps);
 
+/* ---- tile shapes ---------------------------------------------------------------------------
+ * No counterpart in the paper.  Every choice below computes the same values node for node (the
+ * fields are bit-identical); only the launch shape differs.  0 selects the form's default. */
+typedef struct lbm_tuning {
+    int windows_per_warp; /* fused kernel (bulk-copy forms): 32-node windows one warp stages at
+                             once, 1, 2 or 4 (default 1 for FP32, 2 for BF16S)                  */
+    int jacobi_segments;  /* projection sweeps: 32-node segments per warp, 1, 2 or 4 (default 2) */
+    int link_block;       /* link kernel: threads per block, 64, 128 or 256 (default 128)        */
+    int candidates;       /* lbm_autotune: configurations it timed                              */
+    double ms_per_step;   /* lbm_autotune: the chosen configuration's time per step             */
+    double default_ms_per_step; /* lbm_autotune: the defaults' time per step                     */
+} lbm_tuning;
+
+/* Sets the tile shapes (the last three fields are ignored).  Errors: LBM_ERR_ARG (a value outside
+ * its list). */
+int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t);
+int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t);
+
+/* Autotuner: from the current state, times `steps` steps (CUDA events on the handle's stream, one
+ * untimed step first) for each candidate shape, coordinate by coordinate (windows per warp, then
+ * Jacobi segments when the body has Neumann links, then the link block when it has cut links),
+ * restoring the state after each run from `scratch` (lbm_state_bytes bytes of device memory, 256-byte
+ * aligned; the library allocates nothing), keeps the fastest shapes and reports them in *out (may
+ * be NULL).  The state on return is the state on entry.  Synchronises.  steps should cover a
+ * projection step when the body has one (steps >= proj_every).  Errors: LBM_ERR_ARG, LBM_ERR_STATE
+ * (not initialised, timing on, or a reverse sweep in progress), LBM_ERR_CUDA, LBM_ERR_DEVICE (a run
+ * latched a device status; the state is restored). */
+int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out);
+
 /* ---- parameters, saved states and reverse mode --------------------------------------------
  * No counterpart in the paper: gradients of a loss on the final displacement with respect to a
  * per-node shear modulus and the body force, by the discrete adjoint of the steps (reverse

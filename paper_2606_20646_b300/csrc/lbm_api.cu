@@ -452,6 +452,106 @@ int lbm_step_graph(lbm_handle *h, int nsteps) {
     return LBM_OK;
 }
 
+// ---- tile shapes and the autotuner ----------------------------------------------------------
+
+static bool one_of(int v, int a, int b, int c) { return v == 0 || v == a || v == b || v == c; }
+
+int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t) {
+    if (!h || !t) return LBM_ERR_ARG;
+    if (!one_of(t->windows_per_warp, 1, 2, 4) || !one_of(t->jacobi_segments, 1, 2, 4) ||
+        !one_of(t->link_block, 64, 128, 256))
+        return LBM_ERR_ARG;
+    h->tune_nw = t->windows_per_warp;
+    h->tune_jseg = t->jacobi_segments;
+    h->tune_lblock = t->link_block;
+    return LBM_OK;
+}
+
+int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t) {
+    if (!h || !t) return LBM_ERR_ARG;
+    std::memset(t, 0, sizeof(*t));
+    t->windows_per_warp = h->tma_ok ? (h->tune_nw ? h->tune_nw : (h->pop_size == 2 ? 2 : 1)) : 0;
+    t->jacobi_segments = h->tune_jseg ? h->tune_jseg : 2;
+    t->link_block = h->tune_lblock ? h->tune_lblock : 128;
+    return LBM_OK;
+}
+
+// restores the saved state, takes one untimed step with the current shapes, then times `steps`
+// steps on the handle's stream; a latched device status ends the tuning
+static int time_shapes(lbm_handle *h, int steps, void *scratch, double *ms_per_step) {
+    int rc = lbm_load_state(h, scratch);
+    if (rc) return rc;
+    rc = ops(h).step(h, 1);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LBM_ERR_CUDA;
+    }
+    cudaEventRecord(e0, h->stream);
+    rc = ops(h).step(h, steps);
+    cudaEventRecord(e1, h->stream);
+    float ms = 0.0f;
+    const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (!ok) return LBM_ERR_CUDA;
+    rc = lbm_sync(h, nullptr);
+    if (rc) return rc;
+    *ms_per_step = (double)ms / steps;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
+    if (!h || steps < 1 || !scratch || (reinterpret_cast<uintptr_t>(scratch) % kAlign)) return LBM_ERR_ARG;
+    if (!h->initialized || h->timing || (h->opt.adjoint && h->adj_next >= 0)) return LBM_ERR_STATE;
+    int rc = lbm_save_state(h, scratch);
+    if (rc) return rc;
+    int *const shape[3] = {&h->tune_nw, &h->tune_jseg, &h->tune_lblock};
+    const int saved[3] = {h->tune_nw, h->tune_jseg, h->tune_lblock};
+    const int cand[3][3] = {{1, 2, 4}, {1, 2, 4}, {64, 128, 256}};
+    const int dflt[3] = {h->pop_size == 2 ? 2 : 1, 2, 128};
+    const bool used[3] = {h->tma_ok, h->n_neu > 0 && h->opt.proj_every > 0, h->n_cut > 0};
+    for (int c = 0; c < 3; ++c) *shape[c] = 0;
+    double best = 0.0;
+    int count = 0;
+    rc = time_shapes(h, steps, scratch, &best);
+    count++;
+    const double def_ms = best;
+    // coordinate by coordinate; a candidate must beat the best by 1 % to replace it
+    for (int c = 0; c < 3 && rc == LBM_OK; ++c) {
+        if (!used[c]) continue;
+        int chosen = 0;
+        for (int i = 0; i < 3 && rc == LBM_OK; ++i) {
+            if (cand[c][i] == dflt[c]) continue;
+            *shape[c] = cand[c][i];
+            double ms = 0.0;
+            rc = time_shapes(h, steps, scratch, &ms);
+            count++;
+            if (rc == LBM_OK && ms < 0.99 * best) {
+                best = ms;
+                chosen = cand[c][i];
+            }
+        }
+        *shape[c] = chosen;
+    }
+    const int rl = lbm_load_state(h, scratch);
+    if (rc != LBM_OK) {
+        for (int c = 0; c < 3; ++c) *shape[c] = saved[c];
+        return rc;
+    }
+    if (rl) return rl;
+    if (out) {
+        lbm_get_tuning(h, out);
+        out->candidates = count;
+        out->ms_per_step = best;
+        out->default_ms_per_step = def_ms;
+    }
+    return LBM_OK;
+}
+
 int lbm_set_mu_field(lbm_handle *h, const double *mu) {
     if (!h || !mu) return LBM_ERR_ARG;
     if (!h->bound || !h->opt.adjoint) return LBM_ERR_STATE;

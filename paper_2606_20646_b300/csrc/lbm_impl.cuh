@@ -111,9 +111,11 @@ struct lbm_handle {
     long long launches = 0;
     // TMA staging of the FP32 gather: tensor maps of both population buffers
     bool tma_ok = false;
-    int tma_smem = 0;  // dynamic shared memory of the fused kernel's blocks
     void *tma_buf[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
+    // tile shapes (0: the form's default): 32-node windows per warp of the fused kernel, segments
+    // per warp of a Jacobi sweep, threads per block of the link kernel
+    int tune_nw = 0, tune_jseg = 0, tune_lblock = 0;
     // timing
     bool timing = false;
     std::vector<EventPair> events;
@@ -397,15 +399,10 @@ template <typename real, int D, typename pop = real> struct Impl {
                      encode_meta_maps(h->ustar, h->box.npad, D, h->flags, h->box.nx,
                                       (long long)h->box.ny * h->box.nz, &h->tma_maps[j]);
             }
-            if (ok) {
-                h->tma_smem = kTmaWindows<pop> * (TmaLayout<D, sizeof(pop)>::stage_bytes + 8);
-                ok = cudaFuncSetAttribute(k_stream_collide_tma<D, pop>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          h->tma_smem) == cudaSuccess &&
-                     cudaFuncSetAttribute(k_stream_collide_tma<D, pop>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
-                         cudaSuccess &&
+            if (ok)
+                ok = fused_attr<1>() && fused_attr<2>() && fused_attr<4>() &&
                      cudaFuncSetAttribute(k_gather_moments_tma<D, pop>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
                          cudaSuccess;
-            }
             if (ok && h->opt.adjoint && kPlainPop) {
                 h->adj_maps_ok = true;
                 for (int j = 0; j < 2; ++j) {
@@ -420,6 +417,33 @@ template <typename real, int D, typename pop = real> struct Impl {
             cudaGetLastError();
             h->tma_ok = ok;
         }
+    }
+
+    template <int NW> static int fused_smem() { return NW * (TmaLayout<D, sizeof(pop)>::stage_bytes + 8); }
+    template <int NW> static bool fused_attr() {
+        return cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    fused_smem<NW>()) == cudaSuccess &&
+               cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    100) == cudaSuccess;
+    }
+    // the fused kernel with the handle's windows per warp
+    template <int NW> static void launch_fused_nw(lbm_handle *h, const StepArgs<float> &a) {
+        k_stream_collide_tma<D, pop, NW><<<grid_for(h->nseg, NW), 32, fused_smem<NW>(), h->stream>>>(a, *maps_of(h, h->fA));
+    }
+    static void launch_fused(lbm_handle *h, const StepArgs<float> &a) {
+        const int nw = h->tune_nw ? h->tune_nw : kTmaWindows<pop>;
+        if (nw == 4) launch_fused_nw<4>(h, a);
+        else if (nw == 2) launch_fused_nw<2>(h, a);
+        else launch_fused_nw<1>(h, a);
+    }
+    template <int S> static void launch_jacobi_s(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
+        k_jacobi<real, D, S><<<grid_for(h->nseg, 4 * S), 128, 0, h->stream>>>(p, src, dst);
+    }
+    static void launch_jacobi(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
+        const int js = h->tune_jseg ? h->tune_jseg : kJacobiSegs;
+        if (js == 4) launch_jacobi_s<4>(h, p, src, dst);
+        else if (js == 1) launch_jacobi_s<1>(h, p, src, dst);
+        else launch_jacobi_s<2>(h, p, src, dst);
     }
 
     static const TmaMaps *maps_of(lbm_handle *h, const void *buf) {
@@ -470,7 +494,8 @@ template <typename real, int D, typename pop = real> struct Impl {
         a.status = h->status;
         EventPair ep;
         if (h->timing) timing_begin(h, ep, 1);
-        k_cutlinks<real, D, pop><<<grid_for(h->n_cut, 128), 128, 0, h->stream>>>(a);
+        const int lb = h->tune_lblock ? h->tune_lblock : 128;
+        k_cutlinks<real, D, pop><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a);
         if (h->timing) timing_end(h, ep);
         h->launches++;
         CKL();
@@ -489,11 +514,10 @@ template <typename real, int D, typename pop = real> struct Impl {
         real *A = static_cast<real *>(h->dA), *B = static_cast<real *>(h->dB);
         const real *src = nullptr;
         real *dst = A;
-        const unsigned gj = grid_for(h->nseg, 4 * kJacobiSegs);
         EventPair ep;
         if (h->timing && h->opt.proj_iters > 0) timing_begin(h, ep, 3, h->opt.proj_iters);
         for (int it = 0; it < h->opt.proj_iters; ++it) {
-            k_jacobi<real, D><<<gj, 128, 0, h->stream>>>(p, src, dst);
+            launch_jacobi(h, p, src, dst);
             h->launches++;
             src = dst;
             dst = (dst == A) ? B : A;
@@ -530,8 +554,7 @@ template <typename real, int D, typename pop = real> struct Impl {
                 if (h->phase == 0) k_stream_collide<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
                     if (h->tma_ok)
-                        k_stream_collide_tma<D, pop><<<grid_for(h->nseg, kTmaWindows<pop>), 32, h->tma_smem, h->stream>>>(
-                            a, *maps_of(h, h->fA));
+                        launch_fused(h, a);
                     else
                         k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
                 } else k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);

@@ -1033,7 +1033,7 @@ __device__ __forceinline__ bool traction_residual(const real h[D], const real N[
 }
 
 template <typename real, int D, typename pop = real>
-__global__ void __launch_bounds__(128) k_cutlinks(const CutArgs<real> a) {
+__global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
     constexpr int K = D + D * D;
     const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (l >= a.L.ncut) return;
@@ -1405,18 +1405,18 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
     st_vec<4, real>(a.resid + 4 * (long long)node, out);
 }
 
-constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep
+constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep (default; lbm_autotune may pick 1 or 4)
 
 // One damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr),
 //   d'_m = (1 - beta) d_m + beta / deg_m (r_m + sum over active axis neighbours l of d_l),
-// warp w handling segments kJacobiSegs*w .. kJacobiSegs*w + kJacobiSegs - 1.  A node is its flag
+// warp w handling segments S*w .. S*w + S - 1.  A node is its flag
 // byte, one residual vector, its own d vector and 2D neighbour d vectors, all loaded before any is
 // used; a neighbour across a cut link (inactive, or outside a non-periodic box, where the index is
 // clamped into range) is dropped by selection, as a skipped term; nodes with w = 0 keep their d
 // and are not written.
-template <typename real, int D>
+template <typename real, int D, int S = kJacobiSegs>
 __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
-    constexpr int S = kJacobiSegs, Q = 2 * D, V = kDV<D>;
+    constexpr int Q = 2 * D, V = kDV<D>;
     const int lane = threadIdx.x & 31;
     const int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
     if (s0 >= a.nseg) return;

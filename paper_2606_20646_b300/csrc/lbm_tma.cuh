@@ -299,10 +299,11 @@ template <int D, int halo> __device__ __forceinline__ SegStarts seg_starts(const
     return r;
 }
 
-// Windows (segments) per warp of the fused kernel.  A warp waits for its copies before it computes,
-// so the bytes an SM has in flight are its resident warps times one warp's staged bytes.  An FP32
-// stage (10 KB in 3D) keeps HBM busy with one window per warp; a BF16 stage is half that, so each
-// warp stages two windows at once, each on its own single-use barrier, and computes them in turn.
+// Windows (segments) per warp of the fused kernel: the tile a warp stages at once, each window on its
+// own single-use barrier, computed in turn.  A warp waits for its copies before it computes, so the
+// bytes an SM has in flight are its resident warps times one warp's staged bytes.  An FP32 stage
+// (10 KB in 3D) keeps HBM busy with one window per warp; a BF16 stage is half that, so the BF16
+// default stages two.  lbm_autotune times 1, 2 and 4 on the caller's workload.
 template <typename pop> constexpr int kTmaWindows = sizeof(pop) == 2 ? 2 : 1;
 
 // lane 0: issue the bulk copies of one window (population boxes, u* box, flag bytes) on `bar`
@@ -347,14 +348,12 @@ __device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *c
     collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 
-// K3 with TMA staging (FP32 arithmetic): one warp per block, kTmaWindows<pop> 32-node windows per
-// warp.  Lane 0 issues the bulk copies of the warp's windows; every lane waits on each window's
+// K3 with TMA staging (FP32 arithmetic): one warp per block, NW 32-node windows per warp.  Lane 0 issues the bulk copies of the warp's windows; every lane waits on each window's
 // barrier (bounded) before computing it, so no warp can leave while one of its copies is in flight.
-template <int D, typename pop = float>
+template <int D, typename pop = float, int NW = kTmaWindows<pop>>
 __global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<float> a,
                                                               const __grid_constant__ TmaMaps maps) {
     using L = TmaLayout<D, sizeof(pop)>;
-    constexpr int NW = kTmaWindows<pop>;
     extern __shared__ __align__(128) char smem[];
     const int lane = threadIdx.x & 31;
     const int sg0 = blockIdx.x * NW;

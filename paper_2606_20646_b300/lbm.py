@@ -76,6 +76,11 @@ class lbm_kernel_time(C.Structure):
                 ("projection_launches", C.c_longlong), ("jacobi_ms", C.c_double), ("jacobi_launches", C.c_longlong)]
 
 
+class lbm_tuning(C.Structure):
+    _fields_ = [("windows_per_warp", C.c_int), ("jacobi_segments", C.c_int), ("link_block", C.c_int),
+                ("candidates", C.c_int), ("ms_per_step", C.c_double), ("default_ms_per_step", C.c_double)]
+
+
 # symbol -> (restype, argtypes); every entry point declared in include/lbm.h
 _vp, _d, _i, _sz = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_size_t)
 SIGNATURES = {
@@ -92,6 +97,9 @@ SIGNATURES = {
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
     "lbm_enable_timing": (C.c_int, [_vp, C.c_int]),
     "lbm_step_graph": (C.c_int, [_vp, C.c_int]),
+    "lbm_set_tuning": (C.c_int, [_vp, C.POINTER(lbm_tuning)]),
+    "lbm_get_tuning": (C.c_int, [_vp, C.POINTER(lbm_tuning)]),
+    "lbm_autotune": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(lbm_tuning)]),
     "lbm_set_mu_field": (C.c_int, [_vp, _vp]),
     "lbm_set_body_force": (C.c_int, [_vp, _d]),
     "lbm_state_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
@@ -311,6 +319,29 @@ class Simulation:
         """n steps captured as one CUDA graph and launched once (lbm_step_graph)."""
         _check(load_library().lbm_step_graph(self.h, int(n)), "lbm_step_graph")
         return self
+
+    # -- tile shapes -----------------------------------------------------------------------------
+    _TUNE_KEYS = ("windows_per_warp", "jacobi_segments", "link_block", "candidates", "ms_per_step",
+                  "default_ms_per_step")
+
+    def get_tuning(self) -> dict:
+        t = lbm_tuning()
+        _check(load_library().lbm_get_tuning(self.h, C.byref(t)), "lbm_get_tuning")
+        return {k: getattr(t, k) for k in self._TUNE_KEYS[:3]}
+
+    def set_tuning(self, windows_per_warp: int = 0, jacobi_segments: int = 0, link_block: int = 0):
+        t = lbm_tuning(windows_per_warp, jacobi_segments, link_block, 0, 0.0, 0.0)
+        _check(load_library().lbm_set_tuning(self.h, C.byref(t)), "lbm_set_tuning")
+        return self
+
+    def autotune(self, steps: int = 20) -> dict:
+        """Times the candidate tile shapes on this simulation from its current state (restored
+        afterwards) and keeps the fastest (lbm_autotune)."""
+        scratch = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        t = lbm_tuning()
+        _check(load_library().lbm_autotune(self.h, int(steps), _ptr(scratch), C.byref(t)), "lbm_autotune")
+        del scratch
+        return {k: getattr(t, k) for k in self._TUNE_KEYS}
 
     def fields(self, out=None):
         """v (D,*box), F (D*D,*box), u (D,*box) as float64 tensors (device unless `out` given)."""
