@@ -384,7 +384,8 @@ template <typename real, int D, typename pop = real> struct Impl {
         return p;
     }
 
-    // FP32 only: tensor maps for the TMA-staged gather (needs node rows aligned to 4 floats)
+    // FP32 arithmetic only (FP32 or BF16 storage): tensor maps for the TMA-staged gather (rows of a
+    // multiple of 16 nodes, so that window starts and the flag box fall on 16-byte boundaries)
     static void setup_tma(lbm_handle *h) {
         h->tma_ok = false;
         h->adj_maps_ok = false;
