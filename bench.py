@@ -107,14 +107,18 @@ class Clocks:
 # reported only while those sources are unchanged (null otherwise).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = {"sources_sha256": "b04e68ac44a6a69182fc3914f096a6025a81498be2b9038c6e467c7af56575f8",
-                   "bytes_per_launch": 2527437056 + 2096242688, "n": 256,
+TRAFFIC_CAPTURE = {"sources_sha256": "c68cf9fb07fce29d5ac887c1b9bce4b3c9d9efea04fec6f1cd103da2b9d60786",
+                   "bytes_per_launch": 2527338752 + 2096491520, "n": 256,
                    "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
+# the same for the BF16-storage fused kernel (two windows per warp) on the same workload
+BF16_TRAFFIC_CAPTURE = {"sources_sha256": "c68cf9fb07fce29d5ac887c1b9bce4b3c9d9efea04fec6f1cd103da2b9d60786",
+                        "bytes_per_launch": 1522339840 + 1148926464, "n": 256,
+                        "summary": "profiles/k_stream_collide_tma_bf16_shell_3d.md"}
 # the same for the reverse step on the clamped cube (128^3)
 ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
                "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
-ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "de261bedf582e11c624c21edb4c8e105f5a103dc2b357652ffa40d957ff9d87c",
-                       "bytes_per_launch": 741809152 + 573622272, "n": 128,
+ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "81cfad42824ec7d180295d5d7cb514a1578a4da45d12204db29b12a3f77c8267",
+                       "bytes_per_launch": 741803264 + 574143488, "n": 128,
                        "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
@@ -345,6 +349,7 @@ def run_ours(args, world, rank, local):
                 "ms_per_step": round(msb / K, 4), "dtype": "bf16 storage, f32 arithmetic",
                 "stream_collide_ms": round(avgb, 4), "bytes_per_node": bpn,
                 "stream_collide_GBps": round(gbb, 1), "frac": round(gbb / peak, 4), "peak_kind": peak_kind,
+                "traffic": captured_traffic(args.n, BF16_TRAFFIC_CAPTURE) if tune_b["windows_per_warp"] == 2 else None,
                 "error_vs_fp64": {"workload": "shell_3d_128 at t = 1 (640 steps)", "v": rel(vb, vd),
                                   "F_minus_I": rel(Fb - eye, Fd - eye), "u": rel(ub, ud)},
                 "tuning": tune_b, "device_status": stb}
