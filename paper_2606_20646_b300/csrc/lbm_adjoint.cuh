@@ -336,6 +336,8 @@ template <int D> __device__ __forceinline__ float &stG(char *w, int q, int k, in
     return reinterpret_cast<float *>(w + L::slot(q))[k * L::width(q) + AdjLayout<D>::g_lane0(q) + lane];
 }
 
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 template <int D>
 __global__ void __launch_bounds__(32, 16) k_adj_step_tma(const StepArgs<float> a, const AdjArgs<float> j,
                                                         const __grid_constant__ TmaMaps maps) {

@@ -80,8 +80,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     for (int it = 0; it < kTmaSpin; ++it)
         if (mbar_try_wait(bar, parity)) return true;
@@ -183,8 +181,7 @@ struct TmaMaps {
 //   f*_q = (1 - omega) f_q + omega f^eq_q + src_q with omega f^eq_q = base_k +- (omega D/(2Dc)) Phi_A,k
 template <int D, typename pop = float>
 __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *wsm, int node, int lane, uint8_t fl,
-                                               const float us[2 * D], long long l0, bool act, float mu, float lam,
-                                               bool st_pop, bool st_us) {
+                                               const float us[2 * D], long long l0, bool act, float mu, float lam) {
     constexpr int K = D + D * D, Q = 2 * D;
     float S[K];
     #pragma unroll
@@ -226,10 +223,8 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
         unh[i] = hi;
         unl[i] = lo;
         df_add(hi, lo, d);  // u*^{n+1}
-        if (st_us) {
-            a.ustar[i * Pn + node] = act ? hi : 0.0f;
-            a.ustar[(D + i) * Pn + node] = act ? lo : 0.0f;
-        }
+        a.ustar[i * Pn + node] = act ? hi : 0.0f;
+        a.ustar[(D + i) * Pn + node] = act ? lo : 0.0f;
     }
     if (fl & kNeedU) un_store<float, D>(a.un, node, unh, unl);
     const float om1 = 1.0f - a.omega;
@@ -263,7 +258,7 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
                 t = base[k];
             }
             o[k] = act ? fmaf(om1, staged<D, pop>(wsm, q, k, lane), t) : 0.0f;
-            if (st_pop) pop_st<float, pop>(a.fdst, (long long)(q * K + k) * Pn + node, o[k]);
+            pop_st<float, pop>(a.fdst, (long long)(q * K + k) * Pn + node, o[k]);
         }
         if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, o);
     }
@@ -328,26 +323,20 @@ __device__ __forceinline__ void issue_window(const StepArgs<float> &a, const Tma
         tma_load_2d(cur + L::slot(q), (q >> 1) == 0 ? &maps.wide : &maps.narrow, bar, st.start[q], q * K);
 }
 
-// one staged window: closure, recovery, collision, stores.  Every lane inside the row whose 32-byte
-// sector of a plane holds an active node stores to that plane (inactive nodes receive zeros), so
-// each warp writes whole sectors (a partly written sector costs the memory system a read of the
-// rest); sectors with no active node are not written at all.  Nothing reads an inactive node's
+// one staged window: closure, recovery, collision, stores.  Every lane inside the row stores:
+// inactive nodes receive zeros, so each warp writes whole 32-byte sectors of every plane (a partly
+// written sector costs the memory system a read of the rest).  Nothing reads an inactive node's
 // populations or u*: pulls across cut links are replaced by the closure.  Lanes past the row end
-// belong to the next row (their staged flag bytes are the copy's zero fill) and store nothing.
-// Every lane of the warp must call it.
+// belong to the next row and store nothing.
 template <int D, typename pop>
 __device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *cur, int2 sg, int lane, long long l0pre,
                                                int gpre) {
     using L = TmaLayout<D, sizeof(pop)>;
-    constexpr int GP = 32 / (int)sizeof(pop);  // lanes per 32-byte sector of a population plane
-    const uint8_t fl = reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane];
-    const bool act = fl & kActive;
-    const unsigned live = __ballot_sync(0xffffffffu, act);
-    const bool st_pop = ((live >> (lane & ~(GP - 1))) & (GP == 32 ? 0xffffffffu : ((1u << GP) - 1u))) != 0u;
-    const bool st_us = ((live >> (lane & ~7)) & 0xffu) != 0u;  // u* planes are FP32
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
     const int node = sg.x + lane;
+    const uint8_t fl = reinterpret_cast<const uint8_t *>(cur + L::fl_off)[lane];
+    const bool act = fl & kActive;
     float us[2 * D];
     #pragma unroll
     for (int d = 0; d < 2 * D; ++d) us[d] = reinterpret_cast<const float *>(cur + L::us_off)[d * 32 + lane];
@@ -356,7 +345,7 @@ __device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *c
     float mu = a.mtab ? a.mtab[2 * gpre] : a.mu;
     const float lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
     if (a.mu_field) mu = a.mu_field[node];
-    collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam, st_pop, st_us);
+    collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 
 // K3 with TMA staging (FP32 arithmetic): one warp per block, NW 32-node windows per warp.  Lane 0 issues the bulk copies of the warp's windows; every lane waits on each window's
@@ -379,41 +368,27 @@ __global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<fl
         for (int w = 0; w < NW; ++w)
             if (w < nw) issue_window<D, pop>(a, maps, smem + w * L::stage_bytes, bars + w, sg[w]);
     // first cut link and group of each node (used by boundary nodes and multi-specimen bodies),
-    // fetched while the copies are in flight (one window: into registers; several: their lines into
-    // L1, read in the window loop, which stays rolled to keep the kernel's code small); lanes past
-    // the end of the last row read a clamped index and never use it
-    if constexpr (NW == 1) {
-        const int nc = min(sg[0].x + lane, (int)a.b.npad - 1);
-        const long long l0pre = __ldg(a.lstart + nc);
-        const int gpre = a.mtab ? __ldg(a.mat + nc) : 0;
-        __syncwarp();
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars, 0))) {
+    // fetched while the copies are in flight; lanes past the end of the last row read a clamped
+    // index and never use it
+    long long l0pre[NW];
+    int gpre[NW];
+    #pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int node = sg[w].x + lane;
+        const int nc = node < a.b.npad ? node : a.b.npad - 1;
+        l0pre[w] = __ldg(a.lstart + nc);
+        gpre[w] = a.mtab ? __ldg(a.mat + nc) : 0;
+    }
+    __syncwarp();
+    #pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (w >= nw) break;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + w, 0))) {
             if (lane == 0) set_status(a.status, kStTimeout);
-            mbar_wait_bounded(bars, 0);  // let the copies in flight land before the warp exits
+            for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
             return;
         }
-        collide_window<D, pop>(a, smem, sg[0], lane, l0pre, gpre);
-    } else {
-        #pragma unroll
-        for (int w = 0; w < NW; ++w)
-            if (w < nw) {
-                const int nc = min(sg[w].x + lane, (int)a.b.npad - 1);
-                prefetch_l1(a.lstart + nc);
-                if (a.mtab) prefetch_l1(a.mat + nc);
-            }
-        __syncwarp();
-        #pragma unroll 1
-        for (int w = 0; w < nw; ++w) {
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + w, 0))) {
-                if (lane == 0) set_status(a.status, kStTimeout);
-                for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
-                return;
-            }
-            const int2 sgw = __ldg(&a.seg[sg0 + w]);
-            const int nc = min(sgw.x + lane, (int)a.b.npad - 1);
-            collide_window<D, pop>(a, smem + w * L::stage_bytes, sgw, lane, __ldg(a.lstart + nc),
-                                   a.mtab ? (int)__ldg(a.mat + nc) : 0);
-        }
+        collide_window<D, pop>(a, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w]);
     }
 }
 
