@@ -220,3 +220,22 @@ def test_fp32_adjoint_ellipsoid_against_oracle(ellipsoid_case):
     print(f"ellipsoid FP32: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
     assert _rel(g, go) < 1e-4
     assert np.abs(gb - gbo).max() <= 1e-4 * np.abs(gbo).max()
+
+
+def test_fp64_adjoint_equals_oracle_adjoint_cube_32():
+    """The clamped cube at 32^3 (20 steps, checkpoints every 8): the whole gradient field against
+    the oracle's discrete adjoint."""
+    import oracle
+    p = I.inclusion_cube(32, 20)
+    p = p.with_(options=dataclasses.replace(p.options, body_force=B0))
+    mu0 = _mu0(p)
+    o = oracle.Oracle(p).set_mu_field(p.meta["mu_target"]).set_initial()
+    o.step(20)
+    ut = o.fields()[2]
+    act = o.active_mask().reshape(p.box_shape)
+    del o
+    g, gb = _gpu_grad(p, mu0, ut, act, "fp64", 20, 8)
+    go, gbo = _oracle_grad(p, mu0, ut, act, 20)
+    print(f"cube 32: dL/dmu rel-L2 {_rel(g, go):.3e}, dL/db {gb} vs {gbo}")
+    assert _rel(g, go) < 1e-12
+    assert np.abs(gb - gbo).max() <= 1e-12 * np.abs(gbo).max()

@@ -115,3 +115,28 @@ def test_shell_256_fp32_tracks_fp64(shell_t1):
     print(f"FP32 vs FP64 at 256^3, t = 1: v {ev:.3e}, F {eF:.3e}, F-I {eG:.3e}; "
           f"FP32 mirror asymmetry rel-L2 {rel:.3e}, max {mx:.3e}")
     assert ev < 1e-5 and eF < 1e-5
+
+
+def test_shell_256_fp32_full_length_run():
+    """The workload's full length: 4000 steps (t = 3.125, past the sin^2 ramp that ends at t = 2),
+    FP32 in the launch configuration the benchmark times: no device status, finite fields, J
+    within the range of a mildly compressed and stretched shell, the velocity relaxing."""
+    from paper_2606_20646_b300 import lbm
+    p = I.shell_3d(256)
+    sim = lbm.Simulation(p, precision="fp32")
+    sim.set_initial()
+    act = sim.active_mask()
+    vr = []
+    for _ in range(4):
+        sim.step(1000)
+        v, F, u = [t.cpu().numpy() for t in sim.fields()]
+        assert sim.sync(raise_on_status=False) == 0
+        vr.append(float(np.sqrt((v[:, act] ** 2).mean())))
+    assert sim.info()["step"] == 4000
+    sim.close()
+    Fa = F[:, act].T.reshape(-1, 3, 3).astype(np.float64)
+    J = np.linalg.det(Fa)
+    print(f"shell 256^3 FP32, 4000 steps: v_rms per 1000 steps {vr}, J in [{J.min():.4f}, {J.max():.4f}]")
+    assert np.isfinite(F[:, act]).all() and np.isfinite(u[:, act]).all()
+    assert 0.8 < J.min() and J.max() < 1.2
+    assert vr[3] < vr[1]          # after the ramp the damping takes the velocity down
