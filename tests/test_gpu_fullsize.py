@@ -121,7 +121,7 @@ def test_shell_256_fp32_full_length_run():
     """The workload's full length: 4000 steps (t = 3.125, past the sin^2 ramp that ends at t = 2),
     FP32 in the launch configuration the benchmark times: no device status, finite fields, J
     within the range of a mildly compressed and stretched shell (radial BVP: 0.93 to 1.02), the
-    velocity relaxing.  At omega = 0.3 below the paper's 1.8: with 1.8 this stiff shell (lambda = 5)
+    velocity relaxing.  At omega = 1.5, below the paper's 1.8: with 1.8 this stiff shell (lambda = 5)
     blows up 500-1000 steps after the ramp, in the FP32 and FP64 forms alike, starting at the inner
     surface; the extra BGK dissipation of omega = 1.5 holds it (v_rms 2.0e-2 at step 2000, 6e-4 at
     4000)."""
