@@ -142,5 +142,9 @@ def test_shell_256_fp32_full_length_run():
     J = np.linalg.det(Fa)
     print(f"shell 256^3 FP32, 4000 steps: v_rms per 1000 steps {vr}, J in [{J.min():.4f}, {J.max():.4f}]")
     assert np.isfinite(F[:, act]).all() and np.isfinite(u[:, act]).all()
-    assert 0.8 < J.min() and J.max() < 1.2
     assert vr[3] < vr[1]          # after the ramp the damping takes the velocity down
+    # relaxed to the nonlinear radial BVP (inner nominal traction, outer traction-free): its J
+    # spans [1.0014, 1.0191]; the lattice's J (measured [1.0007, 1.0190]) has the same range
+    import radial_bvp as rb
+    r = rb.solve(3, 1.0, 5.0, 0.4, 0.9, ("P", -1.0), ("P", 0.0))
+    assert abs(J.max() - r["J"].max()) < 1e-3 and abs(J.min() - r["J"].min()) < 2e-3
