@@ -299,7 +299,11 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out);
  * No counterpart in the paper: gradients of a loss on the final displacement with respect to a
  * per-node shear modulus and the body force, by the discrete adjoint of the steps (reverse
  * sweep over saved states).  Bodies with Neumann links (whose steps contain the Newton
- * inversion and the projection) are not supported: lbm_adjoint_begin returns LBM_ERR_STATE. */
+ * inversion and the projection) are not supported: lbm_adjoint_begin returns LBM_ERR_STATE.
+ * The initial populations are an input of the sweep, not differentiated: the gradients are those
+ * of the steps.  A start from rest with F = I (P(I) = 0) makes them independent of mu and b, so
+ * the gradients are then complete; a start in motion or strained (equilibrium or characteristic
+ * populations that depend on mu) would need the initial state's own derivative added. */
 
 /* Per-node shear modulus mu (n_box values in box order, device or host memory; values at
  * inactive nodes are ignored), replacing the material's mu (lambda is kept).  Needs

@@ -7,7 +7,8 @@ restores one, recomputes the steps up to the next saved state, each recording th
 (lbm_step_moments: D*D values per node), and reverses those steps in the opposite order
 (lbm_adjoint_step).  Memory: ceil(N/every) saved states plus `every` recorded F fields, the
 latter kept on the simulation for later sweeps.  All arithmetic runs in the library's kernels;
-this module orders the calls.
+this module orders the calls.  The initial populations are held fixed: from rest with F = I they do
+not depend on mu or b and the gradients are complete.
 """
 from __future__ import annotations
 
