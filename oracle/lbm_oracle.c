@@ -33,11 +33,14 @@
  * plain reverse accumulation over stored states; pinned by central differences of this file's
  * forward (single-node moduli, body force, a random direction of the whole modulus field).
  *
- * Parity status: every function is pinned by tests except the projection
- * solver constants (sweep count, damping, gauge), which the paper does not
- * fix -- parity unpinned for those constants; the projection is pinned only
- * through properties (idempotence on compatible fields, residual decrease) and
- * through convergence of the traction benchmarks to the radial BVP.
+ * Parity status: every function is pinned by tests.  The projection operator
+ * (edge increments, Dirichlet boundary edges, zero-mean gauge, compatible F) is
+ * pinned against an independent sparse direct solve of its normal equations
+ * with the sweeps run to convergence; the sweep count and damping used in the
+ * steps are options the paper does not fix (parity unpinned for those two
+ * constants), pinned only through properties (idempotence on compatible fields,
+ * residual decrease) and convergence of the traction benchmarks to the radial
+ * BVP.
  */
 #include <math.h>
 #include <stdio.h>
