@@ -208,11 +208,12 @@ def oracle_sample(n=64, steps=None, warmup=0, budget_s=15.0):
         o.step(warmup)
     nact = o.counts()["n_active"]
     if steps is None:
+        # calibrate on one projection cycle (20 steps, one of them a projection step), so that the
+        # per-step estimate carries the projection's amortised share
         t0 = time.perf_counter()
-        o.step(5)
+        o.step(20)
         dt = time.perf_counter() - t0
-        steps = max(5, int(budget_s / max(dt / 5, 1e-6)))
-        steps = (steps // 20) * 20 or 5
+        steps = max(20, int(budget_s / max(dt / 20, 1e-6)) // 20 * 20)
     t0 = time.perf_counter()
     o.step(steps)
     el = time.perf_counter() - t0
