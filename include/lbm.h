@@ -46,7 +46,7 @@ extern "C" {
 enum lbm_error {
     LBM_OK = 0,
     LBM_ERR_ARG = -1,      /* invalid argument or descriptor                           */
-    LBM_ERR_DOMAIN = -2,   /* empty body, or the body reaches a non-periodic box face  */
+    LBM_ERR_DOMAIN = -2,   /* empty body, or the body extends past a non-periodic box face */
     LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                               */
     LBM_ERR_STORAGE = -4,  /* storage missing, too small or misaligned (256 B)         */
     LBM_ERR_STATE = -5,    /* call out of order (e.g. lbm_step before lbm_set_initial) */
@@ -223,8 +223,9 @@ int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes);
  * descriptors are copied; the arrays they point to may be freed on return.
  * Errors: LBM_ERR_ARG (bad descriptor, omega outside (0,2], dx<=0, c<=0,
  * missing BC for a boundary id is reported later by lbm_bind_storage),
- * LBM_ERR_DOMAIN (no active node, or the body reaches a non-periodic box
- * face), LBM_ERR_STORAGE, LBM_ERR_CUDA. */
+ * LBM_ERR_DOMAIN (no active node, or the body extends past a non-periodic box
+ * face: a cut link leaving the box must cross the surface within one spacing),
+ * LBM_ERR_STORAGE, LBM_ERR_CUDA. */
 int lbm_create(const lbm_grid *grid, const lbm_levelset *levelset, const lbm_material *material,
                const lbm_bc *bcs, int nbc, const lbm_options *options, void *geometry_storage,
                size_t geometry_bytes, void *cuda_stream, lbm_handle **out);

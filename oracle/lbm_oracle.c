@@ -849,7 +849,7 @@ orc_state *orc_create(const orc_problem *p, int *err)
             e[q / 2] = (q % 2 == 0) ? 1.0 : -1.0;
             for (int a = 0; a < 3; a++) Xo[a] = Xm[a] + s->p.dx * e[a];
             if (l < 0 && !(levelset(&s->p, Xo, NULL) > 0.0)) {
-                /* the body reaches a non-periodic box face */
+                /* the body extends past a non-periodic box face */
                 orc_destroy(s);
                 *err = ORC_EDOMAIN;
                 return NULL;

@@ -141,7 +141,7 @@ const char *lbm_error_string(int code) {
     switch (code) {
     case LBM_OK: return "ok";
     case LBM_ERR_ARG: return "invalid argument or descriptor";
-    case LBM_ERR_DOMAIN: return "empty body, or the body reaches a non-periodic box face";
+    case LBM_ERR_DOMAIN: return "empty body, or the body extends past a non-periodic box face";
     case LBM_ERR_CUDA: return "CUDA runtime error";
     case LBM_ERR_STORAGE: return "storage missing, too small or misaligned";
     case LBM_ERR_STATE: return "call out of order";
