@@ -1,0 +1,49 @@
+"""Host logic of the benchmark, on CPU: the algorithmic bytes per node behind every roofline
+fraction it reports, the rule that a stored DRAM capture is reported only while the kernel sources
+hash to the captured ones, and the bounded CPU-baseline sample of the oracle."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_host", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_bytes_per_node():
+    b = _bench()
+    # populations read and written (Q*K values), u* as 8 bytes per component read and written, flags
+    assert b.bytes_per_node(3, 4) == 2 * 72 * 4 + 2 * 3 * 8 + 1 == 625
+    assert b.bytes_per_node(3, 2) == 337          # BF16 storage
+    assert b.bytes_per_node(3, 8) == 1201         # FP64 form
+    assert b.bytes_per_node(2, 4) == 2 * 24 * 4 + 2 * 2 * 8 + 1
+    # reverse step: gbar read and written, F and dL/du* read, dL/dmu (FP64) read and written, flags
+    assert b.adjoint_bytes_per_node(3, 4) == 576 + 36 + 12 + 16 + 1 == 641
+    assert b.recompute_bytes_per_node(3, 4) == 625 + 36
+    # Jacobi sweep: correction vector (padded to 4) read and written, residual vector, flags
+    assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 + 1 == 49
+
+
+def test_traffic_is_reported_only_for_the_captured_sources():
+    b = _bench()
+    cap = dict(b.TRAFFIC_CAPTURE)
+    n = cap["n"]
+    good = b.captured_traffic(n, cap, b.KERNEL_SOURCES)
+    assert good in (None, cap["bytes_per_launch"])   # None once the sources have changed
+    assert b.captured_traffic(n + 1, cap, b.KERNEL_SOURCES) is None          # another workload size
+    stale = dict(cap, sources_sha256="0" * 64)
+    assert b.captured_traffic(n, stale, b.KERNEL_SOURCES) is None             # other sources
+    assert b.captured_traffic(n, None, b.KERNEL_SOURCES) is None
+    # the hash covers every listed source: dropping one changes it
+    assert b.kernel_sources_hash(b.KERNEL_SOURCES[:-1]) != b.kernel_sources_hash(b.KERNEL_SOURCES)
+
+
+def test_oracle_sample_is_bounded_and_whole_projection_cycles():
+    b = _bench()
+    mlups, steps, elapsed, nact = b.oracle_sample(n=16, budget_s=0.5)
+    assert steps >= 20 and steps % 20 == 0
+    assert nact > 0 and mlups > 0 and elapsed < 30
