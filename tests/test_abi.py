@@ -103,3 +103,22 @@ def test_bf16_storage_descriptors_without_gpu(lib):
     opt.adjoint = 0
     opt.precision = 3
     assert lib.lbm_create(*args()) == -1
+
+
+def test_new_entry_points_refuse_bad_arguments_without_gpu(lib):
+    """Tuning, autotuner, saved states and reverse mode check their arguments before any device
+    work: a null handle or buffer is LBM_ERR_ARG."""
+    from paper_2606_20646_b300 import lbm
+    t = lbm.lbm_tuning(0, 0, 0, 0, 0.0, 0.0)
+    assert lib.lbm_set_tuning(None, C.byref(t)) == -1
+    assert lib.lbm_get_tuning(None, C.byref(t)) == -1
+    assert lib.lbm_autotune(None, 20, None, None) == -1
+    n = C.c_size_t(0)
+    assert lib.lbm_state_bytes(None, C.byref(n)) == -1
+    assert lib.lbm_save_state(None, None) == -1
+    assert lib.lbm_load_state(None, None) == -1
+    assert lib.lbm_moments_bytes(None, C.byref(n)) == -1
+    assert lib.lbm_step_moments(None, None) == -1
+    assert lib.lbm_adjoint_begin(None, None) == -1
+    assert lib.lbm_adjoint_step(None, None) == -1
+    assert lib.lbm_adjoint_gradients(None, None, None) == -1
