@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-errors", action="store_true", help="skip the FP32/FP64 errors against the oracle")
     ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
@@ -138,11 +139,29 @@ def captured_traffic(n, cap=TRAFFIC_CAPTURE, sources=KERNEL_SOURCES):
 
 
 def bytes_per_node(D, real_size):
-    """Algorithmic HBM bytes per active node of the fused collide-stream kernel: every
-    population component read once and written once, u* read and written (8 bytes per
+    """Algorithmic HBM bytes per active node of the fused collide-stream kernel as this build moves
+    them: every population component read once and written once, u* read and written (8 bytes per
     component in both forms: an FP64 plane, or an FP32 hi/lo pair), one flag byte."""
     K, Q = D + D * D, 2 * D
     return 2 * Q * K * real_size + 2 * D * 8 + 1
+
+
+def method_bytes_per_node(D, real_size):
+    """The method's algorithmic bytes per active node and step (the coverage contract's figure):
+    every population component read and written once, u* read and written in the population
+    precision, one flag byte -- 601 B in 3D FP32.  The build's FP32 u* pairs add 2 D 4 bytes."""
+    K, Q = D + D * D, 2 * D
+    return 2 * Q * K * real_size + 2 * D * real_size + 1
+
+
+def link_bytes(D, real_size, n_cut, lsq_entries):
+    """Algorithmic bytes of one launch of the link kernel: per cut link its geometry (node,
+    direction, BC index, stencil size: 16 B; eta, N_b, tangents: 8 (1 + D + 2 D) B), the kept pair
+    read (2 K values), the reconstruction written (K values) and the Newton state read and written
+    (2 D values); per Neumann stencil entry its index and D - 1 weights."""
+    K = D + D * D
+    per_link = 16 + 8 * (1 + 3 * D) + (3 * K + 2 * D) * real_size
+    return n_cut * per_link + lsq_entries * (4 + (D - 1) * real_size)
 
 
 def jacobi_bytes_per_node(D, real_size):
@@ -198,10 +217,11 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def oracle_sample(n=64, steps=None, warmup=0, budget_s=15.0):
-    """FP64 oracle on an n^3 copy of the shell workload (single host thread)."""
+def oracle_sample(n=64, steps=None, warmup=0, budget_s=15.0, threads=1):
+    """FP64 oracle on an n^3 copy of the shell workload on `threads` host threads (0: all)."""
     import oracle
     from paper_2606_20646_b300 import inputs as I
+    oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     p = I.shell_3d(n)
     o = oracle.Oracle(p).set_initial()
     if warmup:
@@ -220,18 +240,46 @@ def oracle_sample(n=64, steps=None, warmup=0, budget_s=15.0):
     return nact * steps / el / 1e6, steps, el, nact
 
 
+def oracle_errors(n, steps, dev):
+    """Relative L2 errors of the FP32 and FP64 forms against the FP64 oracle on an n^3 copy of the
+    shell workload after `steps` steps (v, F, F - I, u over the active nodes); the oracle runs on
+    all host threads."""
+    import numpy as np
+    import oracle
+    from paper_2606_20646_b300 import inputs as I, lbm
+    oracle.set_threads(os.cpu_count() or 1)
+    p = I.shell_3d(n)
+    o = oracle.Oracle(p).set_initial()
+    o.step(steps)
+    ref = o.fields()
+    act = o.active_mask()
+    eye = np.eye(3).reshape(9, 1)
+    out = {"workload": f"shell_3d_{n} after {steps} steps (t = {steps * p.dt:.3f})"}
+    for prec in ("fp32", "fp64"):
+        sim = lbm.Simulation(p, precision=prec, device=dev)
+        sim.set_initial().step(steps)
+        g = [t.cpu().numpy() for t in sim.fields()]
+        sim.close()
+        e = {nm: float(np.linalg.norm(a[:, act] - b[:, act]) / np.linalg.norm(b[:, act]))
+             for nm, a, b in zip("vFu", g, ref)}
+        e["F_minus_I"] = float(np.linalg.norm(g[1][:, act] - ref[1][:, act]) / np.linalg.norm(ref[1][:, act] - eye))
+        out[prec] = e
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     t0 = time.time()
-    mlups, steps, el, nact = oracle_sample(n=64, steps=args.steps, warmup=args.warmup)
-    sample = (f"FP64 C oracle (lbm_oracle.c, 1 host thread) on the 64^3 copy of the shell workload "
+    cores = os.cpu_count() or 1
+    mlups, steps, el, nact = oracle_sample(n=64, steps=args.steps, warmup=args.warmup, threads=cores)
+    sample = (f"FP64 C oracle (lbm_oracle.c, {cores} host threads) on the 64^3 copy of the shell workload "
               f"({nact} active nodes), {args.warmup} untimed + {steps} timed steps incl. projection steps")
     line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"shell_3d_{args.n} (64^3 copy on the host)"},
-            "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(time.time() - t0, 1)}
     print(json.dumps(line), flush=True)
@@ -288,18 +336,27 @@ def run_ours(args, world, rank, local):
     ms = max_over_ranks(ms, world)
     value = world * nact * K / (ms / 1e3) / 1e6
     avg_sc = kt["stream_collide_ms"] / max(kt["stream_collide_launches"], 1)
-    bpn = bytes_per_node(3, 4)
+    bpn = method_bytes_per_node(3, 4)          # the method's 601 B per node
     achieved = nact * bpn / (avg_sc / 1e3) / 1e9
+    achieved_moved = nact * bytes_per_node(3, 4) / (avg_sc / 1e3) / 1e9
     share = {"stream_collide": kt["stream_collide_ms"] / ms, "cutlink": kt["cutlink_ms"] / ms,
              "projection": kt["projection_ms"] / ms, "jacobi (within projection)": kt["jacobi_ms"] / ms}
     avg_jac = kt["jacobi_ms"] / max(kt["jacobi_launches"], 1)
     jacobi = {"avg_sweep_us": round(avg_jac * 1e3, 2), "sweeps": kt["jacobi_launches"],
               "GBps": round(nact * jacobi_bytes_per_node(3, 4) / (avg_jac / 1e3) / 1e9, 1) if avg_jac > 0 else None}
     avg_cut = kt["cutlink_ms"] / max(kt["cutlink_launches"], 1)
+    lb = link_bytes(3, 4, info["n_cut"], info["lsq_entries"])
+    links = {"kernel": "k_links_f32<3>", "avg_launch_ms": round(avg_cut, 4), "bytes_per_launch": lb,
+             "achieved_GBps": round(lb / (avg_cut / 1e3) / 1e9, 1) if avg_cut > 0 else None,
+             "frac": round(lb / (avg_cut / 1e3) / 1e9 / peak, 4) if avg_cut > 0 else None}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": captured_traffic(args.n),
                 "kernel": "k_stream_collide_tma<3>", "bytes_per_launch": nact * bpn,
-                "avg_launch_ms": round(avg_sc, 4), "peak_kind": peak_kind}
+                "bytes_per_node": bpn, "avg_launch_ms": round(avg_sc, 4), "peak_kind": peak_kind,
+                "frac_of_bytes_moved": round(achieved_moved / peak, 4),
+                "bytes_per_node_moved": bytes_per_node(3, 4),
+                "note": "frac counts the method's 601 B per active node; frac_of_bytes_moved counts the "
+                        "625 B this build moves (u* as FP32 hi/lo pairs)"}
     del sim
     torch.cuda.empty_cache()
 
@@ -511,13 +568,22 @@ def run_ours(args, world, rank, local):
         del sim
         torch.cuda.empty_cache()
 
+    # ---- errors of the FP32 and FP64 forms against the oracle (64^3 copy, t = 1) -----------------
+    errors = None
+    if rank == 0 and not args.no_errors:
+        errors = oracle_errors(64, 320, dev)
+        torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ---------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, steps, el, nact64 = oracle_sample(n=64, budget_s=15.0)
-        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, 1 host thread, 64^3 copy of the shell ({nact64} active nodes), "
-                         f"{steps} steps incl. projection steps, {el:.1f} s"}
+        cores = os.cpu_count() or 1
+        mlups, steps, el, nact64 = oracle_sample(n=64, budget_s=15.0, threads=cores)
+        m1, s1, el1, _ = oracle_sample(n=64, steps=20, threads=1)
+        cpu = {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 C oracle, {cores} host threads (OpenMP over nodes and links), 64^3 copy of the "
+                         f"shell ({nact64} active nodes), {steps} steps incl. projection steps, {el:.1f} s",
+               "one_thread": {"value": round(m1, 4), "steps": s1, "seconds": round(el1, 1)}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -530,7 +596,7 @@ def run_ours(args, world, rank, local):
                            "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
                            "parallelism": f"replicas x{world}", "tuning": tuning},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
-                "jacobi": jacobi, "cutlink_avg_ms": round(avg_cut, 4),
+                "jacobi": jacobi, "links": links, "errors_vs_oracle": errors,
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "fp64": fp64, "bf16": bf16, "batch_2d": batch,
                 "adjoint": adj,
                 "cpu_baseline": cpu, "device_status": st}

@@ -51,7 +51,8 @@ enum lbm_error {
     LBM_ERR_STORAGE = -4,  /* storage missing, too small or misaligned (256 B)         */
     LBM_ERR_STATE = -5,    /* call out of order (e.g. lbm_step before lbm_set_initial) */
     LBM_ERR_DEVICE = -6,   /* lbm_sync found a non-zero device status word             */
-    LBM_ERR_CAPACITY = -7  /* a fixed capacity (LSQ stencil) was exceeded              */
+    LBM_ERR_CAPACITY = -7, /* a fixed capacity was exceeded (LSQ stencil, census box)  */
+    LBM_ERR_UNSTABLE_C = -8 /* the lattice speed c fails the tangent wave-speed audit   */
 };
 
 /* ---- device status bits returned by lbm_sync ------------------------------ */
@@ -61,7 +62,9 @@ enum lbm_device_status {
     LBM_DEV_NEWTON = 4,    /* traction inversion failed (Eqs. neumann-newton-2d/3d)   */
     LBM_DEV_LSQ = 8,       /* no least-squares fit at a Neumann link                   */
     LBM_DEV_CAPACITY = 16, /* LSQ stencil larger than LBM_LSQ_CAPACITY                */
-    LBM_DEV_TIMEOUT = 128  /* a bounded wait for a TMA copy ran out; that step is invalid */
+    LBM_DEV_TIMEOUT = 128, /* a bounded wait for a TMA copy ran out; that step is invalid */
+    LBM_DEV_BOUNDS = 256   /* bounds-checked build only: an index left its array (the access
+                              was redirected to element 0); the results are invalid        */
 };
 
 /* FP64: populations and arithmetic in FP64.  FP32: both in FP32, populations stored shifted
@@ -77,13 +80,21 @@ enum lbm_precision { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_BF16S = 2 };
  *   SUPERELLIPSE  phi = |xi_1/axes[0]|^p + |xi_2/axes[1]|^p - 1  (2D only)
  *   CYLINDER      phi = |(X_1, X_2) - (c_1, c_2)| - axes[0]   (axis X_3)
  *   HALFSPACE     phi = axes . (X - center), axes a unit outward normal
+ *   SAMPLED       phi given at the lattice nodes (lbm_shape.phi: n_box doubles in box order, device
+ *                 memory the caller keeps valid until lbm_destroy); between nodes the multilinear
+ *                 interpolant (linear along every link, so eta is the root of a linear function),
+ *                 constant beyond the outermost node of a non-periodic axis (a sampled body must
+ *                 not reach such a face: the box-face rule refuses it), periodic on periodic axes;
+ *                 N_b (Eq. level-set-normal) from the same interpolant of the nodes' central
+ *                 differences (one-sided at non-periodic ends); center, axes, rot unused
  * complement != 0 negates phi.  The body is {X : max_s phi_s(X) <= 0}. */
 enum lbm_shape_kind {
     LBM_SHAPE_SPHERE = 0,
     LBM_SHAPE_ELLIPSOID = 1,
     LBM_SHAPE_SUPERELLIPSE = 2,
     LBM_SHAPE_CYLINDER = 3,
-    LBM_SHAPE_HALFSPACE = 4
+    LBM_SHAPE_HALFSPACE = 4,
+    LBM_SHAPE_SAMPLED = 5
 };
 
 enum lbm_bc_kind { LBM_BC_DIRICHLET = 0, LBM_BC_NEUMANN = 1 };
@@ -137,6 +148,7 @@ typedef struct lbm_shape {
     double axes[3];
     double rot[9];
     double p;        /* superellipse exponent                                   */
+    const double *phi; /* SAMPLED: the node samples (device memory), else unused */
 } lbm_shape;
 
 typedef struct lbm_material {
@@ -189,6 +201,12 @@ typedef struct lbm_options {
     int adjoint;      /* non-zero: reserve a per-node shear-modulus field and the reverse-mode
                          buffers of lbm_adjoint_* (Dirichlet-only bodies)                    */
     int reserved;
+    double c_audit;   /* wave-speed audit (Sec. 2, Eq. acoustic-tensor-general-d): lbm_create and
+                         lbm_set_initial require c >= c_audit * c_T, c_T the largest tangent wave
+                         speed sqrt(max_n eig Q(n; F)) of the reference state F = I of every material
+                         and of the initial F0 at every active node (rho0 = 1).  0 selects 2.5 (the
+                         margin every closure case of the library's tests needed at omega = 1.8; the
+                         bulk lattice alone needs sqrt(D)); a negative value turns the audit off */
 } lbm_options;
 
 typedef struct lbm_info {
@@ -296,6 +314,13 @@ int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t);
  * latched a device status; the state is restored). */
 int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out);
 
+/* Bounded waits (no counterpart in the paper).  The bulk-copy kernels poll the barrier of their
+ * copies at most 2^20 times before they latch LBM_DEV_TIMEOUT, wait once more with that limit for
+ * every copy they issued, and return without writing (the step is then invalid).  This sets the
+ * first wait's limit: 0 makes every first wait run out at once, which tests that path without a
+ * fault; a negative value restores 2^20.  Takes effect at the next launch. */
+int lbm_set_wait_limit(lbm_handle *h, int polls);
+
 /* ---- parameters, saved states and reverse mode --------------------------------------------
  * No counterpart in the paper: gradients of a loss on the final displacement with respect to a
  * per-node shear modulus and the body force, by the discrete adjoint of the steps (reverse
@@ -352,8 +377,38 @@ int lbm_adjoint_step(lbm_handle *h, const void *moments);
 int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b);
 
 /* Writes v, F (from U^num, Eq. state-recovery-general) and u = u* + dt/2 v
- * (Eq. u-recovery-general) at the current time.  Any pointer may be NULL. */
+ * (Eq. u-recovery-general) at the current time.  Any pointer may be NULL.  Box planes
+ * (LBM_LAYOUT_PLANES); the same as lbm_fields_ex(h, v, F, u, NULL, NULL, LBM_LAYOUT_PLANES). */
 int lbm_fields(lbm_handle *h, double *v, double *F, double *u);
+
+/* field layouts: PLANES component c of node n at c * n_box + n (structure of arrays); NODES at
+ * n * ncomp + c (array of structures: a node's components contiguous) */
+enum lbm_layout { LBM_LAYOUT_PLANES = 0, LBM_LAYOUT_NODES = 1 };
+
+/* lbm_fields with the diagnostics of Algorithm 1's last loop: the Cauchy stress
+ * sigma = J^-1 P F^T (Eq. cauchy-recovery-general; D*D components, row-major) and J = det F
+ * (1 component), computed in FP64 from the recovered F.  Any pointer may be NULL; inactive nodes
+ * are written as 0.  Device pointers, or host pointers with host staging.  Errors: LBM_ERR_ARG
+ * (unknown layout, host pointer without staging), LBM_ERR_STATE (not initialised), LBM_ERR_CUDA. */
+int lbm_fields_ex(lbm_handle *h, double *v, double *F, double *u, double *sigma, double *J, int layout);
+
+/* Whole-body diagnostics of the current state (Sec. 5.2 reports the J range and the RMS velocity),
+ * reduced on the GPU (warp shuffles, a fixed grid and a fixed order: the values do not depend on
+ * the launch) over the active nodes:
+ *   J_min, J_max    det F;
+ *   v_rms, v_max    |v|;
+ *   c_tangent       the largest tangent wave speed sqrt(max_n eig Q(n; F)) (Eq. acoustic-tensor-
+ *                   general-d, rho0 = 1), the quantity the wave-speed audit bounds;
+ *   incompat_rms    the compatibility residual of the projection's edge relation (Eq. projection-
+ *                   edge-relation) for the current u and F, RMS over active axis edges of
+ *                   |u_m - u_l - (F_m + F_l - 2I)(X_m - X_l)/2|, and n_edges the edge count.
+ * Synchronises the stream.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (not initialised), LBM_ERR_CUDA. */
+typedef struct lbm_diag {
+    double J_min, J_max, v_rms, v_max, c_tangent, incompat_rms;
+    long long n_active, n_edges, step;
+    double t;
+} lbm_diag;
+int lbm_diagnostics(lbm_handle *h, lbm_diag *out);
 
 /* Synchronises the stream and reads (then clears) the device status word.
  * Returns LBM_ERR_DEVICE if it was non-zero, with the bits in *device_status. */
@@ -383,14 +438,16 @@ const char *lbm_error_string(int code);
 #define LBM_CENSUS_MAX_NODES (1LL << 24)
 
 /* Geometry census that allocates nothing.  No counterpart in the paper: it exists for
- * callers that must not allocate device memory when they size a simulation -- code running
- * while a CUDA graph is being captured (an allocation would break or end the capture) and
- * embedding runtimes whose device memory belongs to their own pool.  It returns the same
- * counts that lbm_create computes (lbm_info.n_active, n_cut, n_segments) for the grid and
- * level set, which size the storage of lbm_create and lbm_bind_storage.
+ * callers that must not allocate device memory when they size a simulation -- an embedding
+ * runtime (a serving process, a solver framework) whose device memory is one arena planned ahead
+ * and handed out by its own allocator, so that a library call must not take memory behind its
+ * back, or a process already at its memory limit that must learn how much storage a body needs
+ * before it can free or plan that much.  It returns the same counts that lbm_create computes
+ * (lbm_info.n_active, n_cut, n_segments) for the grid and level set, which size the storage of
+ * lbm_create and lbm_bind_storage, and applies lbm_create's domain rules.
  *
  * Scratch: one file-scope device array of 256 + LBM_CENSUS_MAX_NODES bytes (the active mask
- * and three counters), held by every GPU that loads the library until the process exits.
+ * and four counters), held by every GPU that loads the library until the process exits.
  * The first call on a device, with that device current, looks up the array's device address
  * (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture.  All
  * calls on a device share the array, so calls that overlap on the GPU race; each call clears
@@ -399,7 +456,8 @@ const char *lbm_error_string(int code);
  * allocating library routine.
  * Takes single-body level sets of at most LBM_CENSUS_MAX_SHAPES shapes (ngroups must be 0).
  * Errors: LBM_ERR_ARG (invalid grid or level set, groups, too many shapes), LBM_ERR_CAPACITY
- * (more than LBM_CENSUS_MAX_NODES box nodes), LBM_ERR_CUDA. */
+ * (more than LBM_CENSUS_MAX_NODES box nodes), LBM_ERR_DOMAIN (no active node, or the body extends
+ * past a non-periodic box face; the counts are still written), LBM_ERR_CUDA. */
 #define LBM_CENSUS_MAX_SHAPES 16
 int lbm_census_static(const lbm_grid *grid, const lbm_levelset *levelset, void *cuda_stream, long long *n_active,
                       long long *n_cut, long long *n_segments);

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
-_SHAPE = {"sphere": 0, "ellipsoid": 1, "superellipse": 2, "cylinder": 3, "halfspace": 4}
+_SHAPE = {"sphere": 0, "ellipsoid": 1, "superellipse": 2, "cylinder": 3, "halfspace": 4, "sampled": 5}
 _BCKIND = {"dirichlet": 0, "neumann": 1}
 _PROFILE = {"zero": 0, "affine": 1, "radial": 2, "twist_stretch": 3, "const": 4}
 _RAMP = {"one": 0, "linear": 1, "sin2": 2, "cos": 3, "time": 4}
@@ -29,7 +29,8 @@ MAXB = 16
 
 class _Shape(C.Structure):
     _fields_ = [("kind", C.c_int), ("complement", C.c_int), ("bid", C.c_int), ("pad", C.c_int),
-                ("c", C.c_double * 3), ("a", C.c_double * 3), ("Q", C.c_double * 9), ("p", C.c_double)]
+                ("c", C.c_double * 3), ("a", C.c_double * 3), ("Q", C.c_double * 9), ("p", C.c_double),
+                ("phi", C.c_void_p)]
 
 
 class _BC(C.Structure):
@@ -50,7 +51,7 @@ class _Problem(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C, FP64, no FMA contraction) into liblbm_oracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
@@ -87,9 +88,27 @@ def lib():
         _lib.orc_newton.argtypes = [C.c_int, C.c_double, C.c_double, d, d, d, d, d]
         _lib.orc_project.argtypes = [vp, d, d, C.c_double, d]
         _lib.orc_adjoint.argtypes = [vp, C.c_int, d, d, d]
+        _lib.orc_stress.argtypes = [vp, d, d]
+        _lib.orc_diagnostics.argtypes = [vp, d]
+        _lib.orc_tangent_speed2.restype = C.c_double
+        _lib.orc_tangent_speed2.argtypes = [C.c_int, C.c_double, C.c_double, d]
+        _lib.orc_set_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_levelset.restype = C.c_double
         _lib.orc_levelset.argtypes = [C.POINTER(_Problem), d, i]
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads for the oracle's per-node and per-link loops (0 keeps the current count);
+    returns the count in use.  The results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def tangent_speed2(D, mu, lam, F):
+    """Largest squared tangent wave speed max_n eig Q(n; F) of the neo-Hookean law (rho0 = 1)."""
+    F = _f64(np.asarray(F).reshape(-1))
+    return float(lib().orc_tangent_speed2(int(D), float(mu), float(lam), _dp(F)))
 
 
 def _dp(a):
@@ -125,6 +144,11 @@ def problem_struct(p) -> _Problem:
         for a in range(9):
             t.Q[a] = float(sh.rot.reshape(-1)[a])
         t.p = sh.p
+        if sh.kind == "sampled":
+            arr = _f64(sh.phi).reshape(-1)
+            assert arr.size == p.n_box
+            s._keep = getattr(s, "_keep", []) + [arr]   # the samples live as long as the struct
+            t.phi = arr.ctypes.data
     for j, bc in enumerate(p.bcs):
         t = s.bcs[j]
         t.bid, t.kind, t.profile, t.ramp = bc.boundary_id, _BCKIND[bc.kind], _PROFILE[bc.profile], _RAMP[bc.ramp]
@@ -196,6 +220,23 @@ class Oracle:
         lib().orc_fields(self.h, _dp(v), _dp(F), _dp(u))
         bs = self.p.box_shape
         return v.reshape((D,) + bs), F.reshape((D * D,) + bs), u.reshape((D,) + bs)
+
+    def stress(self):
+        """Cauchy stress sigma = J^-1 P F^T (D*D, *box) and J = det F (*box) at the current time."""
+        D, N = self.D, self.N
+        sig = np.zeros((D * D, N))
+        J = np.zeros(N)
+        lib().orc_stress(self.h, _dp(sig), _dp(J))
+        bs = self.p.box_shape
+        return sig.reshape((D * D,) + bs), J.reshape(bs)
+
+    def diagnostics(self):
+        """J range, RMS and largest |v|, largest tangent wave speed, compatibility residual RMS and
+        the number of active axis edges, over the active nodes."""
+        out = np.zeros(7)
+        lib().orc_diagnostics(self.h, _dp(out))
+        return dict(J_min=out[0], J_max=out[1], v_rms=out[2], v_max=out[3], c_tangent=out[4],
+                    incompat_rms=out[5], n_edges=int(out[6]))
 
     def populations(self):
         Q = 2 * self.D

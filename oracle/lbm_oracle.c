@@ -14,6 +14,10 @@
  * reconstruction with the Dirichlet / Neumann pair relations (Sec. 3.3-3.4)
  * and the BFL-type interpolation (Eqs. bfl-eta-ge-half, bfl-eta-lt-half).
  *
+ * Threads: when built with OpenMP, the per-node and per-link loops of a step (each iteration
+ * writes only its own node's or link's values) are split over host threads; sums over nodes (the
+ * gauge mean) stay serial, so the results do not depend on the thread count (orc_set_threads).
+ *
  * Storage: dense box arrays, node-major: f[(node*Q + q)*K + k].  Directions
  * q = 2A (+e_A) and 2A+1 (-e_A).  State order U = (v_1..v_D, F_11..F_DD) with
  * F row-major (Eq. state-general-d).
@@ -46,6 +50,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXS 16
 #define ORC_MAXB 16
@@ -63,6 +70,7 @@
 typedef struct {
     int kind, complement, bid, pad;
     double c[3], a[3], Q[9], p;
+    const double *phi; /* kind 5: node samples of the level set (box order) */
 } orc_shape;
 
 typedef struct {
@@ -269,8 +277,80 @@ void orc_collide_node(int D, double c, double omega, double dt, double gamma, co
 /* geometry                                                                   */
 /* ------------------------------------------------------------------------- */
 
-static void shape_eval(const orc_shape *s, int D, const double *X, double *phi, double *grad)
+/* Sampled level set (kind 5): phi between nodes is the multilinear interpolant of the node samples
+ * (linear along every lattice link), constant beyond the outermost node of a non-periodic axis and
+ * periodic on periodic axes; its gradient is the same interpolant of the nodes' central differences
+ * (one-sided at non-periodic ends).  A coordinate within 1e-9 spacings of a node is that node. */
+static double sample_at(const orc_problem *p, const double *phi, const int *j)
 {
+    long idx = 0, stride = 1;
+    for (int a = 0; a < p->dim; a++) {
+        int n = p->n[a], k = j[a];
+        if (p->periodic[a]) k = ((k % n) + n) % n;
+        else k = k < 0 ? 0 : (k >= n ? n - 1 : k);
+        idx += stride * k;
+        stride *= n;
+    }
+    return phi[idx];
+}
+
+static void sampled_eval(const orc_problem *p, const double *phi, const double *X, double *v, double *grad)
+{
+    int D = p->dim, i0[3] = {0, 0, 0};
+    double f[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        double xi = (X[a] - p->origin[a]) / p->dx - 0.5;
+        double fl = floor(xi), fr = xi - fl;
+        if (fr < 1e-9) fr = 0.0;
+        else if (fr > 1.0 - 1e-9) { fl += 1.0; fr = 0.0; }
+        i0[a] = (int)fl;
+        f[a] = fr;
+    }
+    double val = 0.0, g[3] = {0, 0, 0};
+    for (int c = 0; c < (1 << D); c++) {
+        double w = 1.0;
+        int j[3] = {0, 0, 0};
+        for (int a = 0; a < D; a++) {
+            int bit = (c >> a) & 1;
+            w *= bit ? f[a] : 1.0 - f[a];
+            j[a] = i0[a] + bit;
+        }
+        if (w == 0.0) continue;
+        val += w * sample_at(p, phi, j);
+        if (grad)
+            for (int a = 0; a < D; a++) {
+                int jp[3] = {j[0], j[1], j[2]}, jm[3] = {j[0], j[1], j[2]};
+                jp[a] += 1;
+                jm[a] -= 1;
+                double ga;
+                if (p->n[a] == 1) ga = 0.0;
+                else if (p->periodic[a] || (j[a] > 0 && j[a] < p->n[a] - 1))
+                    ga = (sample_at(p, phi, jp) - sample_at(p, phi, jm)) / (2.0 * p->dx);
+                else if (j[a] <= 0)
+                    ga = (sample_at(p, phi, jp) - sample_at(p, phi, j)) / p->dx;
+                else
+                    ga = (sample_at(p, phi, j) - sample_at(p, phi, jm)) / p->dx;
+                g[a] += w * ga;
+            }
+    }
+    *v = val;
+    if (grad)
+        for (int a = 0; a < 3; a++) grad[a] = g[a];
+}
+
+static void shape_eval(const orc_problem *pr, const orc_shape *s, int D, const double *X, double *phi, double *grad)
+{
+    if (s->kind == 5) {
+        double v, g[3];
+        sampled_eval(pr, s->phi, X, &v, grad ? g : NULL);
+        if (s->complement) {
+            v = -v;
+            if (grad) for (int a = 0; a < 3; a++) g[a] = -g[a];
+        }
+        *phi = v;
+        if (grad) for (int a = 0; a < 3; a++) grad[a] = D == 3 || a < 2 ? g[a] : 0.0;
+        return;
+    }
     double d[3] = {X[0] - s->c[0], X[1] - s->c[1], D == 3 ? X[2] - s->c[2] : 0.0};
     double g[3] = {0, 0, 0}, v = 0.0;
     const double *Q = s->Q; /* row-major; local xi = Q^T d */
@@ -340,7 +420,7 @@ static double levelset(const orc_problem *p, const double *X, int *which)
     int w = -1;
     for (int s = 0; s < p->nshapes; s++) {
         double v;
-        shape_eval(&p->shapes[s], p->dim, X, &v, NULL);
+        shape_eval(p, &p->shapes[s], p->dim, X, &v, NULL);
         if (w < 0 || v > best) {
             best = v;
             w = s;
@@ -874,7 +954,7 @@ orc_state *orc_create(const orc_problem *p, int *err)
             int which;
             levelset(&s->p, L->Xb, &which);
             double phv, gr[3];
-            shape_eval(&s->p.shapes[which], D, L->Xb, &phv, gr);
+            shape_eval(&s->p, &s->p.shapes[which], D, L->Xb, &phv, gr);
             double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
             for (int a = 0; a < 3; a++) L->Nb[a] = gr[a] / gn; /* Eq. level-set-normal */
             L->bid = s->p.shapes[which].bid;
@@ -1007,6 +1087,7 @@ static void project(orc_state *s, const double *U, double *u)
         }
     }
     for (int it = 0; it < s->p.proj_iters; it++) {
+#pragma omp parallel for schedule(static)
         for (long m = 0; m < N; m++) {
             if (!s->active[m]) continue;
             double deg = bw[m];
@@ -1080,6 +1161,7 @@ static void one_step(orc_state *s)
     double t = s->step * dt;
     const double *b = s->p.b;
     /* recover U^num,n and u^n */
+#pragma omp parallel for schedule(static)
     for (long m = 0; m < N; m++) {
         if (!s->active[m]) continue;
         recover(D, dt, s->p.gamma, b, s->f + (size_t)m * Q * K, s->U + m * K);
@@ -1090,6 +1172,7 @@ static void one_step(orc_state *s)
     if (proj) {
         project(s, s->U, s->u);
         double *Fr = malloc(sizeof(double) * N * D * D);
+#pragma omp parallel for schedule(static)
         for (long m = 0; m < N; m++) {
             if (!s->active[m]) continue;
             for (int i = 0; i < D; i++) s->ustar[m * D + i] = s->u[m * D + i] - 0.5 * dt * s->U[m * K + i];
@@ -1098,6 +1181,7 @@ static void one_step(orc_state *s)
             for (int k = 0; k < D * D; k++)
                 Fr[m * D * D + k] = (1.0 - s->p.theta_F) * s->U[m * K + D + k] + s->p.theta_F * Fc[k];
         }
+#pragma omp parallel for schedule(static)
         for (long m = 0; m < N; m++) {
             if (!s->active[m]) continue;
             double Uo[12], Ur[12], fo[6 * 12], fr[6 * 12];
@@ -1112,23 +1196,28 @@ static void one_step(orc_state *s)
         free(Fr);
     }
     /* collision and u*^{n+1} */
+    int st = 0;
+#pragma omp parallel for schedule(static) reduction(| : st)
     for (long m = 0; m < N; m++) {
         if (!s->active[m]) continue;
         double *Um = s->U + m * K;
         double J = det_n(D, Um + D);
-        if (!(J > 0.0)) s->status |= ORC_ST_JACOBIAN;
+        if (!(J > 0.0)) st |= ORC_ST_JACOBIAN;
         for (int k = 0; k < K; k++)
-            if (!isfinite(Um[k])) s->status |= ORC_ST_NONFINITE;
+            if (!isfinite(Um[k])) st |= ORC_ST_NONFINITE;
         collide(D, c, s->p.omega, dt, s->p.gamma, b, mu_at(s, m), lam, Um, s->f + (size_t)m * Q * K);
         for (int i = 0; i < D; i++) s->ustar[m * D + i] = s->u[m * D + i] + 0.5 * dt * Um[i];
     }
+    s->status |= st;
     if (proj) {
         project(s, s->U, s->u);
+#pragma omp parallel for schedule(static)
         for (long m = 0; m < N; m++)
             if (s->active[m])
                 for (int i = 0; i < D; i++) s->ustar[m * D + i] = s->u[m * D + i] + 0.5 * dt * s->U[m * K + i];
     }
-    /* streaming over interior links (Eq. streaming-general-d) */
+    /* streaming over interior links (Eq. streaming-general-d); each target slot has one source */
+#pragma omp parallel for schedule(static)
     for (long m = 0; m < N; m++) {
         if (!s->active[m]) continue;
         for (int q = 0; q < Q; q++) {
@@ -1140,6 +1229,8 @@ static void one_step(orc_state *s)
     }
     /* cut-link reconstruction */
     double th = t + 0.5 * dt;
+    int stl = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : stl)
     for (long li = 0; li < s->ncut; li++) {
         orc_link *L = &s->links[li];
         const orc_bc *bc = &s->p.bcs[L->bc];
@@ -1171,7 +1262,7 @@ static void one_step(orc_state *s)
                 }
             neumann_traction(bc, D, L->Xb, th, T);
             double h[3] = {L->h[0], L->h[1], L->h[2]};
-            if (orc_newton(D, mu_at(s, L->m), lam, L->Nb, &g[0][0], &L->t[0][0], T, h) < 0) s->status |= ORC_ST_NEWTON;
+            if (orc_newton(D, mu_at(s, L->m), lam, L->Nb, &g[0][0], &L->t[0][0], T, h) < 0) stl |= ORC_ST_NEWTON;
             else for (int i = 0; i < 3; i++) L->h[i] = h[i];
             double Fb[9], Pb[9];
             fb_of_h(D, L->h, L->Nb, &g[0][0], &L->t[0][0], Fb);
@@ -1199,10 +1290,24 @@ static void one_step(orc_state *s)
                 dst[k] = Dp[k] * (2.0 * eta * fo[k] + (1.0 - 2.0 * eta) * fu[k]) + S[k];
         }
     }
+    s->status |= stl;
     double *tmp = s->f;
     s->f = s->fnew;
     s->fnew = tmp;
     s->step++;
+}
+
+/* host threads for the per-node and per-link loops of a step (1: serial); returns the count in
+ * use, 1 when the file was built without OpenMP */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int orc_step(orc_state *s, int nsteps)
@@ -1232,6 +1337,135 @@ int orc_fields(orc_state *s, double *v, double *F, double *u)
 }
 
 /* raw populations, box SoA layout [(q*K + k)*N + m] for tests */
+/* Cauchy stress sigma = J^-1 P F^T (Eq. cauchy-recovery-general, D*D planes, row-major) and
+ * J = det F (one plane) at the current time, box planes, zero off the body */
+int orc_stress(orc_state *s, double *sigma, double *Jout)
+{
+    if (!s->f) return ORC_EARG;
+    int D = s->D, K = s->K, Q = s->Q;
+    long N = s->N;
+    for (long m = 0; m < N; m++) {
+        double U[12] = {0}, P[9], sg[9] = {0};
+        double J = 0.0;
+        if (s->active[m]) {
+            recover(D, s->dt, s->p.gamma, s->p.b, s->f + (size_t)m * Q * K, U);
+            J = orc_piola(D, mu_at(s, m), s->p.lam, U + D, P);
+            for (int i = 0; i < D; i++)
+                for (int B = 0; B < D; B++) {
+                    double acc = 0.0;
+                    for (int A = 0; A < D; A++) acc += P[i * D + A] * U[D + B * D + A];
+                    sg[i * D + B] = acc / J;
+                }
+        }
+        if (Jout) Jout[m] = J;
+        if (sigma)
+            for (int k = 0; k < D * D; k++) sigma[k * N + m] = sg[k];
+    }
+    return s->status;
+}
+
+/* smallest eigenvalue of a symmetric D x D matrix by cyclic Jacobi rotations (plain, to round-off) */
+static double sym_min_eigen_jacobi(int D, const double *Cin)
+{
+    double A[9];
+    memcpy(A, Cin, sizeof(double) * D * D);
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < D; p++)
+            for (int q = p + 1; q < D; q++) off += A[p * D + q] * A[p * D + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < D; p++)
+            for (int q = p + 1; q < D; q++) {
+                double apq = A[p * D + q];
+                if (fabs(apq) < 1e-300) continue;
+                double theta = (A[q * D + q] - A[p * D + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < D; k++) { /* columns p, q */
+                    double akp = A[k * D + p], akq = A[k * D + q];
+                    A[k * D + p] = c * akp - sn * akq;
+                    A[k * D + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < D; k++) { /* rows p, q */
+                    double apk = A[p * D + k], aqk = A[q * D + k];
+                    A[p * D + k] = c * apk - sn * aqk;
+                    A[q * D + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double mn = A[0];
+    for (int k = 1; k < D; k++) mn = fmin(mn, A[k * D + k]);
+    return mn;
+}
+
+/* Largest squared tangent wave speed at F (rho0 = 1): max over unit n of the largest eigenvalue of
+ * Q(n; F) (Eq. acoustic-tensor-general-d).  For the neo-Hookean tangent Q(n) = mu I + kappa a a^T,
+ * a = F^{-T} n, kappa = mu + lam (J^2 + 1)/2: its eigenvalues are mu and mu + kappa |a|^2, and
+ * max |F^{-T} n|^2 over unit n is 1 / (smallest eigenvalue of F^T F). */
+double orc_tangent_speed2(int D, double mu, double lam, const double *F)
+{
+    double C[9];
+    for (int i = 0; i < D; i++)
+        for (int j = 0; j < D; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < D; k++) acc += F[k * D + i] * F[k * D + j];
+            C[i * D + j] = acc;
+        }
+    double J = det_n(D, F);
+    double kappa = mu + 0.5 * lam * (J * J + 1.0);
+    double smin = sym_min_eigen_jacobi(D, C);
+    if (kappa <= 0.0) return mu;
+    return mu + kappa / smin;
+}
+
+/* whole-body diagnostics over the active nodes: out = {J_min, J_max, v_rms, v_max, c_T max,
+ * compatibility residual RMS over active axis edges |u_m - u_l - (G_m + G_l)(X_m - X_l)/2|,
+ * edge count} */
+int orc_diagnostics(orc_state *s, double *out)
+{
+    if (!s->f) return ORC_EARG;
+    int D = s->D, K = s->K, Q = s->Q;
+    long N = s->N;
+    double *U = malloc(sizeof(double) * N * K), *u = malloc(sizeof(double) * N * D);
+    for (long m = 0; m < N; m++) {
+        if (!s->active[m]) continue;
+        recover(D, s->dt, s->p.gamma, s->p.b, s->f + (size_t)m * Q * K, U + m * K);
+        for (int i = 0; i < D; i++) u[m * D + i] = s->ustar[m * D + i] + 0.5 * s->dt * U[m * K + i];
+    }
+    double jmin = INFINITY, jmax = -INFINITY, v2sum = 0.0, v2max = 0.0, c2 = 0.0, e2 = 0.0, ne = 0.0;
+    for (long m = 0; m < N; m++) {
+        if (!s->active[m]) continue;
+        const double *Um = U + m * K;
+        double J = det_n(D, Um + D), v2 = 0.0;
+        for (int i = 0; i < D; i++) v2 += Um[i] * Um[i];
+        jmin = fmin(jmin, J);
+        jmax = fmax(jmax, J);
+        v2sum += v2;
+        v2max = fmax(v2max, v2);
+        c2 = fmax(c2, orc_tangent_speed2(D, mu_at(s, m), s->p.lam, Um + D));
+        for (int A = 0; A < D; A++) {
+            long l = nbr(s, m, A, 1);
+            if (l < 0 || !s->active[l]) continue;
+            for (int i = 0; i < D; i++) {
+                double Gm = Um[D + i * D + A] - (i == A ? 1.0 : 0.0), Gl = U[l * K + D + i * D + A] - (i == A ? 1.0 : 0.0);
+                double e = (u[m * D + i] - u[l * D + i]) + 0.5 * (Gm + Gl) * s->p.dx; /* X_m - X_l = -dx e_A */
+                e2 += e * e;
+            }
+            ne += 1.0;
+        }
+    }
+    out[0] = jmin;
+    out[1] = jmax;
+    out[2] = sqrt(v2sum / (double)s->nactive);
+    out[3] = sqrt(v2max);
+    out[4] = sqrt(c2);
+    out[5] = ne > 0.0 ? sqrt(e2 / ne) : 0.0;
+    out[6] = ne;
+    free(U);
+    free(u);
+    return s->status;
+}
+
 int orc_populations(orc_state *s, double *out)
 {
     if (!s->f) return ORC_EARG;

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(32, 16) k_adj_step_tma(const StepArgs<float> a
             }
     }
     __syncwarp();
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0, a.spin))) {
         if (lane == 0) set_status(a.status, kStTimeout);
         mbar_wait_bounded(bar, 0);  // let the copies in flight land before the warp exits
         return;

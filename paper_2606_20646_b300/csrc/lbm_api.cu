@@ -68,6 +68,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     h->l_h = c.take<char>((size_t)3 * nc * rs);
     h->l_rec = c.take<char>((size_t)K * nc * rs);
     h->l_fo = c.take<char>((size_t)2 * K * nc * rs);
+    h->l_bvec = rs == 4 ? c.take<float4>(nc) : nullptr;
     if (h->has_neumann_bc) {
         h->l_sidx = c.take<int>((size_t)kLsqCap * nc);
         h->l_w = c.take<char>((size_t)2 * kLsqCap * nc * rs);
@@ -89,6 +90,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->dA = h->dB = h->resid = h->vst = h->Gst = nullptr;
     }
     h->staging = h->opt.host_staging ? c.take<double>((size_t)(2 * D + D * D + D * K) * h->box.nbox) : nullptr;
+    h->diag = c.take<double>((size_t)kDiagRec * (kReduceBlocks + 1));
     if (h->opt.adjoint) {
         h->mu_field = c.take<char>((size_t)np * rs);
         h->adj_g[0] = c.take<char>((size_t)Q * K * np * rs);
@@ -146,9 +148,22 @@ const char *lbm_error_string(int code) {
     case LBM_ERR_STORAGE: return "storage missing, too small or misaligned";
     case LBM_ERR_STATE: return "call out of order";
     case LBM_ERR_DEVICE: return "device status word is non-zero";
-    case LBM_ERR_CAPACITY: return "LSQ stencil capacity exceeded";
+    case LBM_ERR_CAPACITY: return "a fixed capacity was exceeded (LSQ stencil, census box)";
+    case LBM_ERR_UNSTABLE_C: return "lattice speed c below the wave-speed audit's bound";
     default: return "unknown error";
     }
+}
+
+// the lattice a sampled shape's node values sit on
+static void set_sampled(ShapeD &d, const lbm_shape &sh, const lbm_grid &g) {
+    d.phi = sh.kind == LBM_SHAPE_SAMPLED ? sh.phi : nullptr;
+    d.per = 0;
+    for (int a = 0; a < 3; ++a) {
+        d.n[a] = a < g.dim ? g.n[a] : 1;
+        d.org[a] = a < g.dim ? g.origin[a] : 0.0;
+        if (a < g.dim && g.periodic[a]) d.per |= 1 << a;
+    }
+    d.dx = g.dx;
 }
 
 static int validate_grid(const lbm_grid *g) {
@@ -159,6 +174,16 @@ static int validate_grid(const lbm_grid *g) {
     long long nbox = (long long)g->n[0] * g->n[1] * nz;
     if (nbox >= (1LL << 31) - 64) return LBM_ERR_ARG;
     return LBM_OK;
+}
+
+// Wave-speed audit (Sec. 2, Eq. acoustic-tensor-general-d): c >= factor * c_T with c_T^2 the largest
+// squared tangent speed; factor = options.c_audit, 2.5 when 0, no audit when negative
+static bool audit_ok(const lbm_options *opt, int dim, double cT2) {
+    (void)dim;
+    if (opt->c_audit < 0.0) return true;
+    const double factor = opt->c_audit > 0.0 ? opt->c_audit : 2.5;
+    if (!(cT2 >= 0.0)) return false;  // NaN or an unphysical material
+    return opt->c >= factor * std::sqrt(cT2) * (1.0 - 1e-12);
 }
 
 int lbm_geometry_bytes(const lbm_grid *grid, size_t *bytes) {
@@ -201,8 +226,9 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         return LBM_ERR_ARG;
     for (int s = 0; s < ls->nshapes; ++s) {
         const lbm_shape &sh = ls->shapes[s];
-        if (sh.kind < 0 || sh.kind > LBM_SHAPE_HALFSPACE) return LBM_ERR_ARG;
+        if (sh.kind < 0 || sh.kind > LBM_SHAPE_SAMPLED) return LBM_ERR_ARG;
         if (sh.kind == LBM_SHAPE_SUPERELLIPSE && (grid->dim != 2 || !(sh.p >= 1.0))) return LBM_ERR_ARG;
+        if (sh.kind == LBM_SHAPE_SAMPLED && !is_device_ptr(sh.phi)) return LBM_ERR_ARG;
     }
     for (int b = 0; b < nbc; ++b) {
         const lbm_bc &bc = bcs[b];
@@ -215,6 +241,13 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         if (bc.kind == LBM_BC_NEUMANN && !(bc.profile == LBM_PROFILE_ZERO || bc.profile == LBM_PROFILE_RADIAL ||
                                            bc.profile == LBM_PROFILE_CONST))
             return LBM_ERR_ARG;
+    }
+    if (!std::isfinite(opt->c_audit)) return LBM_ERR_ARG;
+    // wave-speed audit of the reference state F = I: c_T^2 = lambda + 2 mu for every material
+    {
+        double c2 = mat->lambda + 2.0 * mat->mu;
+        for (int g = 0; g < ls->ngroups; ++g) c2 = std::max(c2, ls->groups[g].material.lambda + 2.0 * ls->groups[g].material.mu);
+        if (!audit_ok(opt, grid->dim, c2)) return LBM_ERR_UNSTABLE_C;
     }
     size_t need = 0;
     lbm_geometry_bytes(grid, &need);
@@ -247,6 +280,7 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
         for (int a = 0; a < 3; ++a) { d.c[a] = sh.center[a]; d.a[a] = sh.axes[a]; }
         for (int a = 0; a < 9; ++a) d.Q[a] = sh.rot[a];
         d.p = sh.p;
+        set_sampled(d, sh, *grid);
     }
     h->ngroups = ls->ngroups;
     for (int g = 0; g < ls->ngroups; ++g) {
@@ -290,6 +324,7 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     carve_geometry(h, h->geo, &h->geo_bytes);
 
     auto fail = [&](int rc) { delete h; return rc; };
+    NvtxRange range("lbm_create geometry pass");
     cudaStream_t st = h->stream;
     if (cudaMemsetAsync(h->geo, 0, h->geo_bytes, st) != cudaSuccess) return fail(LBM_ERR_CUDA);
     if (cudaMemcpyAsync(h->dshapes, h->shapes, sizeof(h->shapes), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -395,6 +430,33 @@ int lbm_set_initial(lbm_handle *h, int mode, const double *v0, const double *F0,
         CK(stage(F0, const_cast<double *>(pF), (size_t)D * D * N));
         CK(stage(u0, const_cast<double *>(pu), (size_t)D * N));
         if (dU0) CK(stage(dU0, const_cast<double *>(pd), (size_t)D * K * N));
+    }
+    if (h->opt.c_audit >= 0.0) {  // wave-speed audit of the initial F0 over the active nodes
+        const unsigned gr = (unsigned)std::max<long long>(1, std::min<long long>(grid_for(h->nseg, 4), kReduceBlocks));
+        const uint8_t *mt = h->ngroups > 0 ? h->gidx : nullptr;
+        const double *mtab = h->ngroups > 0 ? h->mtab_d : nullptr;
+        if (h->D == 2) {
+            if (h->real_size == 8)
+                k_audit_f0<2, double><<<gr, 128, 0, h->stream>>>(h->box, h->seg, (int)h->nseg, h->flags, pF, h->mat.mu, h->mat.lambda, mt, mtab,
+                                                                 h->mu_field_on ? static_cast<const double *>(h->mu_field) : nullptr, h->diag);
+            else
+                k_audit_f0<2, float><<<gr, 128, 0, h->stream>>>(h->box, h->seg, (int)h->nseg, h->flags, pF, h->mat.mu, h->mat.lambda, mt, mtab,
+                                                                h->mu_field_on ? static_cast<const float *>(h->mu_field) : nullptr, h->diag);
+        } else {
+            if (h->real_size == 8)
+                k_audit_f0<3, double><<<gr, 128, 0, h->stream>>>(h->box, h->seg, (int)h->nseg, h->flags, pF, h->mat.mu, h->mat.lambda, mt, mtab,
+                                                                 h->mu_field_on ? static_cast<const double *>(h->mu_field) : nullptr, h->diag);
+            else
+                k_audit_f0<3, float><<<gr, 128, 0, h->stream>>>(h->box, h->seg, (int)h->nseg, h->flags, pF, h->mat.mu, h->mat.lambda, mt, mtab,
+                                                                h->mu_field_on ? static_cast<const float *>(h->mu_field) : nullptr, h->diag);
+        }
+        CKL();
+        std::vector<double> part(gr);
+        CK(cudaMemcpyAsync(part.data(), h->diag, gr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        double c2 = 0.0;
+        for (double x : part) c2 = std::isnan(x) ? x : std::max(c2, x);
+        if (!audit_ok(&h->opt, h->D, c2)) return LBM_ERR_UNSTABLE_C;
     }
     int rc = ops(h).init(h, mode, pv, pF, pu, pd);
     if (rc) return rc;
@@ -506,6 +568,7 @@ static int time_shapes(lbm_handle *h, int steps, void *scratch, double *ms_per_s
 
 int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     if (!h || steps < 1 || !scratch || (reinterpret_cast<uintptr_t>(scratch) % kAlign)) return LBM_ERR_ARG;
+    NvtxRange range("lbm_autotune");
     if (!h->initialized || h->timing || (h->opt.adjoint && h->adj_next >= 0)) return LBM_ERR_STATE;
     int rc = lbm_save_state(h, scratch);
     if (rc) return rc;
@@ -549,6 +612,12 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
         out->ms_per_step = best;
         out->default_ms_per_step = def_ms;
     }
+    return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_handle *h, int polls) {
+    if (!h) return LBM_ERR_ARG;
+    h->wait_limit = polls < 0 ? -1 : polls;
     return LBM_OK;
 }
 
@@ -676,32 +745,65 @@ int lbm_adjoint_gradients(lbm_handle *h, double *grad_mu, double *grad_b) {
     return LBM_OK;
 }
 
-int lbm_fields(lbm_handle *h, double *v, double *F, double *u) {
-    if (!h) return LBM_ERR_ARG;
+int lbm_fields_ex(lbm_handle *h, double *v, double *F, double *u, double *sigma, double *J, int layout) {
+    if (!h || (layout != LBM_LAYOUT_PLANES && layout != LBM_LAYOUT_NODES)) return LBM_ERR_ARG;
     if (!h->initialized) return LBM_ERR_STATE;
     const int D = h->D;
     const long long N = h->box.nbox;
-    double *ptr[3] = {v, F, u};
-    const size_t cnt[3] = {(size_t)D * N, (size_t)D * D * N, (size_t)D * N};
-    double *dev[3] = {nullptr, nullptr, nullptr};
-    bool host[3] = {false, false, false};
-    size_t off = 0;
-    for (int j = 0; j < 3; ++j) {
-        if (!ptr[j]) { off += cnt[j]; continue; }
+    double *ptr[5] = {v, F, u, sigma, J};
+    const size_t cnt[5] = {(size_t)D * N, (size_t)D * D * N, (size_t)D * N, (size_t)D * D * N, (size_t)N};
+    double *dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool host[5] = {false, false, false, false, false};
+    size_t off = 0;  // staging holds (2D + D^2 + D K) n_box values, more than the 2D + 2D^2 + 1 used here
+    for (int j = 0; j < 5; ++j) {
+        if (!ptr[j]) continue;
         if (is_device_ptr(ptr[j])) {
             dev[j] = ptr[j];
         } else {
             if (!h->staging) return LBM_ERR_ARG;
             dev[j] = h->staging + off;
             host[j] = true;
+            off += cnt[j];
         }
-        off += cnt[j];
         CK(cudaMemsetAsync(dev[j], 0, cnt[j] * sizeof(double), h->stream));
     }
-    int rc = ops(h).fields(h, dev[0], dev[1], dev[2]);
+    FieldOut o;
+    o.v = dev[0];
+    o.F = dev[1];
+    o.u = dev[2];
+    o.sigma = dev[3];
+    o.J = dev[4];
+    o.layout = layout;
+    int rc = ops(h).fields(h, o);
     if (rc) return rc;
-    for (int j = 0; j < 3; ++j)
+    for (int j = 0; j < 5; ++j)
         if (host[j]) CK(cudaMemcpyAsync(ptr[j], dev[j], cnt[j] * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_handle *h, double *v, double *F, double *u) {
+    return lbm_fields_ex(h, v, F, u, nullptr, nullptr, LBM_LAYOUT_PLANES);
+}
+
+int lbm_diagnostics(lbm_handle *h, lbm_diag *out) {
+    if (!h || !out) return LBM_ERR_ARG;
+    if (!h->initialized) return LBM_ERR_STATE;
+    int rc = ops(h).diagnostics(h);
+    if (rc) return rc;
+    double r[kDiagRec];
+    CK(cudaMemcpyAsync(r, h->diag + (size_t)kReduceBlocks * kDiagRec, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->n_active = h->n_active;
+    out->J_min = r[2];
+    out->J_max = r[3];
+    out->v_rms = std::sqrt(r[0] / (double)h->n_active);
+    out->v_max = std::sqrt(r[1]);
+    out->c_tangent = std::sqrt(r[4]);
+    out->n_edges = (long long)r[6];
+    out->incompat_rms = r[6] > 0.0 ? std::sqrt(r[5] / r[6]) : 0.0;
+    out->step = h->step;
+    out->t = h->step * (h->grid.dx / h->opt.c);
     return LBM_OK;
 }
 
@@ -710,8 +812,8 @@ int lbm_sync(lbm_handle *h, int *device_status) {
     int stv = 0;
     CK(cudaMemcpyAsync(&stv, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (device_status) *device_status = stv & (31 | kStTimeout);
-    if (stv & (31 | kStTimeout)) {
+    if (device_status) *device_status = stv & (31 | kStTimeout | kStBounds);
+    if (stv & (31 | kStTimeout | kStBounds)) {
         CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
         CK(cudaStreamSynchronize(h->stream));
         return LBM_ERR_DEVICE;

@@ -3,6 +3,7 @@
 // stress and small dense algebra.  Used by the kernels in lbm_kernels.cuh.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -21,11 +22,15 @@ constexpr uint8_t kCutMask = 0x3f;     // bit q: link (m, q) is cut (neighbour m
 
 // device status bits (mirrors lbm_device_status of the C ABI)
 constexpr int kStNonfinite = 1, kStJacobian = 2, kStNewton = 4, kStLsq = 8, kStCapacity = 16, kStDomain = 32,
-              kStNoBC = 64;
+              kStNoBC = 64, kStBounds = 256;
 
 struct ShapeD {
     int kind, complement, bid, pad;
     double c[3], a[3], Q[9], p;
+    // kind 5 (node samples): the samples (box order, caller memory) and the lattice they sit on
+    const double *phi;
+    int n[3], per;  // nodes per axis; bit a: axis a periodic
+    double org[3], dx;
 };
 
 struct BCD {
@@ -37,7 +42,75 @@ struct BCD {
 // level set: phi = max over shapes (Sec. 3.1, Eq. level-set-domain)
 // ---------------------------------------------------------------------------------------------
 
+// Sampled level set: phi between nodes is the multilinear interpolant of the node samples (linear
+// along every lattice link), constant beyond the outermost node of a non-periodic axis (so a body
+// reaching a non-periodic face is refused by the box-face rule) and periodic on periodic axes; its
+// gradient, for the normal of Eq. (level-set-normal), is the same interpolant of the nodes'
+// central differences (one-sided at non-periodic ends).  A coordinate within 1e-9 spacings of a node
+// is that node, so node and link evaluations read the samples exactly.
+__device__ inline double sample_at(const ShapeD &s, int D, const int j[3]) {
+    long long idx = 0, stride = 1;
+    for (int a = 0; a < D; ++a) {
+        const int n = s.n[a];
+        int k = j[a];
+        if ((s.per >> a) & 1) k = ((k % n) + n) % n;
+        else k = k < 0 ? 0 : (k >= n ? n - 1 : k);
+        idx += stride * k;
+        stride *= n;
+    }
+    return s.phi[idx];
+}
+
+__device__ inline double sampled_phi(const ShapeD &s, int D, const double X[3], double g[3]) {
+    int i0[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < D; ++a) {
+        const double xi = (X[a] - s.org[a]) / s.dx - 0.5;
+        double fl = floor(xi), fr = xi - fl;
+        if (fr < 1e-9) fr = 0.0;
+        else if (fr > 1.0 - 1e-9) { fl += 1.0; fr = 0.0; }
+        i0[a] = (int)fl;
+        f[a] = fr;
+    }
+    double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < (1 << D); ++c) {
+        double w = 1.0;
+        int j[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            const int bit = (c >> a) & 1;
+            w *= bit ? f[a] : 1.0 - f[a];
+            j[a] = i0[a] + bit;
+        }
+        if (w == 0.0) continue;
+        v += w * sample_at(s, D, j);
+        if (g)
+            for (int a = 0; a < D; ++a) {
+                int jp[3] = {j[0], j[1], j[2]}, jm[3] = {j[0], j[1], j[2]};
+                jp[a] += 1;
+                jm[a] -= 1;
+                double ga;
+                if (s.n[a] == 1) ga = 0.0;
+                else if (((s.per >> a) & 1) || (j[a] > 0 && j[a] < s.n[a] - 1))
+                    ga = (sample_at(s, D, jp) - sample_at(s, D, jm)) / (2.0 * s.dx);
+                else if (j[a] <= 0)
+                    ga = (sample_at(s, D, jp) - sample_at(s, D, j)) / s.dx;
+                else
+                    ga = (sample_at(s, D, j) - sample_at(s, D, jm)) / s.dx;
+                gr[a] += w * ga;
+            }
+    }
+    if (g) { g[0] = gr[0]; g[1] = gr[1]; g[2] = gr[2]; }
+    return v;
+}
+
 __device__ inline double shape_phi(const ShapeD &s, int D, const double X[3], double g[3]) {
+    if (s.kind == 5) {
+        double gs[3];
+        double v = sampled_phi(s, D, X, g ? gs : nullptr);
+        if (s.complement) { v = -v; gs[0] = -gs[0]; gs[1] = -gs[1]; gs[2] = -gs[2]; }
+        if (g) { g[0] = gs[0]; g[1] = gs[1]; g[2] = (D == 3) ? gs[2] : 0.0; }
+        return v;
+    }
     const double d0 = X[0] - s.c[0], d1 = X[1] - s.c[1], d2 = (D == 3) ? X[2] - s.c[2] : 0.0;
     double v;
     double gx = 0.0, gy = 0.0, gz = 0.0;
@@ -145,7 +218,7 @@ __device__ inline double levelset(const LevelSetD &L, int D, const double X[3], 
 // boundary data: ramps s(t), Dirichlet displacement/velocity, nominal traction
 // ---------------------------------------------------------------------------------------------
 
-__device__ inline void ramp_eval(int kind, double T, double t, double &s, double &sd) {
+__host__ __device__ inline void ramp_eval(int kind, double T, double t, double &s, double &sd) {
     const double pi = 3.14159265358979323846;
     switch (kind) {
     case 1: if (t < T) { s = t / T; sd = 1.0 / T; } else { s = 1.0; sd = 0.0; } return;
@@ -210,6 +283,19 @@ __device__ inline void traction_eval(const BCD &bc, int D, const double X[3], do
     }
 }
 
+// The geometric vector g_l of a cut link for its boundary profile, in which the FP32 forms write the
+// boundary value as M(t) g_l + k(t): X_b - center (affine, twist-stretch), e_R (radial), 0 (others)
+__device__ inline void link_gvec(const BCD &bc, int D, const double Xb[3], double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    const double d[3] = {Xb[0] - bc.center[0], Xb[1] - bc.center[1], (D == 3) ? Xb[2] - bc.center[2] : 0.0};
+    if (bc.profile == 1 || bc.profile == 3) {
+        for (int i = 0; i < 3; ++i) out[i] = d[i];
+    } else if (bc.profile == 2) {
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int i = 0; i < D; ++i) out[i] = d[i] / r;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // constitutive law: compressible neo-Hookean (Sec. 4.1, Eq. validation-nh-energy)
 //   P = mu F + (lam/2 (J^2 - 1) - mu) F^{-T}
@@ -251,6 +337,90 @@ __device__ __forceinline__ real piola(const real F[D * D], real mu, real lam, re
     #pragma unroll
     for (int k = 0; k < D * D; ++k) P[k] = mu * F[k] + s * (C[k] / J);  // F^{-T} = cof(F) / J
     return J;
+}
+
+// J - 1 = det(I + G) - 1 from the displacement gradient G = F - I, without forming F: the sum of
+// the invariants tr G + I_2(G) + det G (3D), tr G + det G (2D), accurate to the relative precision
+// of G instead of the absolute precision of F
+template <typename real, int D> __device__ __forceinline__ real det_m1(const real G[D * D]) {
+    if constexpr (D == 2) {
+        return (G[0] + G[3]) + (G[0] * G[3] - G[1] * G[2]);
+    } else {
+        const real i2 = (G[0] * G[4] - G[1] * G[3]) + (G[0] * G[8] - G[2] * G[6]) + (G[4] * G[8] - G[5] * G[7]);
+        return ((G[0] + G[4]) + G[8]) + i2 + det<real, D>(G);
+    }
+}
+
+// First Piola stress of the neo-Hookean law from G = F - I (FP32 forms).  The same function as
+// piola(), P = mu F + (lam/2 (J^2 - 1) - mu) F^{-T}, rearranged with I - F^{-T} = F^{-T} G^T into
+//   P = mu (G + F^{-T} G^T) + (lam/2) (J - 1)(J + 1) F^{-T}
+// so that the terms cancelling near F = I (mu F - mu F^{-T}, J^2 - 1) are never formed: every term
+// is a product of small quantities, and P keeps the relative precision of G.  Returns J; Fit
+// receives F^{-T}.
+template <typename real, int D>
+__device__ __forceinline__ real piola_g(const real G[D * D], real mu, real lam, real P[D * D], real Fit[D * D]) {
+    real F[D * D], C[D * D];
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) F[k] = G[k] + ((k / D == k % D) ? real(1) : real(0));
+    cofactor<real, D>(F, C);
+    const real jm1 = det_m1<real, D>(G);
+    const real J = real(1) + jm1;
+    const real iJ = real(1) / J;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) Fit[k] = C[k] * iJ;
+    const real vol = real(0.5) * lam * jm1 * (J + real(1));
+    #pragma unroll
+    for (int i = 0; i < D; ++i)
+        #pragma unroll
+        for (int A = 0; A < D; ++A) {
+            real fg = real(0);
+            #pragma unroll
+            for (int k = 0; k < D; ++k) fg += Fit[i * D + k] * G[A * D + k];
+            P[i * D + A] = mu * (G[i * D + A] + fg) + vol * Fit[i * D + A];
+        }
+    return J;
+}
+
+// smallest eigenvalue of a symmetric D x D matrix (row-major): closed form in 2D, the trigonometric
+// form of the cubic's roots in 3D
+template <int D> __host__ __device__ inline double sym_min_eig(const double C[D * D]) {
+    if constexpr (D == 2) {
+        const double h = 0.5 * (C[0] + C[3]), d = 0.5 * (C[0] - C[3]);
+        return h - sqrt(d * d + C[1] * C[1]);
+    } else {
+        const double p1 = C[1] * C[1] + C[2] * C[2] + C[5] * C[5];
+        const double q = (C[0] + C[4] + C[8]) / 3.0;
+        if (!(p1 > 0.0)) return fmin(C[0], fmin(C[4], C[8]));
+        const double a = C[0] - q, b = C[4] - q, c = C[8] - q;
+        const double p = sqrt((a * a + b * b + c * c + 2.0 * p1) / 6.0);
+        const double B[9] = {a / p, C[1] / p, C[2] / p, C[3] / p, b / p, C[5] / p, C[6] / p, C[7] / p, c / p};
+        double r = 0.5 * (B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                          B[2] * (B[3] * B[7] - B[4] * B[6]));
+        r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+        const double phi = acos(r) / 3.0;
+        return q + 2.0 * p * cos(phi + 2.0943951023931954923);  // + 2 pi / 3: the smallest root
+    }
+}
+
+// Squared largest tangent wave speed of the neo-Hookean law at F (rho0 = 1): the largest eigenvalue
+// of the acoustic tensor Q(n; F) = n_A C_iAkB n_B (Eq. acoustic-tensor-general-d) over unit
+// directions n.  Here Q(n) = mu I + kappa a a^T with a = F^{-T} n and kappa = mu + lam (J^2 + 1)/2,
+// so its eigenvalues are mu and mu + kappa |a|^2, and max_n |F^{-T} n|^2 = 1 / sigma_min(F)^2, the
+// reciprocal of the smallest eigenvalue of F^T F.  At F = I: lam + 2 mu.
+template <int D> __host__ __device__ inline double tangent_speed2(const double F[D * D], double mu, double lam) {
+    double C[D * D], J;
+    if constexpr (D == 2) J = F[0] * F[3] - F[1] * F[2];
+    else J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) + F[2] * (F[3] * F[7] - F[4] * F[6]);
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < D; ++k) v += F[k * D + i] * F[k * D + j];
+            C[i * D + j] = v;
+        }
+    const double smin = sym_min_eig<D>(C);
+    const double kappa = mu + 0.5 * lam * (J * J + 1.0);
+    const double top = smin > 0.0 ? mu + kappa / smin : INFINITY;
+    return kappa > 0.0 ? top : mu;
 }
 
 // dense D x D solve by Cramer's rule (D = 2, 3); returns false if singular

@@ -15,10 +15,12 @@
 
 #include <cudaTypedefs.h>
 #include <cstdlib>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
+#include "lbm_links.cuh"
 #include "lbm_adjoint.cuh"
 
 using namespace tlv;
@@ -100,8 +102,10 @@ struct lbm_handle {
     int *l_node = nullptr, *l_q = nullptr, *l_bc = nullptr, *l_ns = nullptr, *l_sidx = nullptr;
     double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
     void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr, *l_fo = nullptr;
+    float4 *l_bvec = nullptr;  // FP32 forms: per-link geometric vector of the boundary profile
     void *u0 = nullptr, *u1 = nullptr;  // projection warm starts (displacement-accumulator layout)
     double *partial = nullptr, *mean = nullptr, *staging = nullptr;
+    double *diag = nullptr;  // diagnostics and audit reductions: kReduceBlocks partial records + the result
     void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
     long long n_neu = 0, n_dir = 0, lsq_entries = 0;
     // state
@@ -116,6 +120,7 @@ struct lbm_handle {
     // tile shapes (0: the form's default): 32-node windows per warp of the fused kernel, segments
     // per warp of a Jacobi sweep, threads per block of the link kernel
     int tune_nw = 0, tune_jseg = 0, tune_lblock = 0;
+    int wait_limit = -1;  // polls of the bulk-copy kernels' first wait (< 0: kTmaSpin)
     // timing
     bool timing = false;
     std::vector<EventPair> events;
@@ -126,6 +131,14 @@ struct lbm_handle {
 // =============================================================================================
 // helpers
 // =============================================================================================
+
+// NVTX range over a host scope (header-only NVTX 3: inert unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define CK(call)                                           \
     do {                                                   \
@@ -330,6 +343,7 @@ template <typename real, int D, typename pop = real> struct Impl {
         L.w = static_cast<real *>(h->l_w);
         L.rec = static_cast<real *>(h->l_rec);
         L.fo = static_cast<real *>(h->l_fo);
+        L.bvec = h->l_bvec;
         L.ncut = h->n_cut;
         return L;
     }
@@ -363,6 +377,8 @@ template <typename real, int D, typename pop = real> struct Impl {
         a.mu_field = h->mu_field_on ? static_cast<const real *>(h->mu_field) : nullptr;
         a.mom_out = static_cast<real *>(h->mom_out);
         a.status = h->status;
+        a.spin = h->wait_limit >= 0 ? h->wait_limit : kTmaSpin;
+        a.ncut = std::max<long long>(h->n_cut, 1);
         return a;
     }
 
@@ -381,6 +397,7 @@ template <typename real, int D, typename pop = real> struct Impl {
         p.resid = static_cast<real *>(h->resid);
         p.t = t;
         p.beta = h->opt.proj_beta;
+        p.status = h->status;
         return p;
     }
 
@@ -452,6 +469,7 @@ template <typename real, int D, typename pop = real> struct Impl {
     }
 
     static int link_build(lbm_handle *h) {
+        NvtxRange range("cut-link geometry");
         setup_tma(h);
         if (h->nseg == 0) return LBM_OK;
         k_link_build<real, D><<<grid_for(h->nseg, 4), 128, 0, h->stream>>>(
@@ -471,6 +489,53 @@ template <typename real, int D, typename pop = real> struct Impl {
             static_cast<real *>(h->ustar));
         CKL();
         return LBM_OK;
+    }
+
+    // boundary values of every boundary condition at time th as M g_l + k (FP32 link kernel): the
+    // ramp and the time factors in FP64 on the host, once per launch
+    static BCTimes bc_times(const lbm_handle *h, double th) {
+        BCTimes T;
+        std::memset(&T, 0, sizeof(T));
+        for (int b = 0; b < h->nbc; ++b) {
+            const BCD &bc = h->bcs[b];
+            double s = 1.0, sd = 0.0;
+            ramp_eval(bc.ramp, bc.t_ramp, th, s, sd);
+            double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, k[3] = {0, 0, 0};
+            if (bc.kind == LBM_BC_DIRICHLET) {  // the lattice sees v_D = d u_D / dt
+                switch (bc.profile) {
+                case LBM_PROFILE_AFFINE:
+                    for (int i = 0; i < 9; ++i) M[i] = sd * bc.A[i];
+                    break;
+                case LBM_PROFILE_RADIAL:
+                    for (int i = 0; i < D; ++i) M[4 * i] = bc.amp * sd;
+                    break;
+                case LBM_PROFILE_TWIST_STRETCH: {
+                    const double al = s * bc.amp, ald = sd * bc.amp;
+                    M[0] = -ald * std::sin(al);
+                    M[1] = -ald * std::cos(al);
+                    M[3] = ald * std::cos(al);
+                    M[4] = -ald * std::sin(al);
+                    if (D == 3) k[2] = sd * bc.vec[2];
+                    break;
+                }
+                case LBM_PROFILE_CONST:
+                    for (int i = 0; i < D; ++i) k[i] = sd * bc.vec[i];
+                    break;
+                default:
+                    break;
+                }
+            } else {  // nominal traction
+                if (bc.profile == LBM_PROFILE_RADIAL)
+                    for (int i = 0; i < D; ++i) M[4 * i] = bc.amp * s;
+                else if (bc.profile == LBM_PROFILE_CONST)
+                    for (int i = 0; i < D; ++i) k[i] = s * bc.vec[i];
+            }
+            BCTimeF &o = T.bc[b];
+            for (int i = 0; i < 9; ++i) o.M[i] = (float)M[i];
+            for (int i = 0; i < 3; ++i) o.k[i] = (float)k[i];
+            o.kind = bc.kind;
+        }
+        return T;
     }
 
     static int cutlinks(lbm_handle *h, double t) {
@@ -496,7 +561,10 @@ template <typename real, int D, typename pop = real> struct Impl {
         EventPair ep;
         if (h->timing) timing_begin(h, ep, 1);
         const int lb = h->tune_lblock ? h->tune_lblock : 128;
-        k_cutlinks<real, D, pop><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a);
+        if constexpr (sizeof(real) == 4)
+            k_links_f32<D, pop><<<grid_for(h->n_cut * kLinkLanes<D>, lb), lb, 0, h->stream>>>(a, bc_times(h, t + 0.5 * a.dt));
+        else
+            k_cutlinks<real, D><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a);
         if (h->timing) timing_end(h, ep);
         h->launches++;
         CKL();
@@ -543,6 +611,7 @@ template <typename real, int D, typename pop = real> struct Impl {
     }
 
     static int step(lbm_handle *h, int nsteps) {
+        NvtxRange range("lbm_step");
         const double dt = h->grid.dx / h->opt.c;
         for (int n = 0; n < nsteps; ++n) {
             const double t = h->step * dt;
@@ -563,6 +632,7 @@ template <typename real, int D, typename pop = real> struct Impl {
                 h->launches++;
                 CKL();
             } else {
+                NvtxRange prange("projection step");
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 2);
                 if (h->phase == 0) k_gather_moments<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
@@ -637,6 +707,7 @@ template <typename real, int D, typename pop = real> struct Impl {
 
     // reverse of step n = h->adj_next, given F of that step as lbm_step_moments recorded it
     static int adjoint_step(lbm_handle *h, const void *moments) {
+        NvtxRange range("lbm_adjoint_step");
         const long long n = h->adj_next;
         StepArgs<real> a = step_args(h);
         AdjArgs<real> j = adj_args(h, h->adj_cur);
@@ -656,11 +727,24 @@ template <typename real, int D, typename pop = real> struct Impl {
         return LBM_OK;
     }
 
-    static int fields(lbm_handle *h, double *v, double *F, double *u) {
+    static int fields(lbm_handle *h, const FieldOut &o) {
         StepArgs<real> a = step_args(h);
         const unsigned g = grid_for(h->nseg, 4);
-        if (h->phase == 0) k_fields<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a, v, F, u);
-        else k_fields<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a, v, F, u);
+        if (h->phase == 0) k_fields<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a, o);
+        else k_fields<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a, o);
+        CKL();
+        return LBM_OK;
+    }
+
+    // whole-body diagnostics: partial records over a fixed grid of kReduceBlocks blocks into h->diag,
+    // the combined record into h->diag + kReduceBlocks * kDiagRec
+    static int diagnostics(lbm_handle *h) {
+        NvtxRange range("lbm_diagnostics");
+        StepArgs<real> a = step_args(h);
+        const unsigned gr = (unsigned)std::max<long long>(1, std::min<long long>(grid_for(h->nseg, 4), kReduceBlocks));
+        if (h->phase == 0) k_diag<real, D, 0, pop><<<gr, 128, 0, h->stream>>>(a, h->diag);
+        else k_diag<real, D, 1, pop><<<gr, 128, 0, h->stream>>>(a, h->diag);
+        k_diag_final<<<1, 256, 0, h->stream>>>(h->diag, (int)gr, h->diag + (size_t)kReduceBlocks * kDiagRec);
         CKL();
         return LBM_OK;
     }

@@ -179,6 +179,23 @@ __device__ __forceinline__ void set_status(int *st, int bits) {
     if (bits) atomicOr(st, bits);
 }
 
+// Bounds-checked build (-DLBM_CHECK, liblbm_b300_check.so): a data-dependent index outside its array
+// latches kStBounds in the status word and is replaced by 0, so the access stays inside the array.
+// Compiled out of the normal build.
+#ifdef LBM_CHECK
+#define TLV_BOUND(idx, n, st)                                                        \
+    do {                                                                             \
+        if ((unsigned long long)(long long)(idx) >= (unsigned long long)(n)) {       \
+            set_status((st), kStBounds);                                             \
+            (idx) = 0;                                                               \
+        }                                                                            \
+    } while (0)
+#else
+#define TLV_BOUND(idx, n, st) \
+    do {                      \
+    } while (0)
+#endif
+
 // =============================================================================================
 // geometry pass (FP64)
 // =============================================================================================
@@ -326,9 +343,11 @@ template <typename real> struct LinkGeom {
     real *h;            // [3*ncut] Newton state (normal image)
     int *ns;            // [ncut]
     int *sidx;          // [kLsqCap*ncut], entry j of link l at j*ncut + l
-    real *w;            // [2*kLsqCap*ncut], tangent a, entry j at (a*kLsqCap + j)*ncut + l
+    real *w;            // [2*kLsqCap*ncut]; FP64: tangent a, entry j at (a*kLsqCap + j)*ncut + l;
+                        // FP32: at (l*kLsqCap + j)*(D-1) + a, and sidx at l*kLsqCap + j
     real *rec;          // [ncut*K] reconstructed incoming populations for the next gather (link-major)
     real *fo;           // [ncut*2K] f*_c(m) then f*_{c^1}(m) of the link's node after the last collision
+    float4 *bvec;       // [ncut] FP32 forms: the link's geometric vector for its boundary profile
     long long ncut;
 };
 
@@ -456,7 +475,12 @@ __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint
             L.Nb[3 * l + a] = N[a];
             L.tan[6 * l + a] = t[0][a];
             L.tan[6 * l + 3 + a] = t[1][a];
-            L.h[3 * l + a] = (real)N[a];
+            L.h[3 * l + a] = sizeof(real) == 4 ? real(0) : (real)N[a];  // FP32 forms keep h - N
+        }
+        if constexpr (sizeof(real) == 4) {
+            double gv[3];
+            link_gvec(bcs[bci], D, Xb, gv);
+            L.bvec[l] = make_float4((float)gv[0], (float)gv[1], (float)gv[2], 0.0f);
         }
         int ns = 0;
         if (kind == 0) {
@@ -522,11 +546,16 @@ __global__ void k_link_build(Box b, const int2 *__restrict__ seg, int nseg, uint
                     if (ns < kLsqCap) {
                         double ph[10];
                         int nb = lsq_basis(D, linear, xi, ph);
-                        L.sidx[(long long)ns * L.ncut + l] = k;
+                        // FP64 tables entry-major (entry j of all links contiguous: one thread per link);
+                        // FP32 tables link-major (a link's entries contiguous: one lane group per link)
+                        if constexpr (sizeof(real) == 4) L.sidx[(long long)l * kLsqCap + ns] = k;
+                        else L.sidx[(long long)ns * L.ncut + l] = k;
                         for (int al = 0; al < D - 1; ++al) {
                             double sacc = 0.0;
                             for (int r = 0; r < nb; ++r) sacc += ph[r] * zs[al][r];
-                            L.w[((long long)al * kLsqCap + ns) * L.ncut + l] = (real)(exp(-r2) * sacc / b.dx);
+                            const real wv = (real)(exp(-r2) * sacc / b.dx);
+                            if constexpr (sizeof(real) == 4) L.w[((long long)l * kLsqCap + ns) * (D - 1) + al] = wv;
+                            else L.w[((long long)al * kLsqCap + ns) * L.ncut + l] = wv;
                         }
                         unsigned *word = reinterpret_cast<unsigned *>(flags + (k & ~3));
                         atomicOr(word, (unsigned)kNeedU << (8 * (k & 3)));
@@ -666,6 +695,8 @@ template <typename real> struct StepArgs {
     const real *mu_field;  // per-node shear modulus replacing mu, or null
     real *mom_out;         // the step's recovered F (or F - I when shifted): D*D planes, or null
     int *status;
+    int spin;              // polls of a bulk-copy kernel's first wait for its copies
+    long long ncut;        // cut links (bounds of the per-link arrays)
 };
 
 // material of a node: its group's (mu, lambda) for multi-specimen bodies, else the global one;
@@ -734,9 +765,20 @@ __device__ __forceinline__ long long link_of(long long l0, unsigned cut, int c) 
 // After computing the post-collision values out[0..K) of direction q at a node with cut bits `cut`,
 // keep the ones its cut links need: f*_c(m) for a cut direction c = q, f*_{c^1}(m) for c = q^1.
 template <typename real, int K>
-__device__ __forceinline__ void keep_link_values(real *lfo, long long l0, unsigned cut, int q, const real *out) {
-    if ((cut >> q) & 1) vstore<K>(lfo + link_of(l0, cut, q) * (2 * K), out);
-    if ((cut >> (q ^ 1)) & 1) vstore<K>(lfo + link_of(l0, cut, q ^ 1) * (2 * K) + K, out);
+__device__ __forceinline__ void keep_link_values(real *lfo, long long l0, unsigned cut, int q, const real *out,
+                                                 long long ncut, int *status) {
+    if ((cut >> q) & 1) {
+        long long l = link_of(l0, cut, q);
+        TLV_BOUND(l, ncut, status);
+        vstore<K>(lfo + l * (2 * K), out);
+    }
+    if ((cut >> (q ^ 1)) & 1) {
+        long long l = link_of(l0, cut, q ^ 1);
+        TLV_BOUND(l, ncut, status);
+        vstore<K>(lfo + l * (2 * K) + K, out);
+    }
+    (void)ncut;
+    (void)status;
 }
 
 // MODE 0: state is pre-collision f^0 (first step, no streaming); MODE 1: state is f*^{n-1}
@@ -756,7 +798,8 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
     #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!((cut >> (q ^ 1)) & 1)) {  // source m - e_q = m + e_{q^1} is active
-            const int src = nbr(a.b, node, x, y, z, q ^ 1);
+            int src = nbr(a.b, node, x, y, z, q ^ 1);
+            TLV_BOUND(src, a.b.npad, a.status);
             #pragma unroll
             for (int k = 0; k < K; ++k) f[q * K + k] = pop_ld<real, pop>(fs, (long long)(q * K + k) * P + src);
         }
@@ -766,7 +809,11 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
         const long long l0 = __ldg(a.lstart + node);
         #pragma unroll
         for (int q = 0; q < Q; ++q)
-            if ((cut >> (q ^ 1)) & 1) vload<K>(a.lrec + link_of(l0, cut, q ^ 1) * K, &f[q * K]);
+            if ((cut >> (q ^ 1)) & 1) {
+                long long l = link_of(l0, cut, q ^ 1);
+                TLV_BOUND(l, a.ncut, a.status);
+                vload<K>(a.lrec + l * K, &f[q * K]);
+            }
     }
     }
 }
@@ -849,7 +896,7 @@ __device__ __forceinline__ void collide_store(const StepArgs<real> &a, int node,
             }
         #pragma unroll
         for (int k = 0; k < K; ++k) pop_st<real, pop>(a.fdst, (long long)(q * K + k) * P + node, out[k]);
-        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
+        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out, a.ncut, a.status);
     }
 }
 
@@ -892,7 +939,13 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs<real> a) 
     if (a.mom_out)
         #pragma unroll
         for (int k = 0; k < D * D; ++k) a.mom_out[(long long)k * a.b.npad + node] = kShifted<real> ? G[k] : F[k];
-    const real J = piola<real, D>(F, mu, lam, Pk);
+    real J;
+    if constexpr (kShifted<real>) {
+        real Fit[D * D];
+        J = piola_g<real, D>(G, mu, lam, Pk, Fit);  // FP32: from G = F - I, no cancellation near F = I
+    } else {
+        J = piola<real, D>(F, mu, lam, Pk);
+    }
     const int st = check_state<real, D>(v, F, J);
     if (st) set_status(a.status, st);
     const long long P = a.b.npad;
@@ -956,9 +1009,23 @@ __global__ void __launch_bounds__(128) k_gather_moments(const StepArgs<real> a) 
     for (int k = 0; k < D * D; ++k) a.Gst[k * P + node] = G[k];
 }
 
-// field output: v, F, u at the current time (FP64, box planes)
+// Output of a field call: any pointer may be null.  layout 0: component c of node n at c*nbox + n;
+// 1: at n*ncomp + c.
+struct FieldOut {
+    double *v, *F, *u, *sigma, *J;
+    int layout;
+};
+
+__device__ __forceinline__ void field_put(double *p, int layout, long long nbox, long long node, int ncomp, int c,
+                                          double val) {
+    if (layout) p[node * ncomp + c] = val;
+    else p[c * nbox + node] = val;
+}
+
+// field output: v, F, u at the current time, and the Cauchy stress sigma = J^-1 P F^T
+// (Eq. cauchy-recovery-general) and J = det F in FP64 from the recovered F
 template <typename real, int D, int MODE, typename pop = real>
-__global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *vout, double *Fout, double *uout) {
+__global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, const FieldOut o) {
     constexpr int K = D + D * D, Q = 2 * D;
     const int sgi = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (sgi >= a.nseg) return;
@@ -976,14 +1043,197 @@ __global__ void __launch_bounds__(128) k_fields(const StepArgs<real> a, double *
     recover<real, D>(a, f, v, G, F);
     const long long N = a.b.nbox, P = a.b.npad;
     for (int i = 0; i < D; ++i) {
-        if (vout) vout[i * N + node] = (double)v[i];
-        if (uout) uout[i * N + node] = disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i];
+        if (o.v) field_put(o.v, o.layout, N, node, D, i, (double)v[i]);
+        if (o.u) field_put(o.u, o.layout, N, node, D, i, disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * (double)v[i]);
     }
-    if (Fout)
-        for (int i = 0; i < D; ++i)
-            for (int B = 0; B < D; ++B)
-                Fout[(i * D + B) * N + node] =
-                    kShifted<real> ? (double)G[i * D + B] + (i == B ? 1.0 : 0.0) : (double)F[i * D + B];
+    double Fd[D * D];
+    for (int i = 0; i < D; ++i)
+        for (int B = 0; B < D; ++B)
+            Fd[i * D + B] = kShifted<real> ? (double)G[i * D + B] + (i == B ? 1.0 : 0.0) : (double)F[i * D + B];
+    if (o.F)
+        for (int k = 0; k < D * D; ++k) field_put(o.F, o.layout, N, node, D * D, k, Fd[k]);
+    if (o.sigma || o.J) {
+        real mu, lam;
+        node_material(a, node, mu, lam);
+        double Pd[D * D];
+        const double J = piola<double, D>(Fd, (double)mu, (double)lam, Pd);
+        if (o.J) field_put(o.J, o.layout, N, node, 1, 0, J);
+        if (o.sigma)
+            for (int i = 0; i < D; ++i)
+                for (int B = 0; B < D; ++B) {
+                    double sacc = 0.0;
+                    for (int A = 0; A < D; ++A) sacc += Pd[i * D + A] * Fd[B * D + A];
+                    field_put(o.sigma, o.layout, N, node, D * D, i * D + B, sacc / J);
+                }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// whole-body diagnostics: per-block partial records over a fixed grid, then one final block
+// ---------------------------------------------------------------------------------------------
+
+// partial record: sum |v|^2, max |v|^2, min J, max J, max c_T^2, sum of squared edge residuals, edges
+constexpr int kDiagRec = 8;
+
+__device__ __forceinline__ void diag_warp_reduce(double r[kDiagRec]) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r[0] += __shfl_down_sync(0xffffffffu, r[0], o);
+        r[1] = fmax(r[1], __shfl_down_sync(0xffffffffu, r[1], o));
+        r[2] = fmin(r[2], __shfl_down_sync(0xffffffffu, r[2], o));
+        r[3] = fmax(r[3], __shfl_down_sync(0xffffffffu, r[3], o));
+        r[4] = fmax(r[4], __shfl_down_sync(0xffffffffu, r[4], o));
+        r[5] += __shfl_down_sync(0xffffffffu, r[5], o);
+        r[6] += __shfl_down_sync(0xffffffffu, r[6], o);
+    }
+}
+
+__device__ __forceinline__ void diag_init(double r[kDiagRec]) {
+    r[0] = 0.0; r[1] = 0.0; r[2] = INFINITY; r[3] = -INFINITY; r[4] = 0.0; r[5] = 0.0; r[6] = 0.0; r[7] = 0.0;
+}
+
+// the state of node `node` as the diagnostics use it: v, G = F - I (FP64 from the form's values), u
+template <typename real, int D, int MODE, typename pop>
+__device__ __forceinline__ void diag_state(const StepArgs<real> &a, int node, double v[D], double G[D * D],
+                                           double u[D]) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    int x, y, z;
+    node_xyz(a.b, node, x, y, z);
+    const uint8_t fl = __ldg(a.flags + node);
+    real f[Q * K];
+    gather<real, D, MODE, pop>(a, node, x, y, z, fl & kCutMask, f);
+    real vr[D], Gr[D * D], Fr[D * D];
+    recover<real, D>(a, f, vr, Gr, Fr);
+    const long long P = a.b.npad;
+    for (int i = 0; i < D; ++i) {
+        v[i] = (double)vr[i];
+        u[i] = disp_get<real>(a.ustar, P, D, i, node) + 0.5 * (double)a.dt * v[i];
+    }
+    for (int k = 0; k < D * D; ++k)
+        G[k] = kShifted<real> ? (double)Gr[k] : (double)Fr[k] - ((k / D == k % D) ? 1.0 : 0.0);
+}
+
+// one thread per active node, segments strided over a fixed grid; the node's state and, for the
+// compatibility residual, the states of its active forward axis neighbours (interior links)
+template <typename real, int D, int MODE, typename pop = real>
+__global__ void __launch_bounds__(128) k_diag(const StepArgs<real> a, double *partial) {
+    __shared__ double sm[4][kDiagRec];
+    double r[kDiagRec];
+    diag_init(r);
+    const int lane = threadIdx.x & 31;
+    for (int sgi = blockIdx.x * 4 + (threadIdx.x >> 5); sgi < a.nseg; sgi += gridDim.x * 4) {
+        const int2 sg = __ldg(&a.seg[sgi]);
+        const int x = sg.x - sg.y * a.b.nx + lane;
+        const int node = sg.x + lane;
+        if (x >= a.b.nx || !(__ldg(a.flags + node) & kActive)) continue;
+        const unsigned cut = __ldg(a.flags + node) & kCutMask;
+        double v[D], G[D * D], u[D];
+        diag_state<real, D, MODE, pop>(a, node, v, G, u);
+        double F[D * D];
+        for (int k = 0; k < D * D; ++k) F[k] = G[k] + ((k / D == k % D) ? 1.0 : 0.0);
+        real mu, lam;
+        node_material(a, node, mu, lam);
+        double v2 = 0.0;
+        for (int i = 0; i < D; ++i) v2 += v[i] * v[i];
+        const double J = 1.0 + det_m1<double, D>(G);
+        r[0] += v2;
+        r[1] = fmax(r[1], v2);
+        r[2] = fmin(r[2], J);
+        r[3] = fmax(r[3], J);
+        r[4] = fmax(r[4], tangent_speed2<D>(F, (double)mu, (double)lam));
+        int y, z, xx;
+        node_xyz(a.b, node, xx, y, z);
+        for (int A = 0; A < D; ++A) {
+            if ((cut >> (2 * A)) & 1) continue;  // +e_A neighbour inactive or outside the box
+            const int l = nbr(a.b, node, xx, y, z, 2 * A);
+            double vl[D], Gl[D * D], ul[D];
+            diag_state<real, D, MODE, pop>(a, l, vl, Gl, ul);
+            for (int i = 0; i < D; ++i) {
+                // u_m - u_l - (G_m + G_l)(X_m - X_l)/2 with X_m - X_l = -dx e_A
+                const double e = (u[i] - ul[i]) + 0.5 * (G[i * D + A] + Gl[i * D + A]) * a.b.dx;
+                r[5] += e * e;
+            }
+            r[6] += 1.0;
+        }
+    }
+    diag_warp_reduce(r);
+    if (lane == 0)
+        for (int k = 0; k < kDiagRec; ++k) sm[threadIdx.x >> 5][k] = r[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 4; ++w) {
+            sm[0][0] += sm[w][0];
+            sm[0][1] = fmax(sm[0][1], sm[w][1]);
+            sm[0][2] = fmin(sm[0][2], sm[w][2]);
+            sm[0][3] = fmax(sm[0][3], sm[w][3]);
+            sm[0][4] = fmax(sm[0][4], sm[w][4]);
+            sm[0][5] += sm[w][5];
+            sm[0][6] += sm[w][6];
+        }
+        for (int k = 0; k < kDiagRec; ++k) partial[blockIdx.x * kDiagRec + k] = sm[0][k];
+    }
+}
+
+// one block of 256: combines n partial diagnostic records in a fixed order into out[0..kDiagRec)
+static __global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partial, int n, double *out) {
+    __shared__ double sm[8][kDiagRec];
+    double r[kDiagRec];
+    diag_init(r);
+    for (int j = threadIdx.x; j < n; j += 256) {
+        const double *p = partial + (long long)j * kDiagRec;
+        r[0] += p[0];
+        r[1] = fmax(r[1], p[1]);
+        r[2] = fmin(r[2], p[2]);
+        r[3] = fmax(r[3], p[3]);
+        r[4] = fmax(r[4], p[4]);
+        r[5] += p[5];
+        r[6] += p[6];
+    }
+    diag_warp_reduce(r);
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < kDiagRec; ++k) sm[threadIdx.x >> 5][k] = r[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            sm[0][0] += sm[w][0];
+            sm[0][1] = fmax(sm[0][1], sm[w][1]);
+            sm[0][2] = fmin(sm[0][2], sm[w][2]);
+            sm[0][3] = fmax(sm[0][3], sm[w][3]);
+            sm[0][4] = fmax(sm[0][4], sm[w][4]);
+            sm[0][5] += sm[w][5];
+            sm[0][6] += sm[w][6];
+        }
+        for (int k = 0; k < kDiagRec; ++k) out[k] = sm[0][k];
+    }
+}
+
+// squared largest tangent wave speed of the initial F0 (FP64 box planes) over the active nodes, per
+// block of a fixed grid (partial[block]), for the wave-speed audit
+template <int D, typename MT>
+__global__ void __launch_bounds__(128) k_audit_f0(Box b, const int2 *__restrict__ seg, int nseg,
+                                                  const uint8_t *__restrict__ flags, const double *__restrict__ F0,
+                                                  double mu_, double lam_, const uint8_t *__restrict__ mat,
+                                                  const double *__restrict__ mtab, const MT *__restrict__ mu_node,
+                                                  double *partial) {
+    __shared__ double sm[4];
+    double c2 = 0.0;
+    const int lane = threadIdx.x & 31;
+    for (int sgi = blockIdx.x * 4 + (threadIdx.x >> 5); sgi < nseg; sgi += gridDim.x * 4) {
+        const int2 sg = __ldg(&seg[sgi]);
+        const int x = sg.x - sg.y * b.nx + lane;
+        const int node = sg.x + lane;
+        if (x >= b.nx || !(__ldg(flags + node) & kActive)) continue;
+        double F[D * D];
+        for (int k = 0; k < D * D; ++k) F[k] = F0[k * b.nbox + node];
+        const double mu = mu_node ? (double)mu_node[node] : (mtab ? mtab[2 * mat[node]] : mu_);
+        const double lam = mtab ? mtab[2 * mat[node] + 1] : lam_;
+        c2 = fmax(c2, tangent_speed2<D>(F, mu, lam));
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c2 = fmax(c2, __shfl_down_sync(0xffffffffu, c2, o));
+    if (lane == 0) sm[threadIdx.x >> 5] = c2;
+    __syncthreads();
+    if (threadIdx.x == 0) partial[blockIdx.x] = fmax(fmax(sm[0], sm[1]), fmax(sm[2], sm[3]));
 }
 
 // =============================================================================================
@@ -1032,8 +1282,12 @@ __device__ __forceinline__ bool traction_residual(const real h[D], const real N[
     return true;
 }
 
-template <typename real, int D, typename pop = real>
+// FP64 form: one thread per cut link, the oracle's arithmetic and iteration (the FP32 forms use
+// k_links_f32).
+template <typename real, int D>
 __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
+    static_assert(sizeof(real) == 8, "FP64 form only");
+    using pop = real;
     constexpr int K = D + D * D;
     const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (l >= a.L.ncut) return;
@@ -1052,7 +1306,8 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
     if (up && !(eta_r >= real(0.5))) {
         int x, y, z;
         node_xyz(a.b, mnode, x, y, z);
-        const int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
+        int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
+        TLV_BOUND(mup, a.b.npad, a.status);
         #pragma unroll
         for (int k = 0; k < K; ++k) fu[k] = pop_ld<real, pop>(a.fstar, (long long)(q * K + k) * a.b.npad + mup);
     } else {
@@ -1085,18 +1340,12 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
             #pragma unroll
             for (int i = 0; i < D; ++i) { t[al][i] = (real)a.L.tan[6 * l + 3 * al + i]; g[al][i] = real(0); }
         // tangent images g_a = t_a + sum_j w_aj (u_j - u_m)  (Eqs. tangent-derivative-2d, tangent-image-3d-lsq)
-        const int m = a.L.node[l];
-        const long long P = a.npad;
-        real um[D], uml[D];
-        un_load<real, D>(a.un, m, um, uml);
         const int ns = a.L.ns[l];
-        if constexpr (!kShifted<real>) {
-            // FP64: g = t + sum_j w_j u_j in stencil order, as the oracle sums it
+        // g = t + sum_j w_j u_j in stencil order, as the oracle sums it
+        #pragma unroll
+        for (int al = 0; al < D - 1; ++al)
             #pragma unroll
-            for (int al = 0; al < D - 1; ++al)
-                #pragma unroll
-                for (int i = 0; i < D; ++i) g[al][i] = t[al][i];
-        }
+            for (int i = 0; i < D; ++i) g[al][i] = t[al][i];
         // stencil entries in groups of 4: all index loads, then all displacement loads, then the sums,
         // so each thread keeps several independent loads in flight
         constexpr int U = 4;
@@ -1107,6 +1356,7 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
             for (int jj = 0; jj < U; ++jj) {
                 const int j = j0 + jj < ns ? j0 + jj : ns - 1;
                 kk[jj] = __ldg(a.L.sidx + (long long)j * a.L.ncut + l);
+                TLV_BOUND(kk[jj], a.npad, a.status);
                 #pragma unroll
                 for (int al = 0; al < D - 1; ++al) w[jj][al] = __ldg(a.L.w + ((long long)al * kLsqCap + j) * a.L.ncut + l);
             }
@@ -1117,19 +1367,11 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
                 if (j0 + jj >= ns) break;
                 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    // FP32: sum w_j (u_j - u_m), equal since sum_j w_j = 0, with less cancellation; the
-                    // difference of the (hi, lo) pairs, hi parts first (exact for nearby values)
-                    const real du = kShifted<real> ? (uu[jj][i] - um[i]) + (uul[jj][i] - uml[i]) : uu[jj][i];
+                    const real du = uu[jj][i];
                     #pragma unroll
                     for (int al = 0; al < D - 1; ++al) g[al][i] += w[jj][al] * du;
                 }
             }
-        }
-        if constexpr (kShifted<real>) {
-            #pragma unroll
-            for (int al = 0; al < D - 1; ++al)
-                #pragma unroll
-                for (int i = 0; i < D; ++i) g[al][i] += t[al][i];
         }
         double Td[3];
         traction_eval(bc, D, Xb, th, Td);
@@ -1137,11 +1379,11 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
         real tinf = 0;
         #pragma unroll
         for (int i = 0; i < D; ++i) { T[i] = (real)Td[i]; tinf = fmax(tinf, fabs(T[i])); }
-        // Newton for the normal image h (Eqs. Fb-decomp-2d/3d, neumann-newton-2d/3d), central FD Jacobian,
-        // halving line search that rejects det F_b <= 0
-        constexpr bool dbl = sizeof(real) == 8;
-        const real tol = (dbl ? real(1e-13) : real(2e-6)) * (mu + lam + tinf);
-        const real fd = dbl ? real(1e-6) : real(1e-3);
+        // Newton for the normal image h (Eqs. Fb-decomp-2d/3d, neumann-newton-2d/3d): central
+        // finite-difference Jacobian, halving line search that rejects det F_b <= 0, stop at
+        // |R| <= 1e-13 (mu + lambda + |T|)
+        const real tol = real(1e-13) * (mu + lam + tinf);
+        const real fd = real(1e-6);
         real h[D], R[D];
         #pragma unroll
         for (int i = 0; i < D; ++i) h[i] = a.L.h[3 * l + i];
@@ -1195,7 +1437,7 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
                 }
                 al *= real(0.5);
             }
-            if (!acc) { conv = rinf <= (dbl ? real(1e3) : real(10)) * tol; break; }
+            if (!acc) { conv = rinf <= real(1e3) * tol; break; }
             #pragma unroll
             for (int i = 0; i < D; ++i) { h[i] = ht[i]; R[i] = Rt[i]; }
         }
@@ -1223,8 +1465,7 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
             S[i] = s * Pb[i * D + A] / c;  // -d_A P_iA / c with d = -s e_A
             #pragma unroll
             for (int B = 0; B < D; ++B)
-                S[D + i * D + B] = kShifted<real> ? (Fb[i * D + B] - ((i == B) ? real(1) : real(0))) / real(D)
-                                                  : Fb[i * D + B] / real(D);
+                S[D + i * D + B] = Fb[i * D + B] / real(D);
         }
     }
     // Interpolated bounce-back of the incoming population f_{c^1}(m) for the next gather
@@ -1264,6 +1505,7 @@ template <typename real> struct ProjArgs {
     const real *u0;    // warm start (displacement-accumulator layout: FP64 planes or FP32 pairs)
     real *resid;       // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start
     double t, beta;
+    int *status;
 };
 
 // Projection correction d and residual, node-major so that a neighbour is one vector load:
@@ -1368,7 +1610,8 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
     }
     #pragma unroll
     for (int q = 0; q < 2 * D; ++q) {
-        const int ln = ((cut >> q) & 1) ? node : nbr(a.b, node, x, y, z, q);
+        int ln = ((cut >> q) & 1) ? node : nbr(a.b, node, x, y, z, q);
+        TLV_BOUND(ln, P, a.status);
         #pragma unroll
         for (int i = 0; i < D; ++i) {
             #pragma unroll
@@ -1576,8 +1819,10 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     #pragma unroll
     for (int A = 0; A < D; ++A) {
         const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
-        const int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
-        const int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
+        int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
+        int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
+        TLV_BOUND(lp, P, a.status);
+        TLV_BOUND(lm, P, a.status);
         #pragma unroll
         for (int i = 0; i < D; ++i) {
             real Gc;
@@ -1618,8 +1863,15 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         }
     real mu, lam;
     node_material(a, node, mu, lam);
-    piola<real, D>(F, mu, lam, Pold);
-    const real J = piola<real, D>(Fr, mu, lam, Pk);
+    real J;
+    if constexpr (kShifted<real>) {
+        real Fit[D * D];
+        piola_g<real, D>(G, mu, lam, Pold, Fit);
+        J = piola_g<real, D>(Gr, mu, lam, Pk, Fit);
+    } else {
+        piola<real, D>(F, mu, lam, Pold);
+        J = piola<real, D>(Fr, mu, lam, Pk);
+    }
     const int st = check_state<real, D>(v, Fr, J);
     if (st) set_status(a.status, st);
     const real Dc = real(D) / a.c;
@@ -1661,7 +1913,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         }
         #pragma unroll
         for (int k = 0; k < K; ++k) pop_st<real, pop>(a.fdst, (long long)(q * K + k) * P + node, out[k]);
-        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out);
+        if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out, a.ncut, a.status);
     }
     #pragma unroll
     for (int i = 0; i < D; ++i) {

@@ -8,7 +8,8 @@ struct PrecOps {
     int (*link_build)(lbm_handle *);
     int (*init)(lbm_handle *, int, const double *, const double *, const double *, const double *);
     int (*step)(lbm_handle *, int);
-    int (*fields)(lbm_handle *, double *, double *, double *);
+    int (*fields)(lbm_handle *, const FieldOut &);
+    int (*diagnostics)(lbm_handle *);
     int (*adjoint_begin)(lbm_handle *, const double *);
     int (*adjoint_step)(lbm_handle *, const void *);
 };

@@ -1,19 +1,24 @@
 // Geometry census without any device allocation (lbm_census_static in include/lbm.h).
 //
 // Some callers cannot allocate device memory at the point where they need to size a
-// simulation: code that runs while a CUDA graph is being captured, or an embedding runtime
-// whose device memory belongs to its own pool and may not be grown from a library call.
+// simulation: an embedding runtime (a serving process, a solver framework) whose device memory
+// is one arena planned ahead and handed out by its own allocator, so that a library call must
+// not take memory behind its back; or a process already running at its memory limit, which has
+// to learn how much storage a body needs before it can free or plan that much.
 // lbm_census_static gives them the counts that size lbm_create's and lbm_bind_storage's
 // storage (active nodes, cut links, active 32-node x-segments) with all of its scratch in one
 // file-scope device array of fixed size: the active mask of the box (one byte per node) and
-// three counters.  Every GPU that loads this library holds the array until the process exits.
+// four counters.  Every GPU that loads this library holds the array until the process exits.
+// It applies lbm_create's domain rules: no active node, or a body that extends past a
+// non-periodic box face, is LBM_ERR_DOMAIN.
 //
 // Host code never dereferences the array's name (on the host it is only a stand-in): the first
 // call on a device, with that device current, asks the runtime for the array's device address
 // with cudaGetSymbolAddress and keeps it for that device.  That first call therefore makes a
 // runtime query and should come before any stream capture.  All calls on a device share the
 // array: calls that overlap on the GPU race with each other.  Each call clears the counters and
-// rewrites the mask before using them.
+// rewrites the mask before using them.  The call synchronises the stream it is given before it
+// returns the counts.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,7 +33,7 @@ namespace {
 
 constexpr long long kCensusMaxNodes = LBM_CENSUS_MAX_NODES;
 constexpr int kMaxDevices = 64;
-constexpr int kMaskOffset = 256;  // bytes [0, 24): counters (active, cut, segments)
+constexpr int kMaskOffset = 256;  // bytes [0, 32): counters (active, cut, segments, box-face violations)
 
 __device__ __align__(256) unsigned char g_census_scratch[kMaskOffset + kCensusMaxNodes];
 
@@ -50,12 +55,15 @@ __global__ void k_census_mask(Box b, const __grid_constant__ ShapeTable shapes, 
 }
 
 // counting variant of the cut-bit pass: the same link rule (neighbour inactive or outside a
-// non-periodic box), summed with warp shuffles and one atomic per warp instead of scanned
-__global__ void k_census_count(Box b, unsigned char *scratch) {
+// non-periodic box), summed with warp shuffles and one atomic per warp instead of scanned.  A link
+// that leaves the box must cross the surface within one spacing (the point one spacing beyond the
+// face lies outside the body), the rule lbm_create applies; links that break it are counted in
+// cnt[3] and make the call return LBM_ERR_DOMAIN.
+__global__ void k_census_count(Box b, const __grid_constant__ ShapeTable shapes, int nshapes, unsigned char *scratch) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(scratch);
     const unsigned char *mask = scratch + kMaskOffset;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    unsigned long long act = 0, cut = 0;
+    unsigned long long act = 0, cut = 0, bad = 0;
     if (i < b.nbox && mask[i]) {
         int x, y, z;
         node_xyz(b, (int)i, x, y, z);
@@ -64,18 +72,27 @@ __global__ void k_census_count(Box b, unsigned char *scratch) {
             const int A = q >> 1, s = (q & 1) ? -1 : 1;
             const int co = (A == 0 ? x : (A == 1 ? y : z)) + s;
             const int n = (A == 0 ? b.nx : (A == 1 ? b.ny : b.nz));
-            if ((co < 0 || co >= n) && !b.per[A]) cut += 1;
-            else if (!mask[nbr(b, (int)i, x, y, z, q)]) cut += 1;
+            if ((co < 0 || co >= n) && !b.per[A]) {
+                cut += 1;
+                double X[3];
+                node_X(b, x, y, z, X);
+                X[A] += s * b.dx;
+                if (!(levelset(shapes.s, nshapes, b.D, X, nullptr) > 0.0)) bad += 1;
+            } else if (!mask[nbr(b, (int)i, x, y, z, q)]) {
+                cut += 1;
+            }
         }
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         act += __shfl_down_sync(0xffffffffu, act, o);
         cut += __shfl_down_sync(0xffffffffu, cut, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (act) atomicAdd(&cnt[0], act);
         if (cut) atomicAdd(&cnt[1], cut);
+        if (bad) atomicAdd(&cnt[3], bad);
     }
 }
 
@@ -133,7 +150,8 @@ extern "C" int lbm_census_static(const lbm_grid *grid, const lbm_levelset *ls, v
     ShapeTable table{};
     for (int s = 0; s < ls->nshapes; ++s) {
         const lbm_shape &sh = ls->shapes[s];
-        if (sh.kind < 0 || sh.kind > LBM_SHAPE_HALFSPACE) return LBM_ERR_ARG;
+        if (sh.kind < 0 || sh.kind > LBM_SHAPE_SAMPLED || (sh.kind == LBM_SHAPE_SAMPLED && !sh.phi)) return LBM_ERR_ARG;
+        if (sh.kind == LBM_SHAPE_SUPERELLIPSE && (grid->dim != 2 || !(sh.p >= 1.0))) return LBM_ERR_ARG;
         ShapeD &d = table.s[s];
         d.kind = sh.kind;
         d.complement = sh.complement != 0;
@@ -144,23 +162,32 @@ extern "C" int lbm_census_static(const lbm_grid *grid, const lbm_levelset *ls, v
         }
         for (int a = 0; a < 9; ++a) d.Q[a] = sh.rot[a];
         d.p = sh.p;
+        d.phi = sh.kind == LBM_SHAPE_SAMPLED ? sh.phi : nullptr;
+        d.per = 0;
+        for (int a = 0; a < 3; ++a) {
+            d.n[a] = a < grid->dim ? grid->n[a] : 1;
+            d.org[a] = a < grid->dim ? grid->origin[a] : 0.0;
+            if (a < grid->dim && grid->periodic[a]) d.per |= 1 << a;
+        }
+        d.dx = grid->dx;
     }
     unsigned char *scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaMemsetAsync(scratch, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemsetAsync(scratch, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) return LBM_ERR_CUDA;
     const unsigned grid_n = (unsigned)((b.nbox + 255) / 256);
     k_census_mask<<<grid_n, 256, 0, st>>>(b, table, ls->nshapes, scratch);
-    k_census_count<<<grid_n, 256, 0, st>>>(b, scratch);
+    k_census_count<<<grid_n, 256, 0, st>>>(b, table, ls->nshapes, scratch);
     k_census_rows<<<(unsigned)(((long long)b.ny * b.nz + 127) / 128), 128, 0, st>>>(b, scratch);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
-    unsigned long long host[3] = {0, 0, 0};
+    unsigned long long host[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(host, scratch, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return LBM_ERR_CUDA;
     *n_active = (long long)host[0];
     *n_cut = (long long)host[1];
     *n_segments = (long long)host[2];
+    if (host[0] == 0 || host[3] != 0) return LBM_ERR_DOMAIN;
     return LBM_OK;
 }

@@ -80,8 +80,10 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < kTmaSpin; ++it)
+// at most `limit` polls (the first wait of a window takes StepArgs::spin, kTmaSpin unless a test
+// shortens it; the drain after a timeout always takes kTmaSpin)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit = kTmaSpin) {
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -90,7 +92,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // (status latched) if the wait ran out.  Every lane of the warp must call it.
 template <int D, typename pop = float>
 __device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorMap *wide, const CUtensorMap *narrow,
-                                                   char *wsm, uint64_t *bar, int2 sg, int lane, int *status) {
+                                                   char *wsm, uint64_t *bar, int2 sg, int lane, int *status, int spin) {
     using L = TmaLayout<D, sizeof(pop)>;
     constexpr int K = L::K, Q = L::Q;
     if (lane == 0) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool tma_gather_segment(const Box &b, const CUtensorM
             tma_load_2d(wsm + L::slot(q), A == 0 ? wide : narrow, bar, start, q * K);
         }
     }
-    bool ok = mbar_wait_bounded(bar, 0);
+    bool ok = mbar_wait_bounded(bar, 0, spin);
     if (!ok) {
         if (lane == 0) set_status(status, kStTimeout);
         mbar_wait_bounded(bar, 0);  // let the copies in flight land before the block can exit
@@ -162,7 +164,9 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
     for (int q = 0; q < Q; ++q) {
         if ((cut >> (q ^ 1)) & 1) {
             float r[K];
-            vload<K>(a.lrec + link_of(l0, cut, q ^ 1) * K, r);
+            long long l = link_of(l0, cut, q ^ 1);
+            TLV_BOUND(l, a.ncut, a.status);
+            vload<K>(a.lrec + l * K, r);
             #pragma unroll
             for (int k = 0; k < K; ++k) stage_put<D, pop>(wsm, q, k, lane, r[k]);
         }
@@ -193,19 +197,14 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     }
     const float hdt = 0.5f * a.dt;
     const float inv_damp = 1.0f / (1.0f + hdt * a.gamma);
-    float v[D], F[D * D], C[D * D], P[D * D];
+    float v[D], P[D * D], Fit[D * D];
     #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = (S[i] + hdt * a.bf[i]) * inv_damp;
-    #pragma unroll
-    for (int k = 0; k < D * D; ++k) F[k] = S[D + k] + ((k / D == k % D) ? 1.0f : 0.0f);
     if (a.mom_out && act)
         #pragma unroll
         for (int k = 0; k < D * D; ++k) a.mom_out[(long long)k * a.b.npad + node] = S[D + k];
-    cofactor<float, D>(F, C);
-    const float J = det<float, D>(F);
-    const float sJ = (0.5f * lam * (J * J - 1.0f) - mu) * (1.0f / J);
-    #pragma unroll
-    for (int k = 0; k < D * D; ++k) P[k] = mu * F[k] + sJ * C[k];
+    // P(F) from G = F - I = S[D..], free of the cancellations near F = I
+    const float J = piola_g<float, D>(S + D, mu, lam, P, Fit);
     float chk = J;
     #pragma unroll
     for (int i = 0; i < D; ++i) chk += v[i];
@@ -260,7 +259,7 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
             o[k] = act ? fmaf(om1, staged<D, pop>(wsm, q, k, lane), t) : 0.0f;
             pop_st<float, pop>(a.fdst, (long long)(q * K + k) * Pn + node, o[k]);
         }
-        if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, o);
+        if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, o, a.ncut, a.status);
     }
 }
 
@@ -383,7 +382,7 @@ __global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<fl
     #pragma unroll
     for (int w = 0; w < NW; ++w) {
         if (w >= nw) break;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + w, 0))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars + w, 0, a.spin))) {
             if (lane == 0) set_status(a.status, kStTimeout);
             for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
             return;
@@ -404,7 +403,7 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     char *wsm = smem + warp * L::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
     const int2 sg = __ldg(&a.seg[sgi]);
-    if (!tma_gather_segment<D, pop>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status)) return;
+    if (!tma_gather_segment<D, pop>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status, a.spin)) return;
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
     const int node = sg.x + lane;

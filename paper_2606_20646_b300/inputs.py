@@ -27,7 +27,7 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-SHAPE_KINDS = ("sphere", "ellipsoid", "superellipse", "cylinder", "halfspace")
+SHAPE_KINDS = ("sphere", "ellipsoid", "superellipse", "cylinder", "halfspace", "sampled")
 BC_KINDS = ("dirichlet", "neumann")
 BC_PROFILES = ("zero", "affine", "radial", "twist_stretch", "const")
 RAMPS = ("one", "linear", "sin2", "cos", "time")
@@ -56,6 +56,8 @@ class Shape:
     superellipse: phi = |xi_1/axes[0]|^p + |xi_2/axes[1]|^p - 1 (2D only)
     cylinder:     phi = |(X_1, X_2) - (c_1, c_2)| - axes[0]     (axis along X_3)
     halfspace:    phi = axes . (X - c)   (axes = unit outward normal)
+    sampled:      phi given at the lattice nodes (``phi``, box-shaped); between nodes the
+                  multilinear interpolant (linear along every link)
     """
     kind: str
     center: Sequence[float] = (0.0, 0.0, 0.0)
@@ -64,9 +66,11 @@ class Shape:
     p: float = 2.0
     complement: bool = False
     boundary_id: int = 0
+    phi: Optional[np.ndarray] = None   # sampled: node values, box-shaped
 
     def __post_init__(self):
         assert self.kind in SHAPE_KINDS, self.kind
+        assert (self.kind == "sampled") == (self.phi is not None), "node samples go with the sampled kind"
         self.center = tuple(float(x) for x in self.center) + (0.0,) * (3 - len(self.center))
         self.axes = tuple(float(x) for x in self.axes) + (1.0,) * (3 - len(self.axes))
         self.rot = np.asarray(self.rot, dtype=np.float64).reshape(3, 3)
@@ -134,6 +138,7 @@ class Options:
     proj_iters: int = 50       # damped-Jacobi sweeps per projection solve
     proj_beta: float = 2.0 / 3.0  # Jacobi damping
     body_force: Sequence[float] = (0.0, 0.0, 0.0)
+    c_audit: float = 0.0       # wave-speed audit factor: c >= c_audit * largest tangent speed (0: 2.5, < 0: off)
 
 
 @dataclass
@@ -394,6 +399,21 @@ def sphere_shell_paper_3d(N: int, t_end: float = 5.0) -> Problem:
     return p
 
 
+def sampled_copy(p: Problem) -> Problem:
+    """The same body with each sphere/circle primitive replaced by its node samples: the signed
+    distance |X - c| - R (negated for a complement) at the lattice nodes, given as a sampled level
+    set with the primitive's boundary id."""
+    X = p.coords()
+    shapes = []
+    for sh in p.shapes:
+        assert sh.kind == "sphere", "sampled copies are made of sphere/circle bodies"
+        r = np.sqrt(sum((X[a] - sh.center[a]) ** 2 for a in range(p.dim)))
+        shapes.append(Shape("sampled", complement=sh.complement, boundary_id=sh.boundary_id,
+                            phi=np.ascontiguousarray(r - sh.axes[0])))
+    q = dataclasses.replace(p, name=p.name + "_sampled", shapes=shapes)
+    return q
+
+
 def tube_3d(nxy: int = 76, nz: int = 300, dx: float = 0.01) -> Problem:
     """Finite tube (Sec. 5.3): R_i=0.15, R_o=0.30 about (0.38,0.38), 0<=Z<=L=3; walls
     traction-free, Z=0 clamped, Z=L stretch 50% + twist 45deg with the cosine ramp T_r=10."""
@@ -584,9 +604,10 @@ def batch_2d(n_spec: int = 96, seed: int = 20260646, side: Sequence[int] = (64, 
         _rest_fields(sp)
         sp.steps = steps
         specs.append((sp, (i0 - margin, j0 - margin)))
-    # one lattice speed for the packed run: 2.5 times the largest longitudinal wave speed at rest,
-    # sqrt(lambda + 2 mu) with rho0 = 1, and at least 10.  The stiffest draws (lambda + 2 mu ~ 42)
-    # blow up at c = 10 and, under this loading, still at c = 2 c_L; 2.16 c_L ran stably.
+    # one lattice speed for the packed run: the smallest the library's wave-speed audit accepts
+    # (2.5 times the largest tangent speed of the reference state, sqrt(lambda + 2 mu) with rho0 = 1;
+    # lbm_create refuses less with LBM_ERR_UNSTABLE_C), and at least 10.  The stiffest draws
+    # (lambda + 2 mu ~ 42) blow up at c = 10 and, under this loading, still at c = 2 c_L; 2.16 c_L ran.
     opts.c = max(10.0, 2.5 * max(np.sqrt(g.lam + 2.0 * g.mu) for g in groups))
     packed = Problem(name=f"batch_2d_{n_spec}", dim=2, n=(width, int(-(-height // 16) * 16), 1), dx=dx,
                      origin=(0.0, 0.0, 0.0), periodic=(False, False, False), mu=1.0, lam=1.0, options=opts,

@@ -14,14 +14,16 @@ import torch
 
 from . import build as _build
 
-_LIB_PATH = _build.LIB
+# LBM_B300_CHECK=1 selects the bounds-checked build (kernels check their data-dependent indices and
+# latch LBM_DEV_BOUNDS); the arithmetic is the same
+_LIB_PATH = _build.LIB_CHECK if os.environ.get("LBM_B300_CHECK") == "1" else _build.LIB
 
-_SHAPE = {"sphere": 0, "ellipsoid": 1, "superellipse": 2, "cylinder": 3, "halfspace": 4}
+_SHAPE = {"sphere": 0, "ellipsoid": 1, "superellipse": 2, "cylinder": 3, "halfspace": 4, "sampled": 5}
 _BCKIND = {"dirichlet": 0, "neumann": 1}
 _PROFILE = {"zero": 0, "affine": 1, "radial": 2, "twist_stretch": 3, "const": 4}
 _RAMP = {"one": 0, "linear": 1, "sin2": 2, "cos": 3, "time": 4}
 PREC = {"fp64": 0, "fp32": 1, "bf16s": 2}
-DEV_STATUS = {1: "nonfinite", 2: "jacobian", 4: "newton", 8: "lsq", 16: "capacity", 128: "timeout"}
+DEV_STATUS = {1: "nonfinite", 2: "jacobian", 4: "newton", 8: "lsq", 16: "capacity", 128: "timeout", 256: "bounds"}
 MAX_SHAPES = 16
 MAX_BCS = 16
 
@@ -33,7 +35,8 @@ class lbm_grid(C.Structure):
 
 class lbm_shape(C.Structure):
     _fields_ = [("kind", C.c_int), ("complement", C.c_int), ("boundary_id", C.c_int), ("reserved", C.c_int),
-                ("center", C.c_double * 3), ("axes", C.c_double * 3), ("rot", C.c_double * 9), ("p", C.c_double)]
+                ("center", C.c_double * 3), ("axes", C.c_double * 3), ("rot", C.c_double * 9), ("p", C.c_double),
+                ("phi", C.c_void_p)]
 
 
 class lbm_material(C.Structure):
@@ -60,7 +63,7 @@ class lbm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("proj_every", C.c_int), ("proj_iters", C.c_int), ("host_staging", C.c_int),
                 ("c", C.c_double), ("omega", C.c_double), ("gamma", C.c_double), ("theta_F", C.c_double),
                 ("proj_beta", C.c_double), ("body_force", C.c_double * 3), ("adjoint", C.c_int),
-                ("reserved", C.c_int)]
+                ("reserved", C.c_int), ("c_audit", C.c_double)]
 
 
 class lbm_info(C.Structure):
@@ -74,6 +77,15 @@ class lbm_kernel_time(C.Structure):
     _fields_ = [("stream_collide_ms", C.c_double), ("cutlink_ms", C.c_double), ("projection_ms", C.c_double),
                 ("stream_collide_launches", C.c_longlong), ("cutlink_launches", C.c_longlong),
                 ("projection_launches", C.c_longlong), ("jacobi_ms", C.c_double), ("jacobi_launches", C.c_longlong)]
+
+
+class lbm_diag(C.Structure):
+    _fields_ = [("J_min", C.c_double), ("J_max", C.c_double), ("v_rms", C.c_double), ("v_max", C.c_double),
+                ("c_tangent", C.c_double), ("incompat_rms", C.c_double), ("n_active", C.c_longlong),
+                ("n_edges", C.c_longlong), ("step", C.c_longlong), ("t", C.c_double)]
+
+
+LAYOUT = {"planes": 0, "nodes": 1}
 
 
 class lbm_tuning(C.Structure):
@@ -93,6 +105,8 @@ SIGNATURES = {
     "lbm_set_initial": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "lbm_step": (C.c_int, [_vp, C.c_int]),
     "lbm_fields": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_fields_ex": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "lbm_diagnostics": (C.c_int, [_vp, C.POINTER(lbm_diag)]),
     "lbm_sync": (C.c_int, [_vp, _i]),
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
     "lbm_enable_timing": (C.c_int, [_vp, C.c_int]),
@@ -101,6 +115,7 @@ SIGNATURES = {
     "lbm_get_tuning": (C.c_int, [_vp, C.POINTER(lbm_tuning)]),
     "lbm_autotune": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(lbm_tuning)]),
     "lbm_set_mu_field": (C.c_int, [_vp, _vp]),
+    "lbm_set_wait_limit": (C.c_int, [_vp, C.c_int]),
     "lbm_set_body_force": (C.c_int, [_vp, _d]),
     "lbm_state_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "lbm_save_state": (C.c_int, [_vp, _vp]),
@@ -153,8 +168,9 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def descriptors(p, precision="fp32", host_staging=False, adjoint=False):
-    """Translate a problem description into the ABI structs."""
+def descriptors(p, precision="fp32", host_staging=False, adjoint=False, keep=None):
+    """Translate a problem description into the ABI structs.  Sampled level sets are copied to the
+    device; the tensors are appended to `keep`, which must outlive the simulation."""
     g = lbm_grid()
     g.dim = p.dim
     for a in range(3):
@@ -171,6 +187,12 @@ def descriptors(p, precision="fp32", host_staging=False, adjoint=False):
         for a in range(9):
             s.rot[a] = float(sh.rot.reshape(-1)[a])
         s.p = sh.p
+        if sh.kind == "sampled":
+            t = torch.as_tensor(np.ascontiguousarray(sh.phi, dtype=np.float64).reshape(-1), device="cuda")
+            assert t.numel() == p.n_box
+            if keep is not None:
+                keep.append(t)
+            s.phi = t.data_ptr()
     groups = getattr(p, "groups", None) or []
     gs = (lbm_group * max(1, len(groups)))()
     for j, gr in enumerate(groups):
@@ -198,6 +220,7 @@ def descriptors(p, precision="fp32", host_staging=False, adjoint=False):
     for a in range(3):
         opt.body_force[a] = float(o.body_force[a])
     opt.adjoint = int(bool(adjoint))
+    opt.c_audit = float(getattr(o, "c_audit", 0.0))
     return g, (shapes, gs), ls, mat, bcs, opt
 
 
@@ -209,7 +232,8 @@ class Simulation:
         lib = load_library()
         self.p, self.precision, self.device = p, precision, torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._desc = descriptors(p, precision, host_staging, adjoint)
+        self._keep = []  # device copies of sampled level sets, alive as long as the simulation
+        self._desc = descriptors(p, precision, host_staging, adjoint, keep=self._keep)
         g, shapes, ls, mat, bcs, opt = self._desc
         nbytes = C.c_size_t(0)
         _check(lib.lbm_geometry_bytes(C.byref(g), C.byref(nbytes)), "lbm_geometry_bytes")
@@ -242,6 +266,11 @@ class Simulation:
         assert t.numel() == self.p.n_box
         _check(load_library().lbm_set_mu_field(self.h, C.c_void_p(t.data_ptr())), "lbm_set_mu_field")
         self.stream.synchronize()
+        return self
+
+    def set_wait_limit(self, polls: int):
+        """First-wait poll limit of the bulk-copy kernels (lbm_set_wait_limit; < 0: the default)."""
+        _check(load_library().lbm_set_wait_limit(self.h, int(polls)), "lbm_set_wait_limit")
         return self
 
     def set_body_force(self, b):
@@ -353,6 +382,25 @@ class Simulation:
         _check(load_library().lbm_fields(self.h, *[_ptr(t) for t in out]), "lbm_fields")
         return out
 
+    def fields_ex(self, sigma: bool = True, J: bool = True, layout: str = "planes"):
+        """(v, F, u, sigma, J) as float64 device tensors (lbm_fields_ex); sigma = J^-1 P F^T.  Layout
+        "planes": (ncomp, *box); "nodes": (*box, ncomp) with a node's components contiguous."""
+        D, bs = self.D, self.p.box_shape
+        shp = (lambda n: (n,) + bs) if layout == "planes" else (lambda n: bs + (n,))
+        out = [torch.empty(shp(D), dtype=torch.float64, device=self.device),
+               torch.empty(shp(D * D), dtype=torch.float64, device=self.device),
+               torch.empty(shp(D), dtype=torch.float64, device=self.device),
+               torch.empty(shp(D * D), dtype=torch.float64, device=self.device) if sigma else None,
+               torch.empty(shp(1), dtype=torch.float64, device=self.device) if J else None]
+        _check(load_library().lbm_fields_ex(self.h, *[_ptr(t) for t in out], LAYOUT[layout]), "lbm_fields_ex")
+        return out
+
+    def diagnostics(self) -> dict:
+        """J range, RMS and largest |v|, largest tangent wave speed, compatibility residual (lbm_diagnostics)."""
+        d = lbm_diag()
+        _check(load_library().lbm_diagnostics(self.h, C.byref(d)), "lbm_diagnostics")
+        return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
+
     def sync(self, raise_on_status: bool = True) -> int:
         st = C.c_int(0)
         rc = load_library().lbm_sync(self.h, C.byref(st))
@@ -402,7 +450,8 @@ def census_static(p, stream: torch.cuda.Stream | None = None) -> dict:
     """Active nodes, cut links and active segments of a problem's grid and level set, computed
     by lbm_census_static (no device allocation; scratch in the library's fixed device array)."""
     lib = load_library()
-    g, shapes, ls, mat, bcs, opt = descriptors(p)
+    keep = []
+    g, shapes, ls, mat, bcs, opt = descriptors(p, keep=keep)
     st = stream if stream is not None else torch.cuda.current_stream()
     a, c, s = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
     _check(lib.lbm_census_static(C.byref(g), C.byref(ls), C.c_void_p(st.cuda_stream), C.byref(a), C.byref(c),

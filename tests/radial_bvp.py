@@ -91,3 +91,39 @@ def displacement_field(res, coords, center):
     r = res["sol"].sol(Rc.reshape(-1))[0].reshape(R.shape)
     Rs = np.where(R > 0, R, 1.0)
     return np.stack([(r - Rc) * d[a] / Rs for a in range(D)])
+
+
+def reference_fields(res, coords, center, mu, lam):
+    """Displacement, deformation gradient and Cauchy stress of the radial solution at node
+    coordinates: u = (r - R) e_R, F = lambda_r e_R (x) e_R + lambda_t (I - e_R (x) e_R)
+    (Eq. spherical-stretches-3d and its 2D reduction), sigma = J^-1 P F^T
+    (Eq. cauchy-recovery-general) with the neo-Hookean P.  Arrays are (comp, *box) with F and sigma
+    row-major; lambda_r is interpolated from the solution's dense table."""
+    D = len(coords)
+    d = [coords[a] - center[a] for a in range(D)]
+    R = np.sqrt(sum(x * x for x in d))
+    Rc = np.clip(R, res["R"][0], res["R"][-1])
+    Rs = np.where(R > 0, R, 1.0)
+    e = [x / Rs for x in d]
+    r = res["sol"].sol(Rc.reshape(-1))[0].reshape(R.shape)
+    Rt = np.linspace(res["R"][0], res["R"][-1], 4001)
+    rt, Pt = res["sol"].sol(Rt)
+    lr_t = np.array([_lambda_r(D, mu, lam, P, l) for P, l in zip(Pt, rt / Rt)])
+    lr = np.interp(Rc, Rt, lr_t)
+    lt = r / Rc
+    u = np.stack([(r - Rc) * e[a] for a in range(D)])
+    F = np.stack([lr * e[i] * e[j] + lt * ((1.0 if i == j else 0.0) - e[i] * e[j])
+                  for i in range(D) for j in range(D)])
+    return u, F, cauchy(F, mu, lam)
+
+
+def cauchy(F, mu, lam):
+    """sigma = J^-1 P F^T for the neo-Hookean law, P = mu F + (lam/2 (J^2 - 1) - mu) F^-T, i.e.
+    sigma = J^-1 (mu F F^T + (lam/2 (J^2 - 1) - mu) I); F given as (D*D, ...) row-major."""
+    D = int(round(np.sqrt(F.shape[0])))
+    Fm = np.moveaxis(F.reshape((D, D) + F.shape[1:]), (0, 1), (-2, -1))
+    J = np.linalg.det(Fm)
+    B = Fm @ np.swapaxes(Fm, -1, -2)
+    s = (0.5 * lam * (J * J - 1.0) - mu)[..., None, None] * np.eye(D)
+    sig = (mu * B + s) / J[..., None, None]
+    return np.moveaxis(sig, (-2, -1), (0, 1)).reshape(F.shape)

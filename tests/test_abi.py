@@ -34,8 +34,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_error_strings(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert lib.lbm_error_string(code)
+    assert lib.lbm_error_string(-9).decode() == "unknown error"
     assert lib.lbm_error_string(-3).decode() == "CUDA runtime error"
 
 
@@ -122,3 +123,35 @@ def test_new_entry_points_refuse_bad_arguments_without_gpu(lib):
     assert lib.lbm_adjoint_begin(None, None) == -1
     assert lib.lbm_adjoint_step(None, None) == -1
     assert lib.lbm_adjoint_gradients(None, None, None) == -1
+
+
+def test_wave_speed_audit_at_create_without_gpu(lib):
+    """lbm_create audits the lattice speed against the largest tangent wave speed of the reference
+    state, sqrt(lambda + 2 mu) (rho0 = 1), before any device work: c below c_audit times it is
+    LBM_ERR_UNSTABLE_C; the default factor is 2.5; a negative factor turns the audit off."""
+    from paper_2606_20646_b300 import inputs as I, lbm
+    p = I.shell_3d(32)                              # mu = 1, lambda = 5: c_T = sqrt(7)
+    g, shapes, ls, mat, bcs, opt = lbm.descriptors(p)
+    h = C.c_void_p()
+    args = lambda: (C.byref(g), C.byref(ls), C.byref(mat), bcs, len(p.bcs), C.byref(opt), None, 0, None, C.byref(h))
+    cT = 7.0 ** 0.5
+    opt.c = 2.5 * cT * 1.001
+    assert lib.lbm_create(*args()) == -4           # passes the audit; no storage given
+    opt.c = 2.5 * cT * 0.999
+    assert lib.lbm_create(*args()) == -8
+    opt.c_audit = 2.0                               # a smaller factor accepts it
+    assert lib.lbm_create(*args()) == -4
+    opt.c_audit = -1.0                              # audit off
+    opt.c = 1.0
+    assert lib.lbm_create(*args()) == -4
+    opt.c_audit = 0.0
+    assert lib.lbm_create(*args()) == -8
+    opt.c_audit = float("nan")
+    assert lib.lbm_create(*args()) == -1
+
+
+def test_field_and_diagnostic_calls_refuse_bad_arguments_without_gpu(lib):
+    from paper_2606_20646_b300 import lbm
+    d = lbm.lbm_diag()
+    assert lib.lbm_fields_ex(None, None, None, None, None, None, 0) == -1
+    assert lib.lbm_diagnostics(None, C.byref(d)) == -1

@@ -26,6 +26,14 @@ def test_algorithmic_bytes_per_node():
     assert b.recompute_bytes_per_node(3, 4) == 625 + 36
     # Jacobi sweep: correction vector (padded to 4) read and written, residual vector, flags
     assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 + 1 == 49
+    # the method's figure: u* in the population precision (the coverage contract's 601 B in 3D FP32)
+    assert b.method_bytes_per_node(3, 4) == 601
+    assert b.method_bytes_per_node(3, 2) == 2 * 72 * 2 + 2 * 3 * 2 + 1
+    assert b.method_bytes_per_node(2, 4) == 209
+    # link kernel: per link 16 B of indices, 8 (1 + 3D) B of FP64 geometry, 3K + 2D values; per
+    # stencil entry an index and D - 1 weights
+    assert b.link_bytes(3, 4, 1, 0) == 16 + 8 * 10 + (36 + 6) * 4
+    assert b.link_bytes(3, 4, 0, 10) == 10 * (4 + 8)
 
 
 def test_traffic_is_reported_only_for_the_captured_sources():
@@ -44,6 +52,7 @@ def test_traffic_is_reported_only_for_the_captured_sources():
 
 def test_oracle_sample_is_bounded_and_whole_projection_cycles():
     b = _bench()
-    mlups, steps, elapsed, nact = b.oracle_sample(n=16, budget_s=0.5)
-    assert steps >= 20 and steps % 20 == 0
-    assert nact > 0 and mlups > 0 and elapsed < 30
+    for threads in (1, 0):
+        mlups, steps, elapsed, nact = b.oracle_sample(n=16, budget_s=0.5, threads=threads)
+        assert steps >= 20 and steps % 20 == 0
+        assert nact > 0 and mlups > 0 and elapsed < 30

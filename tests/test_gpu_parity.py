@@ -132,3 +132,27 @@ def test_geometry_matches_oracle(builder, N):
     assert np.abs(g["eta"] - r["eta"]).max() < 1e-12
     assert np.abs(g["Nb"] - r["Nb"]).max() < 1e-12
     assert (g["ns"] == r["ns"]).all()
+
+
+@pytest.mark.parametrize("builder,N,steps,prec", [(I.affine_annulus_2d, 72, 60, "fp64"),
+                                                  (I.shell_3d, 32, 45, "fp64"),
+                                                  (I.shell_3d, 48, 45, "fp32")])
+def test_sampled_level_set_matches_oracle(builder, N, steps, prec):
+    """A body given by node samples of its level set (Sec. 3.1): mask and cut links bit-exact, eta
+    and N_b to FP64 rounding, and the run at the form's tolerance."""
+    import oracle
+    from paper_2606_20646_b300 import lbm
+    p = I.sampled_copy(builder(N))
+    sim = lbm.Simulation(p, precision=prec)
+    o = oracle.Oracle(p)
+    assert (sim.active_mask() == o.active_mask()).all()
+    g, r = sim.links(), o.links()
+    assert (g["node"] == r["node"]).all() and (g["q"] == r["q"]).all() and (g["bid"] == r["bid"]).all()
+    assert np.abs(g["eta"] - r["eta"]).max() < 1e-12 and np.abs(g["Nb"] - r["Nb"]).max() < 1e-12
+    sim.close()
+    errs, sg, so, *_ = compare(p, steps, prec)
+    assert sg == 0 and so == 0
+    if prec == "fp64":
+        _check64(errs, sg, so)
+    else:
+        assert errs["v"] < TOL32 and errs["F"] < TOL32, errs

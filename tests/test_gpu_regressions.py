@@ -5,7 +5,8 @@ omega = 2) is kept exactly by the cut-link closure: the FP64 form reproduces it 
 every size, the FP32 form below the errors printed for N = 384 (Table tab:2d-curved-summary).
 The rotated ellipsoid (Sec. 5.1, omega = 1.8) is not exact: the FP64 form must refine at near
 second order from N = 80 to 160, and the FP32 form at N = 320 must reach the printed errors, final
-deformation gradient (Eq. ellipsoid-F-3d) and Jacobian range.
+deformation gradient (Eq. ellipsoid-F-3d) and Jacobian range.  The spherical shell (Sec. 5.2) runs
+at the paper's own traction protocol and is held to its printed errors against the radial BVP.
 """
 import json
 import os
@@ -144,3 +145,35 @@ def test_ellipsoid_fp32_N320_against_printed_values(ellipsoid_320):
     assert EF < EF64 + 5e-5
     Fm = F[:, act].mean(axis=1).reshape(3, 3)
     assert np.abs(Fm - np.array(g["F_T"])).max() < 1.5e-4
+
+
+def test_spherical_shell_paper_protocol_N200():
+    """The paper's spherical shell (Sec. 5.2) at its own protocol: N = 200, both surfaces Neumann
+    (inner nominal traction 1.15242 s(t) e_R, sin^2 ramp T_r = 2, outer traction-free), mu = 1,
+    lambda = 2/3, c = 10, omega = 1.8, gamma = 10, projection every 20 steps, 10 000 steps to
+    t = 5.  FP32 form.  Against the radial BVP (Eqs. spherical-stretches-3d,
+    spherical-equilibrium-3d): E(u), E(F), E(sigma) within 1.5 times the printed 1.18e-3, 5.23e-4,
+    2.07e-3; the residual RMS velocity within 1.5 times the printed 4.56e-4; J inside the printed
+    range [1.081, 1.165] widened by 0.005.  The run is stable at omega = 1.8 (the instability of the
+    stiffer lambda = 5 and 10 workloads at that omega is theirs, not a reading shared by the oracle
+    and the kernels)."""
+    import radial_bvp as rb
+    from parity import rel_l2
+    g = GOLD["spherical_shell"]
+    p = I.sphere_shell_paper_3d(200)
+    assert p.steps == 10000 and p.options.omega == 1.8
+    v, F, u, act, info = _run(p, "fp32")
+    assert abs(info["n_active"] - g["active_cut_N200_rounded"][0]) < 0.01 * g["active_cut_N200_rounded"][0]
+    assert abs(info["n_cut"] - g["active_cut_N200_rounded"][1]) < 0.01 * g["active_cut_N200_rounded"][1]
+    r = rb.solve(3, 1.0, 2.0 / 3.0, g["R_i"], g["R_o"], ("P", g["Pr_Ri"]), ("P", 0.0))
+    ur, Fr, sr = rb.reference_fields(r, p.coords(), (0.5, 0.5, 0.5), 1.0, 2.0 / 3.0)
+    Eu = rel_l2(u[:, act], ur[:, act])
+    EF = rel_l2(F[:, act], Fr[:, act])
+    Es = rel_l2(rb.cauchy(F[:, act], 1.0, 2.0 / 3.0), sr[:, act])
+    vrms = float(np.sqrt((v[:, act] ** 2).sum(0).mean()))
+    J = np.linalg.det(np.moveaxis(F[:, act].reshape(3, 3, -1), -1, 0))
+    print(f"shell N=200: E(u) {Eu:.3e} E(F) {EF:.3e} E(sigma) {Es:.3e} v_rms {vrms:.3e} J [{J.min():.4f}, {J.max():.4f}]")
+    assert Eu < 1.5 * g["E_u_N200"] and EF < 1.5 * g["E_F_N200"] and Es < 1.5 * g["E_sigma_N200"]
+    assert vrms < 1.5 * g["v_rms_N200"]
+    lo, hi = g["J_range_N200_LBM"]
+    assert lo - 0.005 < J.min() and J.max() < hi + 0.005

@@ -72,3 +72,24 @@ def test_step_before_initial_state_is_rejected():
     with pytest.raises(lbm.LbmError) as e:
         sim.step(1)
     assert e.value.code == -5
+
+
+def test_bulk_copy_wait_that_runs_out_is_reported():
+    """The fused kernel's bounded wait for its bulk copies: with its first limit set to 0 polls
+    every first wait runs out at once; the kernel latches LBM_DEV_TIMEOUT (128), waits (with the
+    full limit) for the copies it issued and returns without writing, and lbm_sync reports the
+    bit.  No fault: the context stays usable, and a fresh simulation afterwards runs cleanly."""
+    from paper_2606_20646_b300 import lbm
+    p = I.shell_3d(32)                          # rows of 32 nodes: the bulk-copy kernel runs
+    sim = lbm.Simulation(p, precision="fp32")
+    sim.set_initial().step(2)                   # first step (plain kernel, projection), then one fused step
+    assert sim.sync(raise_on_status=False) == 0
+    sim.set_wait_limit(0)
+    sim.step(1)                                 # step 2: a fused step, every first wait runs out
+    st = sim.sync(raise_on_status=False)
+    assert st & 128
+    sim.close()
+    sim = lbm.Simulation(p, precision="fp32")
+    sim.set_initial().step(3)
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()

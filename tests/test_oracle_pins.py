@@ -517,3 +517,43 @@ def test_mu_field_is_local_and_reduces_to_scalar():
     assert d[far].max() == 0.0
     assert d[6, 6, 6] > 0.0
 
+
+
+# --------------------------------------------------------------------------- sampled level set
+
+def _true_phi_annulus(Xb):
+    r = np.sqrt(((Xb[:, :2] - 0.5) ** 2).sum(1))
+    return np.minimum(np.abs(r - 0.42), np.abs(r - 0.18)), r
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_sampled_level_set_links_and_boundary_points(N):
+    """A body given by node samples of its signed distance (Sec. 3.1, phi at the nodes): the active
+    set and the cut links are those of the analytic body (the node values are exact), and each
+    boundary point, the root of the level set's linear interpolant along the link, lies within the
+    interpolation bound dx^2 / (8 R_min) of the true surface (|phi''| <= 1/R along a link of the
+    distance to circles of radius R >= R_min = 0.18)."""
+    p = I.affine_annulus_2d(N)
+    q = I.sampled_copy(p)
+    oa, os_ = oracle.Oracle(p), oracle.Oracle(q)
+    assert (oa.active_mask() == os_.active_mask()).all()
+    la, ls = oa.links(), os_.links()
+    assert (la["node"] == ls["node"]).all() and (la["q"] == ls["q"]).all() and (la["bid"] == ls["bid"]).all()
+    d, _ = _true_phi_annulus(ls["Xb"])
+    assert d.max() <= p.dx ** 2 / (8 * 0.18)
+
+
+def test_sampled_level_set_normal_converges_at_second_order():
+    """N_b from the interpolated central differences of the samples converges to the circle's
+    normal e_R (outer) / -e_R (inner) at second order (RMS over the cut links)."""
+    errs = []
+    for N in (64, 256):
+        q = I.sampled_copy(I.affine_annulus_2d(N))
+        L = oracle.Oracle(q).links()
+        _, r = _true_phi_annulus(L["Xb"])
+        eR = (L["Xb"][:, :2] - 0.5) / r[:, None]
+        outer = np.abs(r - 0.42) < np.abs(r - 0.18)
+        exact = np.where(outer[:, None], eR, -eR)
+        errs.append(np.sqrt(((L["Nb"][:, :2] - exact) ** 2).sum(1).mean()))
+    order = math.log(errs[0] / errs[1]) / math.log(4.0)
+    assert order > 1.8, (errs, order)
