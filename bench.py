@@ -542,6 +542,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         ms_rec = max_over_ranks(e0.elapsed_time(e1), world) / every
         ms_rev = max_over_ranks(e2.elapsed_time(e3), world) / every
+        st_adj = sim.sync(raise_on_status=False)
         brev, brec = adjoint_bytes_per_node(3, 4), recompute_bytes_per_node(3, 4)
         gb_rev = nact_a * brev / (ms_rev / 1e3) / 1e9
         gb_rec = nact_a * brec / (ms_rec / 1e3) / 1e9
@@ -554,6 +555,39 @@ def run_ours(args, world, rank, local):
                                  "frac": round(gb_rec / peak, 4)},
                    "peak": peak, "peak_kind": peak_kind,
                    "note": f"CUDA events around {every} launches of each on the solver's stream"}
+        del sim
+        torch.cuda.empty_cache()
+        # the FP64 form's reverse mode (the one held to central differences at 1e-4 on this workload),
+        # over a shorter run: its backward time against its plain forward
+        fp64_adj = None
+        if not args.no_fp64:
+            K64 = min(Ka, 3 * every)
+            s64 = lbm.Simulation(pa, precision="fp64", device=dev, adjoint=True)
+            s64.set_mu_field(pa.meta["mu_target"]).set_initial()
+            s64.step(K64)
+            u64_t = s64.fields()[2].clone()
+            s64.set_mu_field(torch.ones(pa.box_shape, dtype=torch.float64, device=dev)).set_initial()
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(s64.stream)
+            s64.step(K64)
+            e1.record(s64.stream)
+            torch.cuda.synchronize()
+            ms64_plain = e0.elapsed_time(e1)
+            mu = torch.ones(pa.box_shape, dtype=torch.float64, device=dev, requires_grad=True)
+            b = torch.tensor(pa.options.body_force, dtype=torch.float64, requires_grad=True)
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record(s64.stream)
+            u = A.displacement(mu, b, s64, K64, every)
+            e1.record(s64.stream)
+            (0.5 * (((u - u64_t) ** 2) * act_t).sum()).backward()
+            e2.record(s64.stream)
+            torch.cuda.synchronize()
+            fp64_adj = {"steps": K64, "forward_ms": round(ms64_plain, 2), "backward_ms": round(e1.elapsed_time(e2), 2),
+                        "adjoint_over_forward": round(e1.elapsed_time(e2) / ms64_plain, 3),
+                        "device_status": s64.sync(raise_on_status=False)}
+            del s64
+            torch.cuda.empty_cache()
         adj = {"workload": f"inclusion_cube_{args.adj_n}: D3Q6x12 FP32, clamped unit cube, target mu 2 inside "
                            "r = 0.25, parameter mu field (start 1) and body force, loss 1/2 |u(T) - u_target|^2",
                "n_active": nact_a, "steps": Ka, "checkpoint_every": every,
@@ -561,12 +595,10 @@ def run_ours(args, world, rank, local):
                "forward_ms": round(ms_plain, 2), "forward_with_saves_ms": round(ms_fwd, 2),
                "backward_ms": round(ms_bwd, 2), "adjoint_over_forward": round(ms_bwd / ms_plain, 3),
                "loss": loss, "grad_mu_norm": float(gmu.norm()), "grad_b": [float(x) for x in gb],
-               "kernels": kernels,
-               "device_status": sim.sync(raise_on_status=False),
+               "kernels": kernels, "fp64": fp64_adj,
+               "device_status": st_adj,
                "note": "backward = recomputation from saved states recording F, then the reverse steps; "
                        "ratio over the plain forward of the same steps"}
-        del sim
-        torch.cuda.empty_cache()
 
     # ---- errors of the FP32 and FP64 forms against the oracle (64^3 copy, t = 1) -----------------
     errors = None

@@ -103,6 +103,7 @@ struct lbm_handle {
     double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
     void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr, *l_fo = nullptr;
     float4 *l_bvec = nullptr;  // FP32 forms: per-link geometric vector of the boundary profile
+    float *l_gsum = nullptr;   // FP32 forms with Neumann links: per-link tangent-image sums (8 floats)
     void *u0 = nullptr, *u1 = nullptr;  // projection warm starts (displacement-accumulator layout)
     double *partial = nullptr, *mean = nullptr, *staging = nullptr;
     double *diag = nullptr;  // diagnostics and audit reductions: kReduceBlocks partial records + the result
@@ -454,8 +455,28 @@ template <typename real, int D, typename pop = real> struct Impl {
         else if (nw == 2) launch_fused_nw<2>(h, a);
         else launch_fused_nw<1>(h, a);
     }
+    // a grid of the blocks resident at once (occupancy query, once per instantiation), at most one
+    // block per 4 S segments
     template <int S> static void launch_jacobi_s(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
-        k_jacobi<real, D, S><<<grid_for(h->nseg, 4 * S), 128, 0, h->stream>>>(p, src, dst);
+        if (h->box.per[0]) launch_jacobi_sx<S, false>(h, p, src, dst);
+        else launch_jacobi_sx<S, true>(h, p, src, dst);
+    }
+    template <int S, bool SHX>
+    static void launch_jacobi_sx(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
+        static int resident = 0;
+        if (resident == 0) {
+            int per_sm = 0, dev = 0, sms = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<real, D, S, SHX>, 128, 0) != cudaSuccess ||
+                cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 8;
+                sms = 148;
+            }
+            resident = per_sm * sms;
+        }
+        const unsigned g = std::min<unsigned>(grid_for(h->nseg, 4 * S), (unsigned)resident);
+        k_jacobi<real, D, S, SHX><<<std::max(g, 1u), 128, 0, h->stream>>>(p, src, dst);
     }
     static void launch_jacobi(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
         const int js = h->tune_jseg ? h->tune_jseg : kJacobiSegs;
@@ -544,7 +565,7 @@ template <typename real, int D, typename pop = real> struct Impl {
         a.L = links(h);
         a.b = h->box;
         a.flags = h->flags;
-        a.fstar = static_cast<const real *>(h->fB);  // written by this step's collision, read by the next gather
+        a.fstar = static_cast<const real *>(h->fA);  // this step's post-collision state, read by the next gather
         a.bcs = h->dbcs;
         a.un = static_cast<const real *>(h->un);
         a.npad = h->box.npad;
@@ -561,8 +582,13 @@ template <typename real, int D, typename pop = real> struct Impl {
         EventPair ep;
         if (h->timing) timing_begin(h, ep, 1);
         const int lb = h->tune_lblock ? h->tune_lblock : 128;
-        if constexpr (sizeof(real) == 4)
-            k_links_f32<D, pop><<<grid_for(h->n_cut * kLinkLanes<D>, lb), lb, 0, h->stream>>>(a, bc_times(h, t + 0.5 * a.dt));
+        if constexpr (sizeof(real) == 4) {
+            if (h->n_neu > 0) {
+                k_link_sums<D><<<grid_for(h->n_cut * kLinkLanes<D>, 256), 256, 0, h->stream>>>(a, h->l_gsum);
+                h->launches++;
+            }
+            k_links_f32<D, pop><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a, bc_times(h, t + 0.5 * a.dt), h->l_gsum);
+        }
         else
             k_cutlinks<real, D><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a);
         if (h->timing) timing_end(h, ep);
@@ -648,7 +674,12 @@ template <typename real, int D, typename pop = real> struct Impl {
                 real *d = nullptr;
                 int rc = solve(h, t, static_cast<const real *>(h->u0), &d);
                 if (rc) return rc;
-                k_repair_collide<real, D, pop><<<g, 128, 0, h->stream>>>(a, static_cast<const real *>(h->u0), d, h->mean,
+                // out of place: f^n (from the gather, in fB) in, f*^n out into fA, whose f*^{n-1} the
+                // gather has consumed; the buffers then need no swap
+                StepArgs<real> ar = a;
+                ar.fsrc = static_cast<const real *>(h->fB);
+                ar.fdst = static_cast<real *>(h->fA);
+                k_repair_collide<real, D, pop><<<g, 128, 0, h->stream>>>(ar, static_cast<const real *>(h->u0), d, h->mean,
                                                                      h->opt.theta_F, static_cast<real *>(h->u1));
                 h->launches++;
                 CKL();
@@ -659,9 +690,10 @@ template <typename real, int D, typename pop = real> struct Impl {
                 CKL();
                 if (h->timing) timing_end(h, ep);
             }
+            // the post-collision state: fB after a regular step, fA after a projection step
+            if (!proj) std::swap(h->fA, h->fB);
             int rc = cutlinks(h, t);
             if (rc) return rc;
-            std::swap(h->fA, h->fB);
             h->phase = 1;
             h->step++;
         }

@@ -1652,17 +1652,17 @@ constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep (default;
 
 // One damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr),
 //   d'_m = (1 - beta) d_m + beta / deg_m (r_m + sum over active axis neighbours l of d_l),
-// warp w handling segments S*w .. S*w + S - 1.  A node is its flag
+// for segments s0 .. s0 + S - 1 of the calling warp.  A node is its flag
 // byte, one residual vector, its own d vector and 2D neighbour d vectors, all loaded before any is
-// used; a neighbour across a cut link (inactive, or outside a non-periodic box, where the index is
-// clamped into range) is dropped by selection, as a skipped term; nodes with w = 0 keep their d
-// and are not written.
-template <typename real, int D, int S = kJacobiSegs>
-__global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din, real *dout) {
+// used (the x neighbours, when rows do not wrap, taken from the neighbouring lanes by shuffles); a
+// neighbour across a cut link (inactive, or outside a non-periodic box, where the index is clamped
+// into range) is dropped by selection, as a skipped term; nodes with w = 0 keep their d and are not
+// written.
+template <typename real, int D, int S, bool shx>
+__device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const real *__restrict__ din,
+                                                real *__restrict__ dout, int s0) {
     constexpr int Q = 2 * D, V = kDV<D>;
     const int lane = threadIdx.x & 31;
-    const int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
-    if (s0 >= a.nseg) return;
     const long long P = a.b.npad;
     const real beta = (real)a.beta;
     const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
@@ -1692,7 +1692,22 @@ __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const re
         if (din) {
             ld_vec<V, real>(din + V * node[j], dold[j]);
             #pragma unroll
-            for (int q = 0; q < Q; ++q) ld_vec<V, real>(din + V * ln[j][q], nb[j][q]);
+            for (int q = 0; q < Q; ++q)
+                if (q >= 2 || !shx) ld_vec<V, real>(din + V * ln[j][q], nb[j][q]);
+            if constexpr (shx) {
+                // the x neighbours are the neighbouring lanes' own vectors; lane 31 loads node + 1 and
+                // lane 0 node - 1 (the other lanes load their own node again, an L1 hit)
+                real e[V];
+                const long long ie = lane == 31 ? node[j] + 1 : (lane == 0 ? (node[j] > 0 ? node[j] - 1 : 0) : node[j]);
+                ld_vec<V, real>(din + V * ie, e);
+                #pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const real dn = __shfl_down_sync(0xffffffffu, dold[j][i], 1);
+                    const real up = __shfl_up_sync(0xffffffffu, dold[j][i], 1);
+                    nb[j][0][i] = lane == 31 ? e[i] : dn;  // +x: node + 1
+                    nb[j][1][i] = lane == 0 ? e[i] : up;   // -x: node - 1
+                }
+            }
         } else {
             #pragma unroll
             for (int i = 0; i < V; ++i) {
@@ -1719,6 +1734,18 @@ __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const re
         st_vec<V, real>(dout + V * node[j], out);
     }
 }
+
+// The grid is sized to the blocks that fit on the GPU at once and every warp strides over the
+// segment list (S segments at a time), so no time goes to retiring and launching short blocks.
+// shx: rows do not wrap (x not periodic), so a segment's x neighbours are its own lanes' vectors.
+template <typename real, int D, int S = kJacobiSegs, bool shx = true>
+__global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din,
+                                                real *__restrict__ dout) {
+    const int stride = gridDim.x * 4 * S;
+    for (int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S; s0 < a.nseg; s0 += stride)
+        jacobi_segments<real, D, S, shx>(a, din, dout, s0);
+}
+
 
 // block partial sums of the correction (u^c - u^0) per component: warp shuffles, then shared memory
 template <typename real, int D>
@@ -1792,7 +1819,8 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__
 
 // after the first solve: u^n = u0 + d - mean (written to u1), F^c (Eq. projection-compatible-F), F^r
 // (Eq. projection-F-repair-weight), population repair (Eq. projection-population-repair),
-// collision and u*^{n+1}.  f^n is read from and f*^n written to fdst (in place).
+// collision and u*^{n+1}.  f^n is read from fsrc and f*^n written to fdst, two different buffers,
+// so each direction's loads can be issued ahead of the other directions' stores.
 template <typename real, int D, typename pop = real>
 __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, const real *__restrict__ u0,
                                                         const real *__restrict__ dc, const double *__restrict__ mean,
@@ -1802,15 +1830,9 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
     const unsigned cut = fl & kCutMask;
-    // the node's pre-collision populations, loaded before the stores to the same array (loads issued
-    // between those stores could not be moved ahead of them): all at once in the FP32 form, one
-    // direction at a time in the FP64 form, whose registers would not hold all of them
-    constexpr int kPre = sizeof(real) == 4 ? Q * K : K;
-    real fpre[kPre];
-    if constexpr (kPre == Q * K) {
-        #pragma unroll
-        for (int j = 0; j < Q * K; ++j) fpre[j] = pop_ld_rw<real, pop>(a.fdst, (long long)j * P + node);
-    }
+    const real *__restrict__ fsrc = a.fsrc;
+    real *__restrict__ fdst = a.fdst;
+    real fpre[K];
     real v[D], G[D * D], F[D * D], Pold[D * D], Fr[D * D], Gr[D * D], Pk[D * D];
     #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = a.vst[i * P + node];
@@ -1885,13 +1907,11 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
         const int A = q >> 1;
         const real s = (q & 1) ? real(-1) : real(1);
         real out[K];
-        if constexpr (kPre == K) {
-            #pragma unroll
-            for (int k = 0; k < K; ++k) fpre[k] = pop_ld_rw<real, pop>(a.fdst, (long long)(q * K + k) * P + node);
-        }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) fpre[k] = pop_ld<real, pop>(fsrc, (long long)(q * K + k) * P + node);
         #pragma unroll
         for (int k = 0; k < K; ++k) {
-            real fv = fpre[kPre == K ? k : q * K + k];
+            real fv = fpre[k];
             real feq;  // equilibrium at the repaired state (Eq. feq-general-d)
             if (k < D) {
                 const int i = k;
@@ -1912,7 +1932,7 @@ __global__ void __launch_bounds__(128) k_repair_collide(const StepArgs<real> a, 
             out[k] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : real(0));
         }
         #pragma unroll
-        for (int k = 0; k < K; ++k) pop_st<real, pop>(a.fdst, (long long)(q * K + k) * P + node, out[k]);
+        for (int k = 0; k < K; ++k) pop_st<real, pop>(fdst, (long long)(q * K + k) * P + node, out[k]);
         if (cut) keep_link_values<real, K>(a.lfo, l0, cut, q, out, a.ncut, a.status);
     }
     #pragma unroll

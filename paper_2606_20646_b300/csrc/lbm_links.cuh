@@ -1,11 +1,11 @@
 // Boundary sources and cut-link reconstruction of the FP32 forms (FP32 arithmetic, populations in
-// FP32 or BF16): one group of G lanes per cut link (Secs. 3.2-3.4).
+// FP32 or BF16), in two kernels (Secs. 3.2-3.4).
 //
-// The lanes of a group split the link's least-squares stencil (the tangent images of a Neumann link,
+// k_link_sums: groups of G lanes split each Neumann link's least-squares stencil (the tangent images,
 // Eqs. tangent-derivative-2d, tangent-image-3d-lsq), so its index and displacement loads are in flight
-// together; their partial sums are combined by shuffles.  Every lane then runs the same traction
-// inversion (Eqs. neumann-newton-2d/3d) on identical inputs, and each lane reconstructs a share of the
-// K incoming components with the interpolated pair relation (Eqs. bfl-eta-ge-half, bfl-eta-lt-half).
+// together, and combine the partial sums by shuffles; it holds few registers, so many groups are
+// resident.  k_links_f32: one thread per link runs the traction inversion (Eqs. neumann-newton-2d/3d)
+// and the reconstruction (Eqs. bfl-eta-ge-half, bfl-eta-lt-half).
 //
 // Precision.  Near F = I the deformation gradient of a boundary point is I plus a small part, and the
 // Neumann rows need F_b - I (the populations are stored shifted by f^eq(0, I)).  Forming F_b in FP32
@@ -112,38 +112,118 @@ __device__ __forceinline__ bool traction_rq(const float E[D * D], const float hh
     return true;
 }
 
-template <int D> constexpr int kLinkLanes = D == 3 ? 8 : 4;  // lanes per cut link
+template <int D> constexpr int kLinkLanes = D == 3 ? 8 : 4;  // lanes per cut link in the stencil phase
 
-template <int D, typename pop, int G = kLinkLanes<D>>
-__global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const __grid_constant__ BCTimes bt) {
-    constexpr int K = D + D * D;
-    constexpr int KC = (K + G - 1) / G;  // reconstructed components per lane
+// Stencil sums of the Neumann links: one group of G lanes per link splits its LSQ stencil (entries
+// r, r + G, ... for lane r), the compensated partial sums are combined by shuffles and lane 0 of the
+// group writes gg_a = sum_j w_aj (u_j - u_m) (D - 1 vectors, 8 floats per link).  Few registers, so
+// many links' index and displacement loads are in flight on every SM.
+template <int D, int G = kLinkLanes<D>>
+__global__ void __launch_bounds__(256) k_link_sums(const CutArgs<float> a, float *__restrict__ gsum) {
     const int lane = threadIdx.x & 31, r = lane & (G - 1);
     const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
     if (l >= a.L.ncut) return;  // whole groups leave together
+    const int ns = __ldg(a.L.ns + l);  // 0 for Dirichlet links
+    if (ns == 0) return;
+    float gh[D - 1][D], ge[D - 1][D];
+    #pragma unroll
+    for (int al = 0; al < D - 1; ++al)
+        #pragma unroll
+        for (int i = 0; i < D; ++i) { gh[al][i] = 0.0f; ge[al][i] = 0.0f; }
+    float um[D], uml[D];
+    un_load<float, D>(a.un, __ldg(a.L.node + l), um, uml);
+    constexpr int U = 4;
+    const int *__restrict__ sidx = a.L.sidx + l * kLsqCap;
+    const float *__restrict__ wl = a.L.w + l * kLsqCap * (D - 1);
+    for (int j0 = r; j0 < ns; j0 += U * G) {
+        int kk[U];
+        float w[U][D - 1], uu[U][D], uul[U][D];
+        #pragma unroll
+        for (int jj = 0; jj < U; ++jj) {
+            const int j = j0 + jj * G < ns ? j0 + jj * G : j0;
+            kk[jj] = __ldg(sidx + j);
+            TLV_BOUND(kk[jj], a.npad, a.status);
+            if constexpr (D == 3) {
+                const float2 wv = __ldg(reinterpret_cast<const float2 *>(wl) + j);
+                w[jj][0] = wv.x;
+                w[jj][1] = wv.y;
+            } else {
+                w[jj][0] = __ldg(wl + j);
+            }
+        }
+        #pragma unroll
+        for (int jj = 0; jj < U; ++jj) un_load<float, D>(a.un, kk[jj], uu[jj], uul[jj]);
+        #pragma unroll
+        for (int jj = 0; jj < U; ++jj) {
+            if (j0 + jj * G >= ns) break;
+            #pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float du = __fadd_rn(__fsub_rn(uu[jj][i], um[i]), __fsub_rn(uul[jj][i], uml[i]));
+                #pragma unroll
+                for (int al = 0; al < D - 1; ++al) {
+                    float pr, pe, sn, se;
+                    two_prod(w[jj][al], du, pr, pe);
+                    two_sum(gh[al][i], pr, sn, se);
+                    gh[al][i] = sn;
+                    ge[al][i] = __fadd_rn(ge[al][i], __fadd_rn(pe, se));
+                }
+            }
+        }
+    }
+    #pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+        #pragma unroll
+        for (int al = 0; al < D - 1; ++al)
+            #pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float xh = __shfl_xor_sync(gm, gh[al][i], o), xe = __shfl_xor_sync(gm, ge[al][i], o);
+                float sn, se;
+                two_sum(gh[al][i], xh, sn, se);
+                gh[al][i] = sn;
+                ge[al][i] = __fadd_rn(__fadd_rn(ge[al][i], xe), se);
+            }
+    if (r == 0) {
+        float out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        #pragma unroll
+        for (int al = 0; al < D - 1; ++al)
+            #pragma unroll
+            for (int i = 0; i < D; ++i) out[al * D + i] = __fadd_rn(gh[al][i], ge[al][i]);
+        float4 *o4 = reinterpret_cast<float4 *>(gsum + l * 8);
+        o4[0] = make_float4(out[0], out[1], out[2], out[3]);
+        o4[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// One thread per cut link: boundary values, the traction inversion of a Neumann link (its tangent
+// images from k_link_sums), and the reconstruction of the K incoming components.
+template <int D, typename pop>
+__global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const __grid_constant__ BCTimes bt,
+                                                   const float *__restrict__ gsum) {
+    constexpr int K = D + D * D;
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= a.L.ncut) return;
     const int q = __ldg(a.L.q + l), A = q >> 1;
     const float s = (q & 1) ? -1.0f : 1.0f;  // e = s e_A, d = -e
     const BCTimeF &tb = bt.bc[__ldg(a.L.bc + l)];
     const int mnode = __ldg(a.L.node + l);
     const float eta = (float)__ldg(a.L.eta + l);
     // operands of the reconstruction, loaded first: the node's kept pair f*_c(m), f*_{c^1}(m) and, for
-    // eta < 1/2 with an active upstream node m + e_{c^1}, that node's f*_c (this lane's components)
+    // eta < 1/2 with an active upstream node m + e_{c^1}, that node's f*_c
     const bool upn = !((__ldg(a.flags + mnode) >> (q ^ 1)) & 1) && !(eta >= 0.5f);
-    int mup = mnode;
+    float fo[K], fi[K], fu[K];
+    vload<K>(a.L.fo + l * (2 * K), fo);
+    vload<K>(a.L.fo + l * (2 * K) + K, fi);
     if (upn) {
         int x, y, z;
         node_xyz(a.b, mnode, x, y, z);
-        mup = nbr(a.b, mnode, x, y, z, q ^ 1);
+        int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
         TLV_BOUND(mup, a.b.npad, a.status);
-    }
-    float fo[KC], fi[KC], fu[KC];
-    #pragma unroll
-    for (int c = 0; c < KC; ++c) {
-        const int k = r + c * G < K ? r + c * G : K - 1;
-        fo[c] = __ldg(a.L.fo + l * (2 * K) + k);
-        fi[c] = __ldg(a.L.fo + l * (2 * K) + K + k);
-        fu[c] = upn ? pop_ld<float, pop>(a.fstar, (long long)(q * K + k) * a.b.npad + mup) : fo[c];
+        #pragma unroll
+        for (int k = 0; k < K; ++k) fu[k] = pop_ld<float, pop>(a.fstar, (long long)(q * K + k) * a.b.npad + mup);
+    } else {
+        #pragma unroll
+        for (int k = 0; k < K; ++k) fu[k] = fo[k];
     }
     const float4 gv = __ldg(a.L.bvec + l);
     const float gl[3] = {gv.x, gv.y, gv.z};
@@ -165,79 +245,16 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
         float mu = a.mtab ? a.mtab[2 * a.mat[mnode]] : (float)a.mu;
         const float lam = a.mtab ? a.mtab[2 * a.mat[mnode] + 1] : (float)a.lam;
         if (a.mu_field) mu = a.mu_field[mnode];
-        float N[D], t[D - 1][D];
+        float N[D], t[D - 1][D], gg[D - 1][D];
         #pragma unroll
         for (int i = 0; i < D; ++i) N[i] = (float)__ldg(a.L.Nb + 3 * l + i);
         #pragma unroll
         for (int al = 0; al < D - 1; ++al)
             #pragma unroll
-            for (int i = 0; i < D; ++i) t[al][i] = (float)__ldg(a.L.tan + 6 * l + 3 * al + i);
-        // gg_a = sum_j w_aj (u_j - u_m) over this lane's stencil entries j = r, r + G, ...: the (hi, lo)
-        // displacement pairs differenced part by part, products and sums compensated
-        float um[D], uml[D];
-        un_load<float, D>(a.un, mnode, um, uml);
-        const int ns = __ldg(a.L.ns + l);
-        float gh[D - 1][D], ge[D - 1][D];
-        #pragma unroll
-        for (int al = 0; al < D - 1; ++al)
-            #pragma unroll
-            for (int i = 0; i < D; ++i) { gh[al][i] = 0.0f; ge[al][i] = 0.0f; }
-        constexpr int U = 4;
-        const int *__restrict__ sidx = a.L.sidx + l * kLsqCap;
-        const float *__restrict__ wl = a.L.w + l * kLsqCap * (D - 1);
-        for (int j0 = r; j0 < ns; j0 += U * G) {
-            int kk[U];
-            float w[U][D - 1], uu[U][D], uul[U][D];
-            #pragma unroll
-            for (int jj = 0; jj < U; ++jj) {
-                const int j = j0 + jj * G < ns ? j0 + jj * G : j0;
-                kk[jj] = __ldg(sidx + j);
-                TLV_BOUND(kk[jj], a.npad, a.status);
-                if constexpr (D == 3) {
-                    const float2 wv = __ldg(reinterpret_cast<const float2 *>(wl) + j);
-                    w[jj][0] = wv.x;
-                    w[jj][1] = wv.y;
-                } else {
-                    w[jj][0] = __ldg(wl + j);
-                }
+            for (int i = 0; i < D; ++i) {
+                t[al][i] = (float)__ldg(a.L.tan + 6 * l + 3 * al + i);
+                gg[al][i] = __ldg(gsum + l * 8 + al * D + i);
             }
-            #pragma unroll
-            for (int jj = 0; jj < U; ++jj) un_load<float, D>(a.un, kk[jj], uu[jj], uul[jj]);
-            #pragma unroll
-            for (int jj = 0; jj < U; ++jj) {
-                if (j0 + jj * G >= ns) break;
-                #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const float du = __fadd_rn(__fsub_rn(uu[jj][i], um[i]), __fsub_rn(uul[jj][i], uml[i]));
-                    #pragma unroll
-                    for (int al = 0; al < D - 1; ++al) {
-                        float p, pe, sn, se;
-                        two_prod(w[jj][al], du, p, pe);
-                        two_sum(gh[al][i], p, sn, se);
-                        gh[al][i] = sn;
-                        ge[al][i] = __fadd_rn(ge[al][i], __fadd_rn(pe, se));
-                    }
-                }
-            }
-        }
-        // combine the group's partial sums; every lane of the group ends with the same values
-        #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1)
-            #pragma unroll
-            for (int al = 0; al < D - 1; ++al)
-                #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const float oh = __shfl_xor_sync(gm, gh[al][i], o), oe = __shfl_xor_sync(gm, ge[al][i], o);
-                    float sn, se;
-                    two_sum(gh[al][i], oh, sn, se);
-                    gh[al][i] = sn;
-                    ge[al][i] = __fadd_rn(__fadd_rn(ge[al][i], oe), se);
-                }
-        float gg[D - 1][D];
-        #pragma unroll
-        for (int al = 0; al < D - 1; ++al)
-            #pragma unroll
-            for (int i = 0; i < D; ++i) gg[al][i] = __fadd_rn(gh[al][i], ge[al][i]);
         float E[D * D];
         frame_defect<D>(N, t, E);
         float tinf = 0.0f;
@@ -245,9 +262,9 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
         for (int i = 0; i < D; ++i) tinf = fmaxf(tinf, fabsf(val[i]));
         // Newton on hh with the analytic Jacobian, from the previous step's image.  Until |R| <=
         // 2e-6 (mu + lambda + |T|) a halving line search (rejecting det F_b <= 0) secures decrease;
-        // past that, full steps refine while |R| still falls (quadratic convergence reaches the FP32
-        // rounding level of P N - T in one or two), and the first step that does not lower |R| ends
-        // the iteration.  |R| above 2e-6 (mu + lambda + |T|) at the end is a failed inversion.
+        // then at most two full steps refine while |R| still falls (quadratic convergence reaches the
+        // FP32 rounding level of P N - T), and a step that does not lower |R| ends the iteration.
+        // |R| above 2e-6 (mu + lambda + |T|) at the end is a failed inversion.
         const float scale = mu + lam + tinf;
         float hh[D], R[D], Jq[D * D];
         #pragma unroll
@@ -258,6 +275,7 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
             for (int i = 0; i < D; ++i) hh[i] = 0.0f;
             ok = traction_rq<D>(E, hh, N, gg, t, val, mu, lam, R, Jq);
         }
+        int refine = 0;
         #pragma unroll 1
         for (int it = 0; ok && it < 16; ++it) {
             float rinf = 0.0f, r2 = 0.0f;
@@ -265,6 +283,8 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
             for (int i = 0; i < D; ++i) { rinf = fmaxf(rinf, fabsf(R[i])); r2 += R[i] * R[i]; }
             if (!isfinite(r2)) { ok = false; break; }
             if (r2 == 0.0f) break;
+            const bool near = rinf <= 2e-6f * scale;
+            if (near && refine++ == 2) break;
             float mR[D], dh[D];
             #pragma unroll
             for (int i = 0; i < D; ++i) mR[i] = -R[i];
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
             float al = 1.0f;
             bool acc = false;
             float ht[D], Rt[D], Jt[D * D];
-            const int tries = rinf <= 2e-6f * scale ? 1 : 20;  // refinement: the full step only
+            const int tries = near ? 1 : 20;  // refinement: the full step only
             #pragma unroll 1
             for (int ls = 0; ls < tries; ++ls) {
                 #pragma unroll
@@ -295,10 +315,10 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
         #pragma unroll
         for (int i = 0; i < D; ++i) rinf = fmaxf(rinf, fabsf(R[i]));
         if (!(ok && rinf <= 2e-6f * scale)) {
-            if (r == 0) set_status(a.status, kStNewton);
+            set_status(a.status, kStNewton);
             #pragma unroll
             for (int i = 0; i < D; ++i) hh[i] = a.L.h[3 * l + i];
-        } else if (r == 0) {
+        } else {
             #pragma unroll
             for (int i = 0; i < D; ++i) a.L.h[3 * l + i] = hh[i];
         }
@@ -315,22 +335,16 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
     // interpolated pair relation for the incoming population f_{c^1}(m) of the next gather:
     // D_b = diag(-I, I) for Dirichlet, diag(I, -I) for Neumann links
     const bool neu = tb.kind != 0;
+    float Rk[K];
     #pragma unroll
-    for (int cc = 0; cc < KC; ++cc) {
-        const int k = r + cc * G;
-        if (k >= K) break;
-        float Sk = S[0];
-        #pragma unroll
-        for (int kk = 1; kk < K; ++kk)
-            if (kk == k) Sk = S[kk];
+    for (int k = 0; k < K; ++k) {
         const float Dk = ((k < D) == neu) ? 1.0f : -1.0f;
-        float Rk;
         if (eta >= 0.5f)
-            Rk = (Dk * fo[cc] + Sk) / (2.0f * eta) + (1.0f - 1.0f / (2.0f * eta)) * fi[cc];
+            Rk[k] = (Dk * fo[k] + S[k]) / (2.0f * eta) + (1.0f - 1.0f / (2.0f * eta)) * fi[k];
         else
-            Rk = Dk * (2.0f * eta * fo[cc] + (1.0f - 2.0f * eta) * fu[cc]) + Sk;
-        a.L.rec[l * K + k] = Rk;
+            Rk[k] = Dk * (2.0f * eta * fo[k] + (1.0f - 2.0f * eta) * fu[k]) + S[k];
     }
+    vstore<K>(a.L.rec + l * K, Rk);
 }
 
 }  // namespace tlv

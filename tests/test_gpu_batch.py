@@ -42,11 +42,10 @@ def _packed_run(packed, precision):
     return v, F, u, act
 
 
-# FP32: F within 1e-5; v within 5e-5, the level the FP32 traction inversion allows: its Newton
-# stops at |R| <= 2e-6 (mu + lambda + |T|), about 3e-5 for these materials, and the fast ramp
-# keeps the traction-free holes' sources in every step's velocity
+# FP32: v and F within 1e-5 (measured: v 1.1e-6, F 4.4e-8 at worst over the specimens; the FP32
+# traction inversion refines to the rounding level of its residual)
 @pytest.mark.parametrize("precision,tol", [("fp64", {"v": 1e-12, "F": 1e-12, "u": 1e-12}),
-                                           ("fp32", {"v": 5e-5, "F": 1e-5})])
+                                           ("fp32", {"v": 1e-5, "F": 1e-5})])
 def test_packed_specimens_match_the_oracle_alone(small_batch, precision, tol):
     import oracle
     packed, specs = small_batch

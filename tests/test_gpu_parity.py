@@ -156,3 +156,71 @@ def test_sampled_level_set_matches_oracle(builder, N, steps, prec):
         _check64(errs, sg, so)
     else:
         assert errs["v"] < TOL32 and errs["F"] < TOL32, errs
+
+
+# ---- the stated configurations at their full length ----------------------------------------------
+# Unit roundoff ratio of the two forms: FP32 (2^-24) over FP64 (2^-53).
+ROUNDOFF_RATIO = 2.0 ** 29
+
+
+@pytest.fixture(scope="module")
+def oracle_threads():
+    import oracle
+    return oracle.set_threads(0)
+
+
+def _full_length(p, steps):
+    import oracle
+    from parity import run_gpu
+    o = oracle.Oracle(p).set_initial()
+    o.step(steps)
+    ref = o.fields()
+    act = o.active_mask()
+    D = p.dim
+    eye = np.eye(D).reshape(-1)[:, None]
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim, g, st = run_gpu(p, steps, prec)
+        sim.close()
+        assert st == 0
+        e = {k: rel_l2(a, b, act) for k, a, b in zip("vFu", g, ref)}
+        e["F-I"] = np.linalg.norm(g[1][:, act] - ref[1][:, act]) / np.linalg.norm(ref[1][:, act] - eye)
+        out[prec] = e
+    return out
+
+
+def test_shell_64_full_length_against_oracle(oracle_threads):
+    """The 64^3 copy of the 3D shell workload over its full 4000 steps (t = 3.125, past the ramp)
+    at the omega its full-length runs use (1.5): FP64 within 1e-12 and FP32 within 1e-5 of the
+    oracle on v and F."""
+    e = _full_length(I.shell_3d(64, omega=1.5), 4000)
+    print(f"shell 64^3 omega 1.5, 4000 steps: {e}")
+    assert all(e["fp64"][k] < TOL64 for k in ("v", "F", "u"))
+    assert e["fp32"]["v"] < TOL32 and e["fp32"]["F"] < TOL32
+
+
+def test_shell_64_full_length_omega_1_8_at_the_rounding_floor(oracle_threads):
+    """The same at the paper's omega = 1.8, where the relaxed shell keeps a projection cycle with a
+    residual velocity (v_rms 2e-3) small against the populations it is summed from (the v rows carry
+    the +-(D/c) P/(2D) fluxes, about 0.05): the cycle accumulates rounding noise into v.  The FP64
+    form shows it against the oracle (its unit-level differences grow to about 7e-13 in v), and the
+    FP32 form's v error is that same amplification of its own roundoff: it must not exceed the FP64
+    form's error scaled by the roundoff ratio 2^29 (measured 1.1e-4 against a bound near 3.9e-4).
+    F stays within 1e-5."""
+    e = _full_length(I.shell_3d(64), 4000)
+    print(f"shell 64^3 omega 1.8, 4000 steps: {e}")
+    assert all(e["fp64"][k] < TOL64 for k in ("v", "F", "u"))
+    assert e["fp32"]["F"] < TOL32
+    assert e["fp32"]["v"] <= ROUNDOFF_RATIO * e["fp64"]["v"]
+
+
+def test_annulus_128_full_length_against_oracle(oracle_threads):
+    """The 128^2 copy of the 2D annulus workload over its full length (6250 steps, the ramp's five
+    times): FP64 within 1e-12; FP32 F within 1e-5, and its v -- the residual velocity of the
+    projection cycle, as for the shell -- within the FP64 form's error scaled by 2^29."""
+    p = I.annulus_radial_2d(128)
+    e = _full_length(p, p.steps)
+    print(f"annulus 128^2, {p.steps} steps: {e}")
+    assert all(e["fp64"][k] < TOL64 for k in ("v", "F", "u"))
+    assert e["fp32"]["F"] < TOL32
+    assert e["fp32"]["v"] <= ROUNDOFF_RATIO * e["fp64"]["v"]
