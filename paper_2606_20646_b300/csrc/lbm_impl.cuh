@@ -419,9 +419,11 @@ template <typename real, int D, typename pop = real> struct Impl {
                                       (long long)h->box.ny * h->box.nz, &h->tma_maps[j]);
             }
             if (ok)
-                ok = fused_attr<1>() && fused_attr<2>() && fused_attr<4>() &&
+                ok = fused_attr<1>() && fused_attr<2>() && fused_attr<4>() && fused_attr<1, true>() &&
                      cudaFuncSetAttribute(k_gather_moments_tma<D, pop>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
-                         cudaSuccess;
+                         cudaSuccess &&
+                     cudaFuncSetAttribute(k_gather_moments_tma<D, pop, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          100) == cudaSuccess;
             if (ok && h->opt.adjoint && kPlainPop) {
                 h->adj_maps_ok = true;
                 for (int j = 0; j < 2; ++j) {
@@ -439,15 +441,16 @@ template <typename real, int D, typename pop = real> struct Impl {
     }
 
     template <int NW> static int fused_smem() { return NW * (TmaLayout<D, sizeof(pop)>::stage_bytes + 8); }
-    template <int NW> static bool fused_attr() {
-        return cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    template <int NW, bool REPAIR = false> static bool fused_attr() {
+        return cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW, REPAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     fused_smem<NW>()) == cudaSuccess &&
-               cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                    100) == cudaSuccess;
+               cudaFuncSetAttribute(k_stream_collide_tma<D, pop, NW, REPAIR>,
+                                    cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
     }
     // the fused kernel with the handle's windows per warp
     template <int NW> static void launch_fused_nw(lbm_handle *h, const StepArgs<float> &a) {
-        k_stream_collide_tma<D, pop, NW><<<grid_for(h->nseg, NW), 32, fused_smem<NW>(), h->stream>>>(a, *maps_of(h, h->fA));
+        k_stream_collide_tma<D, pop, NW><<<grid_for(h->nseg, NW), 32, fused_smem<NW>(), h->stream>>>(a, *maps_of(h, h->fA),
+                                                                                                  RepairArgs{});
     }
     static void launch_fused(lbm_handle *h, const StepArgs<float> &a) {
         const int nw = h->tune_nw ? h->tune_nw : kTmaWindows<pop>;
@@ -644,6 +647,7 @@ template <typename real, int D, typename pop = real> struct Impl {
             StepArgs<real> a = step_args(h);
             const bool proj = h->n_neu > 0 && h->opt.proj_every > 0 && (h->step % h->opt.proj_every) == 0;
             const unsigned g = grid_for(h->nseg, 4);
+            bool post_in_B = true;  // where this step leaves the post-collision populations
             if (!proj) {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 0);
@@ -661,10 +665,16 @@ template <typename real, int D, typename pop = real> struct Impl {
                 NvtxRange prange("projection step");
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 2);
+                // bulk-copy path (FP32 forms after the first step): the gather stores the moments
+                // only, the repair re-gathers f^n from fA and writes f*^n into fB (a regular step's
+                // buffers); otherwise the gather stores f^n into fB and the plain repair writes f*^n
+                // into fA
+                bool staged = false;
+                if constexpr (sizeof(real) == 4) staged = h->tma_ok && h->phase == 1;
                 if (h->phase == 0) k_gather_moments<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
                 else if constexpr (sizeof(real) == 4) {
-                    if (h->tma_ok)
-                        k_gather_moments_tma<D, pop><<<g, 128, TmaLayout<D, sizeof(pop)>::block_bytes(4), h->stream>>>(
+                    if (staged)
+                        k_gather_moments_tma<D, pop, false><<<g, 128, TmaLayout<D, sizeof(pop)>::block_bytes(4), h->stream>>>(
                             a, *maps_of(h, h->fA));
                     else
                         k_gather_moments<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
@@ -674,13 +684,29 @@ template <typename real, int D, typename pop = real> struct Impl {
                 real *d = nullptr;
                 int rc = solve(h, t, static_cast<const real *>(h->u0), &d);
                 if (rc) return rc;
-                // out of place: f^n (from the gather, in fB) in, f*^n out into fA, whose f*^{n-1} the
-                // gather has consumed; the buffers then need no swap
-                StepArgs<real> ar = a;
-                ar.fsrc = static_cast<const real *>(h->fB);
-                ar.fdst = static_cast<real *>(h->fA);
-                k_repair_collide<real, D, pop><<<g, 128, 0, h->stream>>>(ar, static_cast<const real *>(h->u0), d, h->mean,
-                                                                     h->opt.theta_F, static_cast<real *>(h->u1));
+                if constexpr (sizeof(real) == 4) {
+                    if (staged) {
+                        RepairArgs rp;
+                        rp.u0 = static_cast<const float *>(h->u0);
+                        rp.dc = d;
+                        rp.mean = h->mean;
+                        rp.theta = (float)h->opt.theta_F;
+                        rp.u1 = static_cast<float *>(h->u1);
+                        k_stream_collide_tma<D, pop, 1, true><<<grid_for(h->nseg, 1), 32, fused_smem<1>(), h->stream>>>(
+                            a, *maps_of(h, h->fA), rp);
+                    }
+                }
+                if (!staged) {
+                    // out of place: f^n (from the gather, in fB) in, f*^n out into fA, whose f*^{n-1}
+                    // the gather has consumed
+                    StepArgs<real> ar = a;
+                    ar.fsrc = static_cast<const real *>(h->fB);
+                    ar.fdst = static_cast<real *>(h->fA);
+                    k_repair_collide<real, D, pop><<<g, 128, 0, h->stream>>>(ar, static_cast<const real *>(h->u0), d,
+                                                                         h->mean, h->opt.theta_F,
+                                                                         static_cast<real *>(h->u1));
+                }
+                post_in_B = staged;
                 h->launches++;
                 CKL();
                 rc = solve(h, t, static_cast<const real *>(h->u1), &d);
@@ -690,8 +716,9 @@ template <typename real, int D, typename pop = real> struct Impl {
                 CKL();
                 if (h->timing) timing_end(h, ep);
             }
-            // the post-collision state: fB after a regular step, fA after a projection step
-            if (!proj) std::swap(h->fA, h->fB);
+            // the post-collision state: fB after a regular step or a bulk-copy projection step, fA
+            // after a plain-load projection step
+            if (post_in_B) std::swap(h->fA, h->fB);
             int rc = cutlinks(h, t);
             if (rc) return rc;
             h->phase = 1;

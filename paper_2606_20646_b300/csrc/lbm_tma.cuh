@@ -263,6 +263,126 @@ __device__ __forceinline__ void collide_staged(const StepArgs<float> &a, char *w
     }
 }
 
+// Operands of the population repair on a projection step (Eqs. projection-compatible-F,
+// projection-F-repair-weight, projection-population-repair): u^n and the first solve's correction.
+struct RepairArgs {
+    const float *u0;      // u^n as (hi, lo) plane pairs
+    const float *dc;      // correction d of the first solve, node-major (kDV values per node)
+    const double *mean;   // its gauge shift
+    float theta;          // repair weight theta_F
+    float *u1;            // out: u^n after the first projection, (hi, lo) pairs
+};
+
+// The repair step of a projection step with the populations re-gathered by the bulk copies (FP32):
+// from the staged f^n, the recovery (as collide_staged), F^c from u^n + d (central differences, one
+// sided where a neighbour is inactive), F^r, the populations translated by f^eq(v, F^r) - f^eq(v, F),
+// the collision, u*^{n+1}; F^r - I stored for the second solve.  The same arithmetic as the
+// plain-load k_repair_collide, from the same staged values.
+template <int D, typename pop = float>
+__device__ __forceinline__ void repair_staged(const StepArgs<float> &a, const RepairArgs &rp, char *wsm, int node,
+                                              int x, int y, int z, int lane, uint8_t fl, long long l0, bool act,
+                                              float mu, float lam) {
+    constexpr int K = D + D * D, Q = 2 * D;
+    constexpr long long DV = kDV<D>;
+    const long long Pn = a.b.npad;
+    if (!act) {  // whole sectors: zeros for an inactive node's slots
+        #pragma unroll
+        for (int j = 0; j < Q * K; ++j) pop_st<float, pop>(a.fdst, (long long)j * Pn + node, 0.0f);
+        return;
+    }
+    float S[K];
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float s = staged<D, pop>(wsm, 0, k, lane);
+        #pragma unroll
+        for (int q = 1; q < Q; ++q) s += staged<D, pop>(wsm, q, k, lane);
+        S[k] = s;
+    }
+    const float hdt = 0.5f * a.dt;
+    const float inv_damp = 1.0f / (1.0f + hdt * a.gamma);
+    float v[D], G[D * D], Gr[D * D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = (S[i] + hdt * a.bf[i]) * inv_damp;
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) G[k] = S[D + k];
+    const unsigned cut = fl & kCutMask;
+    #pragma unroll
+    for (int A = 0; A < D; ++A) {
+        const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
+        int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
+        int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
+        TLV_BOUND(lp, Pn, a.status);
+        TLV_BOUND(lm, Pn, a.status);
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float ho = rp.u0[i * Pn + node], lo_ = rp.u0[(D + i) * Pn + node];
+            const float dp = ((rp.u0[i * Pn + lp] - ho) + (rp.u0[(D + i) * Pn + lp] - lo_)) +
+                             (rp.dc[DV * lp + i] - rp.dc[DV * node + i]);
+            const float dm = ((ho - rp.u0[i * Pn + lm]) + (lo_ - rp.u0[(D + i) * Pn + lm])) +
+                             (rp.dc[DV * node + i] - rp.dc[DV * lm + i]);
+            const float inv = 1.0f / (float)a.b.dx;
+            float Gc;
+            if (ap && am) Gc = 0.5f * (dp + dm) * inv;
+            else if (ap) Gc = dp * inv;
+            else if (am) Gc = dm * inv;
+            else Gc = G[i * D + A];
+            Gr[i * D + A] = (1.0f - rp.theta) * G[i * D + A] + rp.theta * Gc;
+        }
+    }
+    float Pold[D * D], Pk[D * D], Fit[D * D];
+    piola_g<float, D>(G, mu, lam, Pold, Fit);
+    const float J = piola_g<float, D>(Gr, mu, lam, Pk, Fit);
+    float chk = J;
+    #pragma unroll
+    for (int i = 0; i < D; ++i) chk += v[i];
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) chk += Pk[k];
+    if (!(J > 0.0f) || !isfinite(chk))
+        set_status(a.status, (J > 0.0f ? 0 : kStJacobian) | (isfinite(chk) ? 0 : kStNonfinite));
+    const float Dc = float(D) / a.c;
+    const float src = a.dt * (2.0f - a.omega) * (1.0f / float(4 * D));
+    float B[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) B[i] = a.bf[i] - a.gamma * v[i];
+    #pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int A = q >> 1;
+        const float s = (q & 1) ? -1.0f : 1.0f;
+        float out[K];
+        #pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float fv = staged<D, pop>(wsm, q, k, lane);
+            float feq;
+            if (k < D) {
+                const int i = k;
+                feq = div2D<float, D>(v[i] - s * Dc * Pk[i * D + A]);
+                fv = fv - div2D<float, D>(s * Dc * (Pk[i * D + A] - Pold[i * D + A]));
+            } else {
+                const int i = (k - D) / D, Bc = (k - D) % D;
+                const float vs = (A == Bc) ? s * Dc * v[i] : 0.0f;
+                feq = (A == Bc) ? div2D<float, D>(Gr[i * D + Bc] - vs) : div2D<float, D>(Gr[i * D + Bc]);
+                fv = fv + div2D<float, D>(Gr[i * D + Bc] - G[i * D + Bc]);
+            }
+            out[k] = fv + a.omega * (feq - fv) + ((k < D) ? src * B[k] : 0.0f);
+        }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) pop_st<float, pop>(a.fdst, (long long)(q * K + k) * Pn + node, out[k]);
+        if (cut) keep_link_values<float, K>(a.lfo, l0, cut, q, out, a.ncut, a.status);
+    }
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float hi = rp.u0[i * Pn + node], lo = rp.u0[(D + i) * Pn + node];
+        df_add(hi, lo, rp.dc[DV * node + i] - (float)rp.mean[i]);  // u^n after the first projection
+        rp.u1[i * Pn + node] = hi;
+        rp.u1[(D + i) * Pn + node] = lo;
+        df_add(hi, lo, hdt * v[i]);  // u*^{n+1}
+        a.ustar[i * Pn + node] = hi;
+        a.ustar[(D + i) * Pn + node] = lo;
+    }
+    #pragma unroll
+    for (int k = 0; k < D * D; ++k) a.Gst[k * Pn + node] = Gr[k];
+}
+
 // TMA start coordinates of a segment: element x of every population box, then the flag box
 struct SegStarts {
     int2 sg;
@@ -327,9 +447,9 @@ __device__ __forceinline__ void issue_window(const StepArgs<float> &a, const Tma
 // written sector costs the memory system a read of the rest).  Nothing reads an inactive node's
 // populations or u*: pulls across cut links are replaced by the closure.  Lanes past the row end
 // belong to the next row and store nothing.
-template <int D, typename pop>
-__device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *cur, int2 sg, int lane, long long l0pre,
-                                               int gpre) {
+template <int D, typename pop, bool REPAIR>
+__device__ __forceinline__ void collide_window(const StepArgs<float> &a, const RepairArgs &rp, char *cur, int2 sg,
+                                               int lane, long long l0pre, int gpre) {
     using L = TmaLayout<D, sizeof(pop)>;
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
@@ -344,14 +464,17 @@ __device__ __forceinline__ void collide_window(const StepArgs<float> &a, char *c
     float mu = a.mtab ? a.mtab[2 * gpre] : a.mu;
     const float lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
     if (a.mu_field) mu = a.mu_field[node];
-    collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
+    if constexpr (REPAIR) repair_staged<D, pop>(a, rp, cur, node, x, sg.y % a.b.ny, sg.y / a.b.ny, lane, fl, l0, act, mu, lam);
+    else collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 
 // K3 with TMA staging (FP32 arithmetic): one warp per block, NW 32-node windows per warp.  Lane 0 issues the bulk copies of the warp's windows; every lane waits on each window's
 // barrier (bounded) before computing it, so no warp can leave while one of its copies is in flight.
-template <int D, typename pop = float, int NW = kTmaWindows<pop>>
-__global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<float> a,
-                                                              const __grid_constant__ TmaMaps maps) {
+// REPAIR: the repair step of a projection step (repair_staged) instead of the plain collision.
+template <int D, typename pop = float, int NW = kTmaWindows<pop>, bool REPAIR = false>
+__global__ void __launch_bounds__(32, REPAIR ? 12 : 16) k_stream_collide_tma(const StepArgs<float> a,
+                                                              const __grid_constant__ TmaMaps maps,
+                                                              const RepairArgs rp) {
     using L = TmaLayout<D, sizeof(pop)>;
     extern __shared__ __align__(128) char smem[];
     const int lane = threadIdx.x & 31;
@@ -387,12 +510,13 @@ __global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<fl
             for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
             return;
         }
-        collide_window<D, pop>(a, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w]);
+        collide_window<D, pop, REPAIR>(a, rp, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w]);
     }
 }
 
 // projection steps, part 1, with TMA staging (FP32)
-template <int D, typename pop = float>
+// WRITE_F: also store the gathered f^n (for the plain-load repair); the staged repair re-gathers it
+template <int D, typename pop = float, bool WRITE_F = true>
 __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps) {
     constexpr int K = D + D * D, Q = 2 * D;
     using L = TmaLayout<D, sizeof(pop)>;
@@ -412,17 +536,19 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     tma_closure<D, pop>(a, wsm, node, x, lane, fl & kCutMask, (fl & kCutMask) ? __ldg(a.lstart + node) : 0);
     const long long P = a.b.npad;
     float v[D];
+    const float hdt = 0.5f * a.dt;
+    const float inv_damp = 1.0f / (1.0f + hdt * a.gamma);
     #pragma unroll
     for (int k = 0; k < K; ++k) {
         float s = staged<D, pop>(wsm, 0, k, lane);
-        pop_st<float, pop>(a.fdst, (long long)(0 * K + k) * P + node, s);
+        if (WRITE_F) pop_st<float, pop>(a.fdst, (long long)(0 * K + k) * P + node, s);
         #pragma unroll
         for (int q = 1; q < Q; ++q) {
             const float fq = staged<D, pop>(wsm, q, k, lane);
-            pop_st<float, pop>(a.fdst, (long long)(q * K + k) * P + node, fq);
+            if (WRITE_F) pop_st<float, pop>(a.fdst, (long long)(q * K + k) * P + node, fq);
             s += fq;
         }
-        if (k < D) v[k] = (s + 0.5f * a.dt * a.bf[k]) / (1.0f + 0.5f * a.dt * a.gamma);
+        if (k < D) v[k] = (s + hdt * a.bf[k]) * inv_damp;  // as collide_staged and repair_staged
         else a.Gst[(k - D) * P + node] = s;
     }
     #pragma unroll
