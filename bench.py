@@ -104,22 +104,20 @@ class Clocks:
 
 
 # DRAM traffic of the fused kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# of one launch on this workload), stored with the SHA-256 of the kernel sources it was measured on;
-# reported only while those sources are unchanged (null otherwise).
+# of one launch) on the 128^3 copy of the workload, stored with the SHA-256 of the kernel sources it
+# was measured on and reported only while those sources are unchanged (null otherwise).  Each
+# 32-node window of the launch stages and stores whole boxes, so the traffic is scaled to the
+# timed box by its number of windows (segments).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = {"sources_sha256": "c68cf9fb07fce29d5ac887c1b9bce4b3c9d9efea04fec6f1cd103da2b9d60786",
-                   "bytes_per_launch": 2527338752 + 2096491520, "n": 256,
-                   "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
-# the same for the BF16-storage fused kernel (two windows per warp) on the same workload
-BF16_TRAFFIC_CAPTURE = {"sources_sha256": "c68cf9fb07fce29d5ac887c1b9bce4b3c9d9efea04fec6f1cd103da2b9d60786",
-                        "bytes_per_launch": 1522339840 + 1148926464, "n": 256,
-                        "summary": "profiles/k_stream_collide_tma_bf16_shell_3d.md"}
-# the same for the reverse step on the clamped cube (128^3)
+TRAFFIC_CAPTURE = None
+# the same for the BF16-storage fused kernel (two windows per warp)
+BF16_TRAFFIC_CAPTURE = None
+# the same for the reverse step on the clamped cube (128^3, the timed size itself)
 ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
                "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
 ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "81cfad42824ec7d180295d5d7cb514a1578a4da45d12204db29b12a3f77c8267",
-                       "bytes_per_launch": 741803264 + 574143488, "n": 128,
+                       "bytes_per_launch": 741803264 + 574143488, "windows": None,
                        "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
@@ -132,10 +130,14 @@ def kernel_sources_hash(sources=KERNEL_SOURCES):
     return h.hexdigest()
 
 
-def captured_traffic(n, cap=TRAFFIC_CAPTURE, sources=KERNEL_SOURCES):
-    if not cap or cap.get("n") != n or cap.get("sources_sha256") != kernel_sources_hash(sources):
+def captured_traffic(windows, cap=TRAFFIC_CAPTURE, sources=KERNEL_SOURCES):
+    """Captured bytes per launch, scaled from the captured launch's windows to `windows` (None: the
+    capture ran the timed size itself); None when there is no capture of the current sources."""
+    if not cap or cap.get("sources_sha256") != kernel_sources_hash(sources):
         return None
-    return cap["bytes_per_launch"]
+    if cap.get("windows") is None:
+        return cap["bytes_per_launch"]
+    return int(round(cap["bytes_per_launch"] * windows / cap["windows"]))
 
 
 def bytes_per_node(D, real_size):
@@ -350,7 +352,7 @@ def run_ours(args, world, rank, local):
              "achieved_GBps": round(lb / (avg_cut / 1e3) / 1e9, 1) if avg_cut > 0 else None,
              "frac": round(lb / (avg_cut / 1e3) / 1e9 / peak, 4) if avg_cut > 0 else None}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": captured_traffic(args.n),
+                "frac": round(achieved / peak, 4), "traffic": captured_traffic(info["n_segments"]),
                 "kernel": "k_stream_collide_tma<3>", "bytes_per_launch": nact * bpn,
                 "bytes_per_node": bpn, "avg_launch_ms": round(avg_sc, 4), "peak_kind": peak_kind,
                 "frac_of_bytes_moved": round(achieved_moved / peak, 4),
@@ -407,7 +409,7 @@ def run_ours(args, world, rank, local):
                 "ms_per_step": round(msb / K, 4), "dtype": "bf16 storage, f32 arithmetic",
                 "stream_collide_ms": round(avgb, 4), "bytes_per_node": bpn,
                 "stream_collide_GBps": round(gbb, 1), "frac": round(gbb / peak, 4), "peak_kind": peak_kind,
-                "traffic": captured_traffic(args.n, BF16_TRAFFIC_CAPTURE) if tune_b["windows_per_warp"] == 2 else None,
+                "traffic": captured_traffic(info["n_segments"], BF16_TRAFFIC_CAPTURE) if tune_b["windows_per_warp"] == 2 else None,
                 "error_vs_fp64": {"workload": "shell_3d_128 at t = 1 (640 steps)", "v": rel(vb, vd),
                                   "F_minus_I": rel(Fb - eye, Fd - eye), "u": rel(ub, ud)},
                 "tuning": tune_b, "device_status": stb}
@@ -549,7 +551,7 @@ def run_ours(args, world, rank, local):
         kernels = {"reverse": {"kernel": "k_adj_step_tma<3>", "ms_per_launch": round(ms_rev, 4),
                                "bytes_per_node": brev, "achieved_GBps": round(gb_rev, 1),
                                "frac": round(gb_rev / peak, 4),
-                               "traffic": captured_traffic(args.adj_n, ADJ_TRAFFIC_CAPTURE, ADJ_SOURCES)},
+                               "traffic": captured_traffic(None, ADJ_TRAFFIC_CAPTURE, ADJ_SOURCES) if args.adj_n == 128 else None},
                    "recompute": {"kernel": "k_stream_collide_tma<3> recording F", "ms_per_launch": round(ms_rec, 4),
                                  "bytes_per_node": brec, "achieved_GBps": round(gb_rec, 1),
                                  "frac": round(gb_rec / peak, 4)},

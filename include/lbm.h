@@ -291,7 +291,7 @@ int lbm_step_graph(lbm_handle *h, int nsteps);
 typedef struct lbm_tuning {
     int windows_per_warp; /* fused kernel (bulk-copy forms): 32-node windows one warp stages at
                              once, 1, 2 or 4 (default 1 for FP32, 2 for BF16S)                  */
-    int jacobi_segments;  /* projection sweeps: 32-node segments per warp, 1, 2 or 4 (default 2) */
+    int jacobi_segments;  /* projection sweeps: 32-node segments per warp, 1, 2 or 4 (default 1) */
     int link_block;       /* link kernel: threads per block, 64, 128 or 256 (default 128)        */
     int candidates;       /* lbm_autotune: configurations it timed                              */
     double ms_per_step;   /* lbm_autotune: the chosen configuration's time per step             */

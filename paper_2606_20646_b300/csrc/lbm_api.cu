@@ -534,7 +534,7 @@ int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t) {
     if (!h || !t) return LBM_ERR_ARG;
     std::memset(t, 0, sizeof(*t));
     t->windows_per_warp = h->tma_ok ? (h->tune_nw ? h->tune_nw : (h->pop_size == 2 ? 2 : 1)) : 0;
-    t->jacobi_segments = h->tune_jseg ? h->tune_jseg : 2;
+    t->jacobi_segments = h->tune_jseg ? h->tune_jseg : 1;
     t->link_block = h->tune_lblock ? h->tune_lblock : 128;
     return LBM_OK;
 }
@@ -576,7 +576,7 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     int *const shape[3] = {&h->tune_nw, &h->tune_jseg, &h->tune_lblock};
     const int saved[3] = {h->tune_nw, h->tune_jseg, h->tune_lblock};
     const int cand[3][3] = {{1, 2, 4}, {1, 2, 4}, {64, 128, 256}};
-    const int dflt[3] = {h->pop_size == 2 ? 2 : 1, 2, 128};
+    const int dflt[3] = {h->pop_size == 2 ? 2 : 1, 1, 128};
     const bool used[3] = {h->tma_ok, h->n_neu > 0 && h->opt.proj_every > 0, h->n_cut > 0};
     for (int c = 0; c < 3; ++c) *shape[c] = 0;
     double best = 0.0;

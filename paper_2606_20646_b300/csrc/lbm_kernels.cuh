@@ -1648,7 +1648,7 @@ __global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
     st_vec<4, real>(a.resid + 4 * (long long)node, out);
 }
 
-constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep (default; lbm_autotune may pick 1 or 4)
+constexpr int kJacobiSegs = 1;  // segments per warp in a Jacobi sweep (default; lbm_autotune may pick 2 or 4)
 
 // One damped-Jacobi sweep on the correction d (d = 0 before the first sweep: din == nullptr),
 //   d'_m = (1 - beta) d_m + beta / deg_m (r_m + sum over active axis neighbours l of d_l),
@@ -1660,27 +1660,27 @@ constexpr int kJacobiSegs = 2;  // segments per warp in a Jacobi sweep (default;
 // written.
 template <typename real, int D, int S, bool shx>
 __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const real *__restrict__ din,
-                                                real *__restrict__ dout, int s0) {
+                                                real *__restrict__ dout, int s0, const int2 (&sgs)[S]) {
     constexpr int Q = 2 * D, V = kDV<D>;
     const int lane = threadIdx.x & 31;
     const long long P = a.b.npad;
     const real beta = (real)a.beta;
     const bool per = a.b.per[0] | a.b.per[1] | a.b.per[2];
-    long long node[S], ln[S][Q];
+    int node[S], ln[S][Q];  // node indices fit 32 bits (boxes below 2^31 nodes)
     bool in[S];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
         const bool seg_ok = s0 + j < a.nseg;
-        const int2 sg = seg_ok ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
+        const int2 sg = sgs[j];
         const int x = sg.x - sg.y * a.b.nx + lane;
         in[j] = seg_ok && x < a.b.nx;
-        const long long nd = in[j] ? sg.x + lane : 0;  // lanes outside the row read node 0, unused
+        const int nd = in[j] ? sg.x + lane : 0;  // lanes outside the row read node 0, unused
         node[j] = nd;
         const int y = per ? sg.y % a.b.ny : 0, z = per ? sg.y / a.b.ny : 0;
         #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            long long l = nbr(a.b, (int)nd, x, y, z, q);
-            ln[j][q] = l < 0 ? 0 : (l >= P ? P - 1 : l);  // only inactive nodes can point outside
+            const int l = nbr(a.b, nd, x, y, z, q);
+            ln[j][q] = l < 0 ? 0 : (l >= P ? (int)(P - 1) : l);  // only inactive nodes can point outside
         }
     }
     real r[S][4], dold[S][V], nb[S][Q][V];
@@ -1688,18 +1688,18 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
     #pragma unroll
     for (int j = 0; j < S; ++j) {
         cut[j] = __ldg(a.flags + node[j]) & kCutMask;
-        ld_vec<4, real>(a.resid + 4 * node[j], r[j]);
+        ld_vec<4, real>(a.resid + 4LL * node[j], r[j]);
         if (din) {
-            ld_vec<V, real>(din + V * node[j], dold[j]);
+            ld_vec<V, real>(din + (long long)V * node[j], dold[j]);
             #pragma unroll
             for (int q = 0; q < Q; ++q)
-                if (q >= 2 || !shx) ld_vec<V, real>(din + V * ln[j][q], nb[j][q]);
+                if (q >= 2 || !shx) ld_vec<V, real>(din + (long long)V * ln[j][q], nb[j][q]);
             if constexpr (shx) {
                 // the x neighbours are the neighbouring lanes' own vectors; lane 31 loads node + 1 and
                 // lane 0 node - 1 (the other lanes load their own node again, an L1 hit)
                 real e[V];
-                const long long ie = lane == 31 ? node[j] + 1 : (lane == 0 ? (node[j] > 0 ? node[j] - 1 : 0) : node[j]);
-                ld_vec<V, real>(din + V * ie, e);
+                const int ie = lane == 31 ? node[j] + 1 : (lane == 0 ? (node[j] > 0 ? node[j] - 1 : 0) : node[j]);
+                ld_vec<V, real>(din + (long long)V * ie, e);
                 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const real dn = __shfl_down_sync(0xffffffffu, dold[j][i], 1);
@@ -1731,7 +1731,7 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
             for (int q = 0; q < Q; ++q) acc += ((cut[j] >> q) & 1) ? real(0) : nb[j][q][i];
             out[i] = (real(1) - beta) * dold[j][i] + w * acc;
         }
-        st_vec<V, real>(dout + V * node[j], out);
+        st_vec<V, real>(dout + (long long)V * node[j], out);
     }
 }
 
@@ -1742,8 +1742,21 @@ template <typename real, int D, int S = kJacobiSegs, bool shx = true>
 __global__ void __launch_bounds__(128) k_jacobi(const ProjArgs<real> a, const real *__restrict__ din,
                                                 real *__restrict__ dout) {
     const int stride = gridDim.x * 4 * S;
-    for (int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S; s0 < a.nseg; s0 += stride)
-        jacobi_segments<real, D, S, shx>(a, din, dout, s0);
+    int s0 = (blockIdx.x * 4 + (threadIdx.x >> 5)) * S;
+    // the segment descriptors of the next iteration are loaded while this one's nodes are swept
+    int2 nxt[S];
+    #pragma unroll
+    for (int j = 0; j < S; ++j) nxt[j] = s0 + j < a.nseg ? __ldg(&a.seg[s0 + j]) : make_int2(0, 0);
+    for (; s0 < a.nseg; s0 += stride) {
+        int2 cur[S];
+        #pragma unroll
+        for (int j = 0; j < S; ++j) {
+            cur[j] = nxt[j];
+            const int sn = s0 + stride + j;
+            nxt[j] = sn < a.nseg ? __ldg(&a.seg[sn]) : make_int2(0, 0);
+        }
+        jacobi_segments<real, D, S, shx>(a, din, dout, s0, cur);
+    }
 }
 
 

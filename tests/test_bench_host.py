@@ -38,14 +38,22 @@ def test_algorithmic_bytes_per_node():
 
 def test_traffic_is_reported_only_for_the_captured_sources():
     b = _bench()
-    cap = dict(b.TRAFFIC_CAPTURE)
-    n = cap["n"]
-    good = b.captured_traffic(n, cap, b.KERNEL_SOURCES)
-    assert good in (None, cap["bytes_per_launch"])   # None once the sources have changed
-    assert b.captured_traffic(n + 1, cap, b.KERNEL_SOURCES) is None          # another workload size
+    cur = b.kernel_sources_hash(b.KERNEL_SOURCES)
+    cap = {"sources_sha256": cur, "bytes_per_launch": 1000, "windows": 40}
+    # scaled by windows from the captured launch to the timed one
+    assert b.captured_traffic(40, cap, b.KERNEL_SOURCES) == 1000
+    assert b.captured_traffic(100, cap, b.KERNEL_SOURCES) == 2500
+    # a capture of the timed size itself is reported as it is
+    assert b.captured_traffic(None, dict(cap, windows=None), b.KERNEL_SOURCES) == 1000
     stale = dict(cap, sources_sha256="0" * 64)
-    assert b.captured_traffic(n, stale, b.KERNEL_SOURCES) is None             # other sources
-    assert b.captured_traffic(n, None, b.KERNEL_SOURCES) is None
+    assert b.captured_traffic(40, stale, b.KERNEL_SOURCES) is None            # other sources
+    assert b.captured_traffic(40, None, b.KERNEL_SOURCES) is None
+    # the stored captures are either current or reported as null
+    for c, src in ((b.TRAFFIC_CAPTURE, b.KERNEL_SOURCES), (b.BF16_TRAFFIC_CAPTURE, b.KERNEL_SOURCES),
+                   (b.ADJ_TRAFFIC_CAPTURE, b.ADJ_SOURCES)):
+        if c:
+            got = b.captured_traffic(c.get("windows") or None, c, src)
+            assert got in (None, c["bytes_per_launch"])
     # the hash covers every listed source: dropping one changes it
     assert b.kernel_sources_hash(b.KERNEL_SOURCES[:-1]) != b.kernel_sources_hash(b.KERNEL_SOURCES)
 
