@@ -19,6 +19,7 @@
 
 #include "lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_proj.cuh"
 #include "lbm_tma.cuh"
 #include "lbm_links.cuh"
 #include "lbm_adjoint.cuh"
