@@ -110,14 +110,18 @@ class Clocks:
 # timed box by its number of windows (segments).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = None
+TRAFFIC_CAPTURE = {"sources_sha256": "ce9c50662bb7605bf5952b44143c9bfd144388f7c4e10fd10770fa38797ec17a",
+                   "bytes_per_launch": 374856064 + 265386880, "windows": 30112,
+                   "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
 # the same for the BF16-storage fused kernel (two windows per warp)
-BF16_TRAFFIC_CAPTURE = None
+BF16_TRAFFIC_CAPTURE = {"sources_sha256": "ce9c50662bb7605bf5952b44143c9bfd144388f7c4e10fd10770fa38797ec17a",
+                        "bytes_per_launch": 217926528 + 133869184, "windows": 30112,
+                        "summary": "profiles/k_stream_collide_tma_bf16_shell_3d.md"}
 # the same for the reverse step on the clamped cube (128^3, the timed size itself)
 ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
                "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
-ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "81cfad42824ec7d180295d5d7cb514a1578a4da45d12204db29b12a3f77c8267",
-                       "bytes_per_launch": 741803264 + 574143488, "windows": None,
+ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "1e51edf289d4040ba2929255d36082e21048b9796bf9057604779843ecd92a4e",
+                       "bytes_per_launch": 741835605 + 577194155, "windows": None,
                        "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
@@ -358,7 +362,10 @@ def run_ours(args, world, rank, local):
                 "frac_of_bytes_moved": round(achieved_moved / peak, 4),
                 "bytes_per_node_moved": bytes_per_node(3, 4),
                 "note": "frac counts the method's 601 B per active node; frac_of_bytes_moved counts the "
-                        "625 B this build moves (u* as FP32 hi/lo pairs)"}
+                        "625 B this build moves (u* as FP32 hi/lo pairs); avg_launch_ms is the kernel's time "
+                        "per step (with the overlapped link schedule its two launches, boundary windows "
+                        "then the others beside the link kernels); traffic is the ncu DRAM bytes of one "
+                        "launch over every window of the 128^3 copy, scaled by windows"}
     del sim
     torch.cuda.empty_cache()
 
@@ -627,6 +634,7 @@ def run_ours(args, world, rank, local):
                                        "R_i=0.4 R_o=0.9, mu=1 lambda=5, internal pressure sin^2 ramp, "
                                        "projection every 20 steps",
                            "n_active": nact, "n_cut_links": info["n_cut"], "lsq_entries": info["lsq_entries"],
+                           "n_windows": info["n_segments"], "n_boundary_windows": info["n_boundary_segments"],
                            "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
                            "parallelism": f"replicas x{world}", "tuning": tuning},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},
