@@ -362,10 +362,8 @@ def run_ours(args, world, rank, local):
                 "frac_of_bytes_moved": round(achieved_moved / peak, 4),
                 "bytes_per_node_moved": bytes_per_node(3, 4),
                 "note": "frac counts the method's 601 B per active node; frac_of_bytes_moved counts the "
-                        "625 B this build moves (u* as FP32 hi/lo pairs); avg_launch_ms is the kernel's time "
-                        "per step (with the overlapped link schedule its two launches, boundary windows "
-                        "then the others beside the link kernels); traffic is the ncu DRAM bytes of one "
-                        "launch over every window of the 128^3 copy, scaled by windows"}
+                        "625 B this build moves (u* as FP32 hi/lo pairs); traffic is the ncu DRAM bytes of "
+                        "one launch on the 128^3 copy, scaled by windows"}
     del sim
     torch.cuda.empty_cache()
 
@@ -634,7 +632,7 @@ def run_ours(args, world, rank, local):
                                        "R_i=0.4 R_o=0.9, mu=1 lambda=5, internal pressure sin^2 ramp, "
                                        "projection every 20 steps",
                            "n_active": nact, "n_cut_links": info["n_cut"], "lsq_entries": info["lsq_entries"],
-                           "n_windows": info["n_segments"], "n_boundary_windows": info["n_boundary_segments"],
+                           "n_windows": info["n_segments"],
                            "l2": "no flush: populations (2 x 4.8 GB) are far larger than the 126 MB L2",
                            "parallelism": f"replicas x{world}", "tuning": tuning},
                 "roofline": roofline, "kernel_share_of_step": {k: round(v, 4) for k, v in share.items()},

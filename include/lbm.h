@@ -216,7 +216,6 @@ typedef struct lbm_info {
     size_t geometry_bytes, storage_bytes;
     long long launches;      /* kernels launched by lbm_step since creation */
     long long lsq_entries;   /* total LSQ stencil entries over Neumann links */
-    long long n_boundary_segments; /* windows the link kernels read or feed (LBM_LINKS_OVERLAP) */
 } lbm_info;
 
 typedef struct lbm_kernel_time {
@@ -250,17 +249,15 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *levelset, const lbm_mat
                size_t geometry_bytes, void *cuda_stream, lbm_handle **out);
 
 /* Bytes of solver storage (populations x2, u*, u^n, cut-link records, LSQ
- * weights, projection scratch, partitioned window list, optional host staging). */
+ * weights, projection scratch, optional host staging). */
 int lbm_storage_bytes(const lbm_handle *h, size_t *bytes);
 
 /* Binds the solver storage (>= lbm_storage_bytes, 256-byte aligned) and builds
  * the per-link geometry in FP64 on the GPU: eta by bisection of phi
  * (Eq. cut-link-point), boundary normal (Eq. level-set-normal), boundary id,
  * tangent frame and LSQ tangent-derivative weights (Eq. tangent-derivative-2d,
- * Eq. tangent-image-3d-lsq); sorts the windows into boundary windows and the others
- * (LBM_LINKS_OVERLAP) and, on the first bind, creates the handle's second stream (non-blocking,
- * the highest priority) and two events, which lbm_destroy releases.  Errors: LBM_ERR_STORAGE,
- * LBM_ERR_ARG (a boundary id with no BC), LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
+ * Eq. tangent-image-3d-lsq).  Errors: LBM_ERR_STORAGE, LBM_ERR_ARG (a boundary
+ * id with no BC), LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
 int lbm_bind_storage(lbm_handle *h, void *storage, size_t bytes);
 
 /* Initial state (Eq. initial-data-general): v0 (D planes), F0 (D*D planes),
@@ -291,34 +288,24 @@ int lbm_step_graph(lbm_handle *h, int nsteps);
 /* ---- tile shapes ---------------------------------------------------------------------------
  * No counterpart in the paper.  Every choice below computes the same values node for node (the
  * fields are bit-identical); only the launch shape differs.  0 selects the form's default. */
-/* Link schedule of a regular (non-projection) step.  SERIAL: the fused kernel over every window,
- * then the link kernels.  OVERLAP: the fused kernel over the boundary windows (those holding a node
- * the link kernels read or feed: a cut node, a node of a Neumann stencil, the upstream node of a
- * cut link), then the link kernels on a second stream of the handle alongside the fused kernel over
- * the other windows; the step ends when both are done.  The two compute the same values: no
- * kernel of the other windows reads or writes what the link kernels read or write. */
-enum { LBM_LINKS_OVERLAP = 1, LBM_LINKS_SERIAL = 2 };
-
 typedef struct lbm_tuning {
     int windows_per_warp; /* fused kernel (bulk-copy forms): 32-node windows one warp stages at
                              once, 1, 2 or 4 (default 1 for FP32, 2 for BF16S)                  */
     int jacobi_segments;  /* projection sweeps: 32-node segments per warp, 1, 2 or 4 (default 1) */
     int link_block;       /* link kernel: threads per block, 64, 128 or 256 (default 128)        */
-    int link_schedule;    /* regular steps: LBM_LINKS_OVERLAP (default) or LBM_LINKS_SERIAL       */
     int candidates;       /* lbm_autotune: configurations it timed                              */
     double ms_per_step;   /* lbm_autotune: the chosen configuration's time per step             */
     double default_ms_per_step; /* lbm_autotune: the defaults' time per step                     */
 } lbm_tuning;
 
-/* Sets the tile shapes and the link schedule (the last three fields are ignored; 0 in a field
- * selects its default).  Errors: LBM_ERR_ARG (a value outside its list). */
+/* Sets the tile shapes (the last three fields are ignored).  Errors: LBM_ERR_ARG (a value outside
+ * its list). */
 int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t);
 int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t);
 
 /* Autotuner: from the current state, times `steps` steps (CUDA events on the handle's stream, one
  * untimed step first) for each candidate shape, coordinate by coordinate (windows per warp, then
- * Jacobi segments when the body has Neumann links, then the link block and the link schedule when
- * it has cut links),
+ * Jacobi segments when the body has Neumann links, then the link block when it has cut links),
  * restoring the state after each run from `scratch` (lbm_state_bytes bytes of device memory, 256-byte
  * aligned; the library allocates nothing), keeps the fastest shapes and reports them in *out (may
  * be NULL).  The state on return is the state on entry.  Synchronises.  steps should cover a

@@ -57,7 +57,6 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     h->ustar = c.take<char>((size_t)D * np * 8);
     h->un = c.take<char>((size_t)(D == 3 ? 32 : 16) * np);  // node-major u^n (see kUnStride)
     h->dmask = c.take<uint8_t>(np);
-    h->seg_part = c.take<int2>(std::max<long long>(h->nseg, 1));
     h->l_node = c.take<int>(nc);
     h->l_q = c.take<int>(nc);
     h->l_bc = c.take<int>(nc);
@@ -379,34 +378,6 @@ int lbm_storage_bytes(const lbm_handle *h, size_t *bytes) {
     return LBM_OK;
 }
 
-// boundary windows first, then the others (the geometry pass's window scratch holds the classes and
-// their scan); the second stream and its events for the overlapped link schedule
-static int partition_windows(lbm_handle *h) {
-    cudaStream_t st = h->stream;
-    const int ns = (int)h->nseg;
-    h->nseg_bnd = 0;
-    if (ns > 0) {
-        k_seg_class<<<grid_for(ns, 4), 128, 0, st>>>(h->box, h->seg, ns, h->flags, h->segflag);
-        CKL();
-        if (scan(h->segflag, h->segidx, ns, h->scan_scratch, st)) return LBM_ERR_CUDA;
-        k_seg_partition<<<grid_for(ns, 256), 256, 0, st>>>(h->seg, ns, h->segflag, h->segidx, h->seg_part);
-        CKL();
-        int last[2] = {0, 0};
-        CK(cudaMemcpyAsync(&last[0], h->segidx + (ns - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&last[1], h->segflag + (ns - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        h->nseg_bnd = (long long)last[0] + last[1];
-    }
-    if (!h->link_stream) {
-        int lo = 0, hi = 0;
-        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        CK(cudaStreamCreateWithPriority(&h->link_stream, cudaStreamNonBlocking, hi));
-        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    }
-    return LBM_OK;
-}
-
 int lbm_bind_storage(lbm_handle *h, void *storage, size_t bytes) {
     if (!h) return LBM_ERR_ARG;
     size_t need = 0;
@@ -434,8 +405,6 @@ int lbm_bind_storage(lbm_handle *h, void *storage, size_t bytes) {
         if (h->bcs[bc[l]].kind == LBM_BC_NEUMANN) { h->n_neu++; h->lsq_entries += ns[l]; }
         else h->n_dir++;
     }
-    rc = partition_windows(h);
-    if (rc) return rc;
     h->bound = true;
     h->initialized = false;
     return LBM_OK;
@@ -553,12 +522,11 @@ static bool one_of(int v, int a, int b, int c) { return v == 0 || v == a || v ==
 int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t) {
     if (!h || !t) return LBM_ERR_ARG;
     if (!one_of(t->windows_per_warp, 1, 2, 4) || !one_of(t->jacobi_segments, 1, 2, 4) ||
-        !one_of(t->link_block, 64, 128, 256) || !one_of(t->link_schedule, LBM_LINKS_OVERLAP, LBM_LINKS_SERIAL, 0))
+        !one_of(t->link_block, 64, 128, 256))
         return LBM_ERR_ARG;
     h->tune_nw = t->windows_per_warp;
     h->tune_jseg = t->jacobi_segments;
     h->tune_lblock = t->link_block;
-    h->tune_links = t->link_schedule;
     return LBM_OK;
 }
 
@@ -568,7 +536,6 @@ int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t) {
     t->windows_per_warp = h->tma_ok ? (h->tune_nw ? h->tune_nw : (h->pop_size == 2 ? 2 : 1)) : 0;
     t->jacobi_segments = h->tune_jseg ? h->tune_jseg : 1;
     t->link_block = h->tune_lblock ? h->tune_lblock : 128;
-    t->link_schedule = h->tune_links ? h->tune_links : LBM_LINKS_OVERLAP;
     return LBM_OK;
 }
 
@@ -606,25 +573,23 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     if (!h->initialized || h->timing || (h->opt.adjoint && h->adj_next >= 0)) return LBM_ERR_STATE;
     int rc = lbm_save_state(h, scratch);
     if (rc) return rc;
-    constexpr int NC = 4;
-    int *const shape[NC] = {&h->tune_nw, &h->tune_jseg, &h->tune_lblock, &h->tune_links};
-    const int saved[NC] = {h->tune_nw, h->tune_jseg, h->tune_lblock, h->tune_links};
-    const int cand[NC][3] = {{1, 2, 4}, {1, 2, 4}, {64, 128, 256}, {LBM_LINKS_OVERLAP, LBM_LINKS_SERIAL, 0}};
-    const int dflt[NC] = {h->pop_size == 2 ? 2 : 1, 1, 128, LBM_LINKS_OVERLAP};
-    const bool used[NC] = {h->tma_ok, h->n_neu > 0 && h->opt.proj_every > 0, h->n_cut > 0,
-                           h->n_cut > 0 && h->nseg_bnd > 0 && h->nseg_bnd < h->nseg};
-    for (int c = 0; c < NC; ++c) *shape[c] = 0;
+    int *const shape[3] = {&h->tune_nw, &h->tune_jseg, &h->tune_lblock};
+    const int saved[3] = {h->tune_nw, h->tune_jseg, h->tune_lblock};
+    const int cand[3][3] = {{1, 2, 4}, {1, 2, 4}, {64, 128, 256}};
+    const int dflt[3] = {h->pop_size == 2 ? 2 : 1, 1, 128};
+    const bool used[3] = {h->tma_ok, h->n_neu > 0 && h->opt.proj_every > 0, h->n_cut > 0};
+    for (int c = 0; c < 3; ++c) *shape[c] = 0;
     double best = 0.0;
     int count = 0;
     rc = time_shapes(h, steps, scratch, &best);
     count++;
     const double def_ms = best;
     // coordinate by coordinate; a candidate must beat the best by 1 % to replace it
-    for (int c = 0; c < NC && rc == LBM_OK; ++c) {
+    for (int c = 0; c < 3 && rc == LBM_OK; ++c) {
         if (!used[c]) continue;
         int chosen = 0;
         for (int i = 0; i < 3 && rc == LBM_OK; ++i) {
-            if (cand[c][i] == dflt[c] || cand[c][i] == 0) continue;
+            if (cand[c][i] == dflt[c]) continue;
             *shape[c] = cand[c][i];
             double ms = 0.0;
             rc = time_shapes(h, steps, scratch, &ms);
@@ -638,7 +603,7 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     }
     const int rl = lbm_load_state(h, scratch);
     if (rc != LBM_OK) {
-        for (int c = 0; c < NC; ++c) *shape[c] = saved[c];
+        for (int c = 0; c < 3; ++c) *shape[c] = saved[c];
         return rc;
     }
     if (rl) return rl;
@@ -875,7 +840,6 @@ int lbm_get_info(const lbm_handle *h, lbm_info *info) {
     info->storage_bytes = sb;
     info->launches = h->launches;
     info->lsq_entries = h->lsq_entries;
-    info->n_boundary_segments = h->nseg_bnd;
     return LBM_OK;
 }
 
@@ -941,9 +905,6 @@ void lbm_destroy(lbm_handle *h) {
         cudaGraphExecDestroy(h->graph_exec);
     }
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
-    if (h->link_stream) cudaStreamDestroy(h->link_stream);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 

@@ -20,7 +20,6 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_proj.cuh"
-#include "lbm_sched.cuh"
 #include "lbm_tma.cuh"
 #include "lbm_links.cuh"
 #include "lbm_adjoint.cuh"
@@ -111,12 +110,6 @@ struct lbm_handle {
     double *diag = nullptr;  // diagnostics and audit reductions: kReduceBlocks partial records + the result
     void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
     long long n_neu = 0, n_dir = 0, lsq_entries = 0;
-    // the window list partitioned into boundary windows (the first nseg_bnd) and the others, and
-    // the second stream the link kernels run on alongside the other windows of a regular step
-    int2 *seg_part = nullptr;
-    long long nseg_bnd = 0;
-    cudaStream_t link_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // state
     bool initialized = false;
     int phase = 0;  // 0: fA holds pre-collision f^0; 1: fA holds post-collision f*^{n-1}
@@ -127,9 +120,8 @@ struct lbm_handle {
     void *tma_buf[2] = {nullptr, nullptr};
     TmaMaps tma_maps[2];
     // tile shapes (0: the form's default): 32-node windows per warp of the fused kernel, segments
-    // per warp of a Jacobi sweep, threads per block of the link kernel; link schedule
-    // (LBM_LINKS_OVERLAP or LBM_LINKS_SERIAL)
-    int tune_nw = 0, tune_jseg = 0, tune_lblock = 0, tune_links = 0;
+    // per warp of a Jacobi sweep, threads per block of the link kernel
+    int tune_nw = 0, tune_jseg = 0, tune_lblock = 0;
     int wait_limit = -1;  // polls of the bulk-copy kernels' first wait (< 0: kTmaSpin)
     // timing
     bool timing = false;
@@ -220,16 +212,16 @@ inline int scan(const int *in, int *out, long long n, int *scratch, cudaStream_t
     return LBM_OK;
 }
 
-inline void timing_begin(lbm_handle *h, EventPair &ep, int cls, int launches = 1, cudaStream_t st = nullptr) {
+inline void timing_begin(lbm_handle *h, EventPair &ep, int cls, int launches = 1) {
     ep.cls = cls;
     ep.launches = launches;
     cudaEventCreate(&ep.a);
     cudaEventCreate(&ep.b);
-    cudaEventRecord(ep.a, st ? st : h->stream);
+    cudaEventRecord(ep.a, h->stream);
 }
 
-inline void timing_end(lbm_handle *h, EventPair &ep, cudaStream_t st = nullptr) {
-    cudaEventRecord(ep.b, st ? st : h->stream);
+inline void timing_end(lbm_handle *h, EventPair &ep) {
+    cudaEventRecord(ep.b, h->stream);
     h->events.push_back(ep);
 }
 
@@ -458,7 +450,7 @@ template <typename real, int D, typename pop = real> struct Impl {
     }
     // the fused kernel with the handle's windows per warp
     template <int NW> static void launch_fused_nw(lbm_handle *h, const StepArgs<float> &a) {
-        k_stream_collide_tma<D, pop, NW><<<grid_for(a.nseg, NW), 32, fused_smem<NW>(), h->stream>>>(a, *maps_of(h, h->fA),
+        k_stream_collide_tma<D, pop, NW><<<grid_for(h->nseg, NW), 32, fused_smem<NW>(), h->stream>>>(a, *maps_of(h, h->fA),
                                                                                                   RepairArgs{});
     }
     static void launch_fused(lbm_handle *h, const StepArgs<float> &a) {
@@ -466,21 +458,6 @@ template <typename real, int D, typename pop = real> struct Impl {
         if (nw == 4) launch_fused_nw<4>(h, a);
         else if (nw == 2) launch_fused_nw<2>(h, a);
         else launch_fused_nw<1>(h, a);
-    }
-    // the regular step's kernel over the windows a.seg[0 .. a.nseg)
-    static void launch_regular(lbm_handle *h, const StepArgs<real> &a) {
-        if constexpr (sizeof(real) == 4) {
-            if (h->tma_ok) {
-                launch_fused(h, a);
-                return;
-            }
-        }
-        k_stream_collide<real, D, 1, pop><<<grid_for(a.nseg, 4), 128, 0, h->stream>>>(a);
-    }
-    // regular steps run the link kernels alongside the windows they do not touch
-    static bool overlapped(const lbm_handle *h) {
-        return h->tune_links != LBM_LINKS_SERIAL && h->link_stream && h->n_cut > 0 && h->nseg_bnd > 0 &&
-               h->nseg_bnd < h->nseg;
     }
     // a grid of the blocks resident at once (occupancy query, once per instantiation), at most one
     // block per 4 S segments
@@ -586,14 +563,13 @@ template <typename real, int D, typename pop = real> struct Impl {
         return T;
     }
 
-    // the link kernels on stream st, fstar = this step's post-collision state (read by the next gather)
-    static int cutlinks(lbm_handle *h, double t, const void *fstar, cudaStream_t st) {
+    static int cutlinks(lbm_handle *h, double t) {
         if (h->n_cut == 0) return LBM_OK;
         CutArgs<real> a;
         a.L = links(h);
         a.b = h->box;
         a.flags = h->flags;
-        a.fstar = static_cast<const real *>(fstar);
+        a.fstar = static_cast<const real *>(h->fA);  // this step's post-collision state, read by the next gather
         a.bcs = h->dbcs;
         a.un = static_cast<const real *>(h->un);
         a.npad = h->box.npad;
@@ -608,18 +584,18 @@ template <typename real, int D, typename pop = real> struct Impl {
         a.D = D;
         a.status = h->status;
         EventPair ep;
-        if (h->timing) timing_begin(h, ep, 1, 1, st);
+        if (h->timing) timing_begin(h, ep, 1);
         const int lb = h->tune_lblock ? h->tune_lblock : 128;
         if constexpr (sizeof(real) == 4) {
             if (h->n_neu > 0) {
-                k_link_sums<D><<<grid_for(h->n_cut * kLinkLanes<D>, 256), 256, 0, st>>>(a, h->l_gsum);
+                k_link_sums<D><<<grid_for(h->n_cut * kLinkLanes<D>, 256), 256, 0, h->stream>>>(a, h->l_gsum);
                 h->launches++;
             }
-            k_links_f32<D, pop><<<grid_for(h->n_cut, lb), lb, 0, st>>>(a, bc_times(h, t + 0.5 * a.dt), h->l_gsum);
+            k_links_f32<D, pop><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a, bc_times(h, t + 0.5 * a.dt), h->l_gsum);
         }
         else
-            k_cutlinks<real, D><<<grid_for(h->n_cut, lb), lb, 0, st>>>(a);
-        if (h->timing) timing_end(h, ep, st);
+            k_cutlinks<real, D><<<grid_for(h->n_cut, lb), lb, 0, h->stream>>>(a);
+        if (h->timing) timing_end(h, ep);
         h->launches++;
         CKL();
         return LBM_OK;
@@ -673,35 +649,16 @@ template <typename real, int D, typename pop = real> struct Impl {
             const bool proj = h->n_neu > 0 && h->opt.proj_every > 0 && (h->step % h->opt.proj_every) == 0;
             const unsigned g = grid_for(h->nseg, 4);
             bool post_in_B = true;  // where this step leaves the post-collision populations
-            bool links_done = false;
-            if (!proj && h->phase == 1 && overlapped(h)) {
-                // boundary windows, then the link kernels on the second stream alongside the other
-                // windows; the step ends when both are done
-                StepArgs<real> ab = a, ai = a;
-                ab.seg = h->seg_part;
-                ab.nseg = (int)h->nseg_bnd;
-                ai.seg = h->seg_part + h->nseg_bnd;
-                ai.nseg = (int)(h->nseg - h->nseg_bnd);
-                EventPair ep;
-                if (h->timing) timing_begin(h, ep, 0);
-                launch_regular(h, ab);
-                CKL();
-                CK(cudaEventRecord(h->ev_fork, h->stream));
-                CK(cudaStreamWaitEvent(h->link_stream, h->ev_fork, 0));
-                int rc = cutlinks(h, t, a.fdst, h->link_stream);
-                if (rc) return rc;
-                CK(cudaEventRecord(h->ev_join, h->link_stream));
-                launch_regular(h, ai);
-                CKL();
-                if (h->timing) timing_end(h, ep);
-                CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-                h->launches += 2;
-                links_done = true;
-            } else if (!proj) {
+            if (!proj) {
                 EventPair ep;
                 if (h->timing) timing_begin(h, ep, 0);
                 if (h->phase == 0) k_stream_collide<real, D, 0, pop><<<g, 128, 0, h->stream>>>(a);
-                else launch_regular(h, a);
+                else if constexpr (sizeof(real) == 4) {
+                    if (h->tma_ok)
+                        launch_fused(h, a);
+                    else
+                        k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
+                } else k_stream_collide<real, D, 1, pop><<<g, 128, 0, h->stream>>>(a);
                 if (h->timing) timing_end(h, ep);
                 h->launches++;
                 CKL();
@@ -763,10 +720,8 @@ template <typename real, int D, typename pop = real> struct Impl {
             // the post-collision state: fB after a regular step or a bulk-copy projection step, fA
             // after a plain-load projection step
             if (post_in_B) std::swap(h->fA, h->fB);
-            if (!links_done) {
-                int rc = cutlinks(h, t, h->fA, h->stream);
-                if (rc) return rc;
-            }
+            int rc = cutlinks(h, t);
+            if (rc) return rc;
             h->phase = 1;
             h->step++;
         }

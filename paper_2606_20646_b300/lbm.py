@@ -70,8 +70,7 @@ class lbm_info(C.Structure):
     _fields_ = [("n_box", C.c_longlong), ("n_active", C.c_longlong), ("n_cut", C.c_longlong),
                 ("n_neumann", C.c_longlong), ("n_dirichlet", C.c_longlong), ("n_segments", C.c_longlong),
                 ("step", C.c_longlong), ("t", C.c_double), ("dt", C.c_double), ("geometry_bytes", C.c_size_t),
-                ("storage_bytes", C.c_size_t), ("launches", C.c_longlong), ("lsq_entries", C.c_longlong),
-                ("n_boundary_segments", C.c_longlong)]
+                ("storage_bytes", C.c_size_t), ("launches", C.c_longlong), ("lsq_entries", C.c_longlong)]
 
 
 class lbm_kernel_time(C.Structure):
@@ -91,8 +90,7 @@ LAYOUT = {"planes": 0, "nodes": 1}
 
 class lbm_tuning(C.Structure):
     _fields_ = [("windows_per_warp", C.c_int), ("jacobi_segments", C.c_int), ("link_block", C.c_int),
-                ("link_schedule", C.c_int), ("candidates", C.c_int), ("ms_per_step", C.c_double),
-                ("default_ms_per_step", C.c_double)]
+                ("candidates", C.c_int), ("ms_per_step", C.c_double), ("default_ms_per_step", C.c_double)]
 
 
 # symbol -> (restype, argtypes); every entry point declared in include/lbm.h
@@ -352,21 +350,16 @@ class Simulation:
         return self
 
     # -- tile shapes -----------------------------------------------------------------------------
-    _TUNE_KEYS = ("windows_per_warp", "jacobi_segments", "link_block", "link_schedule", "candidates",
-                  "ms_per_step", "default_ms_per_step")
-    LINK_SCHEDULE = {"overlap": 1, "serial": 2}
+    _TUNE_KEYS = ("windows_per_warp", "jacobi_segments", "link_block", "candidates", "ms_per_step",
+                  "default_ms_per_step")
 
     def get_tuning(self) -> dict:
         t = lbm_tuning()
         _check(load_library().lbm_get_tuning(self.h, C.byref(t)), "lbm_get_tuning")
-        return {k: getattr(t, k) for k in self._TUNE_KEYS[:4]}
+        return {k: getattr(t, k) for k in self._TUNE_KEYS[:3]}
 
-    def set_tuning(self, windows_per_warp: int = 0, jacobi_segments: int = 0, link_block: int = 0,
-                   link_schedule=0):
-        """Tile shapes and the link schedule (0: the default; link_schedule also "overlap" or
-        "serial")."""
-        ls = self.LINK_SCHEDULE.get(link_schedule, link_schedule) if isinstance(link_schedule, str) else link_schedule
-        t = lbm_tuning(windows_per_warp, jacobi_segments, link_block, int(ls), 0, 0.0, 0.0)
+    def set_tuning(self, windows_per_warp: int = 0, jacobi_segments: int = 0, link_block: int = 0):
+        t = lbm_tuning(windows_per_warp, jacobi_segments, link_block, 0, 0.0, 0.0)
         _check(load_library().lbm_set_tuning(self.h, C.byref(t)), "lbm_set_tuning")
         return self
 
