@@ -278,10 +278,45 @@ struct RepairArgs {
 // sided where a neighbour is inactive), F^r, the populations translated by f^eq(v, F^r) - f^eq(v, F),
 // the collision, u*^{n+1}; F^r - I stored for the second solve.  The same arithmetic as the
 // plain-load k_repair_collide, from the same staged values.
+// Corrected gradient of u^c = u^0 + d (central differences, one-sided next to a cut link) for the
+// repair, from the node's and its axis neighbours' u^0 pairs and corrections; computed before the
+// warp waits for its bulk copies, so these scattered loads overlap the copies.  own[A] marks an axis
+// with no neighbour on either side, where the repair keeps the gathered gradient.
+template <int D>
+__device__ __forceinline__ void repair_gradient(const StepArgs<float> &a, const RepairArgs &rp, int node, int x, int y,
+                                                int z, uint8_t fl, float Gc[D * D], bool own[D]) {
+    constexpr long long DV = kDV<D>;
+    const long long Pn = a.b.npad;
+    const unsigned cut = fl & kCutMask;
+    const float inv = 1.0f / (float)a.b.dx;
+    #pragma unroll
+    for (int A = 0; A < D; ++A) {
+        const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
+        int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
+        int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
+        TLV_BOUND(lp, Pn, a.status);
+        TLV_BOUND(lm, Pn, a.status);
+        own[A] = !ap && !am;
+        #pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float ho = rp.u0[i * Pn + node], lo_ = rp.u0[(D + i) * Pn + node];
+            const float dp = ((rp.u0[i * Pn + lp] - ho) + (rp.u0[(D + i) * Pn + lp] - lo_)) +
+                             (rp.dc[DV * lp + i] - rp.dc[DV * node + i]);
+            const float dm = ((ho - rp.u0[i * Pn + lm]) + (lo_ - rp.u0[(D + i) * Pn + lm])) +
+                             (rp.dc[DV * node + i] - rp.dc[DV * lm + i]);
+            float g = 0.0f;
+            if (ap && am) g = 0.5f * (dp + dm) * inv;
+            else if (ap) g = dp * inv;
+            else if (am) g = dm * inv;
+            Gc[i * D + A] = g;
+        }
+    }
+}
+
 template <int D, typename pop = float>
 __device__ __forceinline__ void repair_staged(const StepArgs<float> &a, const RepairArgs &rp, char *wsm, int node,
-                                              int x, int y, int z, int lane, uint8_t fl, long long l0, bool act,
-                                              float mu, float lam) {
+                                              int lane, uint8_t fl, long long l0, bool act, float mu, float lam,
+                                              const float Gc[D * D], const bool own[D]) {
     constexpr int K = D + D * D, Q = 2 * D;
     constexpr long long DV = kDV<D>;
     const long long Pn = a.b.npad;
@@ -307,28 +342,10 @@ __device__ __forceinline__ void repair_staged(const StepArgs<float> &a, const Re
     for (int k = 0; k < D * D; ++k) G[k] = S[D + k];
     const unsigned cut = fl & kCutMask;
     #pragma unroll
-    for (int A = 0; A < D; ++A) {
-        const bool ap = !((cut >> (2 * A)) & 1), am = !((cut >> (2 * A + 1)) & 1);
-        int lp = ap ? nbr(a.b, node, x, y, z, 2 * A) : node;
-        int lm = am ? nbr(a.b, node, x, y, z, 2 * A + 1) : node;
-        TLV_BOUND(lp, Pn, a.status);
-        TLV_BOUND(lm, Pn, a.status);
+    for (int A = 0; A < D; ++A)
         #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const float ho = rp.u0[i * Pn + node], lo_ = rp.u0[(D + i) * Pn + node];
-            const float dp = ((rp.u0[i * Pn + lp] - ho) + (rp.u0[(D + i) * Pn + lp] - lo_)) +
-                             (rp.dc[DV * lp + i] - rp.dc[DV * node + i]);
-            const float dm = ((ho - rp.u0[i * Pn + lm]) + (lo_ - rp.u0[(D + i) * Pn + lm])) +
-                             (rp.dc[DV * node + i] - rp.dc[DV * lm + i]);
-            const float inv = 1.0f / (float)a.b.dx;
-            float Gc;
-            if (ap && am) Gc = 0.5f * (dp + dm) * inv;
-            else if (ap) Gc = dp * inv;
-            else if (am) Gc = dm * inv;
-            else Gc = G[i * D + A];
-            Gr[i * D + A] = (1.0f - rp.theta) * G[i * D + A] + rp.theta * Gc;
-        }
-    }
+        for (int i = 0; i < D; ++i)
+            Gr[i * D + A] = (1.0f - rp.theta) * G[i * D + A] + rp.theta * (own[A] ? G[i * D + A] : Gc[i * D + A]);
     float Pold[D * D], Pk[D * D], Fit[D * D];
     piola_g<float, D>(G, mu, lam, Pold, Fit);
     const float J = piola_g<float, D>(Gr, mu, lam, Pk, Fit);
@@ -449,7 +466,8 @@ __device__ __forceinline__ void issue_window(const StepArgs<float> &a, const Tma
 // belong to the next row and store nothing.
 template <int D, typename pop, bool REPAIR>
 __device__ __forceinline__ void collide_window(const StepArgs<float> &a, const RepairArgs &rp, char *cur, int2 sg,
-                                               int lane, long long l0pre, int gpre) {
+                                               int lane, long long l0pre, int gpre, const float *Gc,
+                                               const bool *own) {
     using L = TmaLayout<D, sizeof(pop)>;
     const int x = sg.x - sg.y * a.b.nx + lane;
     if (x >= a.b.nx) return;
@@ -464,7 +482,7 @@ __device__ __forceinline__ void collide_window(const StepArgs<float> &a, const R
     float mu = a.mtab ? a.mtab[2 * gpre] : a.mu;
     const float lam = a.mtab ? a.mtab[2 * gpre + 1] : a.lam;
     if (a.mu_field) mu = a.mu_field[node];
-    if constexpr (REPAIR) repair_staged<D, pop>(a, rp, cur, node, x, sg.y % a.b.ny, sg.y / a.b.ny, lane, fl, l0, act, mu, lam);
+    if constexpr (REPAIR) repair_staged<D, pop>(a, rp, cur, node, lane, fl, l0, act, mu, lam, Gc, own);
     else collide_staged<D, pop>(a, cur, node, lane, fl, us, l0, act, mu, lam);
 }
 
@@ -501,6 +519,16 @@ __global__ void __launch_bounds__(32, REPAIR ? 12 : 16) k_stream_collide_tma(con
         l0pre[w] = __ldg(a.lstart + nc);
         gpre[w] = a.mtab ? __ldg(a.mat + nc) : 0;
     }
+    // the repair's corrected gradient (one window per warp), also while the copies are in flight
+    float Gc[REPAIR ? D * D : 1];
+    bool own[REPAIR ? D : 1];
+    if constexpr (REPAIR) {
+        static_assert(!REPAIR || NW == 1, "the repair runs one window per warp");
+        const int x = sg[0].x - sg[0].y * a.b.nx + lane;
+        const int node = sg[0].x + lane;
+        const uint8_t fl = x < a.b.nx ? __ldg(a.flags + node) : 0;
+        if (fl & kActive) repair_gradient<D>(a, rp, node, x, sg[0].y % a.b.ny, sg[0].y / a.b.ny, fl, Gc, own);
+    }
     __syncwarp();
     #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(32, REPAIR ? 12 : 16) k_stream_collide_tma(con
             for (int v = w; v < nw; ++v) mbar_wait_bounded(bars + v, 0);  // copies in flight land first
             return;
         }
-        collide_window<D, pop, REPAIR>(a, rp, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w]);
+        collide_window<D, pop, REPAIR>(a, rp, smem + w * L::stage_bytes, sg[w], lane, l0pre[w], gpre[w], Gc, own);
     }
 }
 
