@@ -555,14 +555,23 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     char *wsm = smem + warp * L::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * L::warp_bytes) + warp;
     const int2 sg = __ldg(&a.seg[sgi]);
-    if (!tma_gather_segment<D, pop>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status, a.spin)) return;
+    const long long P = a.b.npad;
+    // the node's flags, first cut link and u* pair are loaded before the warp waits for its copies
+    // (lanes past the end of the row read their in-range slot and never use it)
     const int x = sg.x - sg.y * a.b.nx + lane;
-    if (x >= a.b.nx) return;
     const int node = sg.x + lane;
     const uint8_t fl = __ldg(a.flags + node);
+    const long long l0 = __ldg(a.lstart + node);
+    float ush[D], usl[D];
+    #pragma unroll
+    for (int i = 0; i < D; ++i) {
+        ush[i] = a.ustar[i * P + node];
+        usl[i] = a.ustar[(D + i) * P + node];
+    }
+    if (!tma_gather_segment<D, pop>(a.b, &maps.wide, &maps.narrow, wsm, bar, sg, lane, a.status, a.spin)) return;
+    if (x >= a.b.nx) return;
     if (!(fl & kActive)) return;
-    tma_closure<D, pop>(a, wsm, node, x, lane, fl & kCutMask, (fl & kCutMask) ? __ldg(a.lstart + node) : 0);
-    const long long P = a.b.npad;
+    tma_closure<D, pop>(a, wsm, node, x, lane, fl & kCutMask, (fl & kCutMask) ? l0 : 0);
     float v[D];
     const float hdt = 0.5f * a.dt;
     const float inv_damp = 1.0f / (1.0f + hdt * a.gamma);
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(128) k_gather_moments_tma(const StepArgs<float
     #pragma unroll
     for (int i = 0; i < D; ++i) {
         a.vst[i * P + node] = v[i];
-        float hi = a.ustar[i * P + node], lo = a.ustar[(D + i) * P + node];
+        float hi = ush[i], lo = usl[i];
         df_add(hi, lo, 0.5f * a.dt * v[i]);
         a.u0[i * P + node] = hi;
         a.u0[(D + i) * P + node] = lo;
