@@ -110,18 +110,18 @@ class Clocks:
 # timed box by its number of windows (segments).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = {"sources_sha256": "ce9c50662bb7605bf5952b44143c9bfd144388f7c4e10fd10770fa38797ec17a",
-                   "bytes_per_launch": 374856064 + 265386880, "windows": 30112,
+TRAFFIC_CAPTURE = {"sources_sha256": "f383b77b289d3cefa57234498a29e69d42b8b00f957a408c8e09626461970f97",
+                   "bytes_per_launch": 374868608 + 264868864, "windows": 30112,
                    "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
 # the same for the BF16-storage fused kernel (two windows per warp)
-BF16_TRAFFIC_CAPTURE = {"sources_sha256": "ce9c50662bb7605bf5952b44143c9bfd144388f7c4e10fd10770fa38797ec17a",
-                        "bytes_per_launch": 217926528 + 133869184, "windows": 30112,
+BF16_TRAFFIC_CAPTURE = {"sources_sha256": "f383b77b289d3cefa57234498a29e69d42b8b00f957a408c8e09626461970f97",
+                        "bytes_per_launch": 217929088 + 134015744, "windows": 30112,
                         "summary": "profiles/k_stream_collide_tma_bf16_shell_3d.md"}
 # the same for the reverse step on the clamped cube (128^3, the timed size itself)
 ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
                "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
-ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "1e51edf289d4040ba2929255d36082e21048b9796bf9057604779843ecd92a4e",
-                       "bytes_per_launch": 741835605 + 577194155, "windows": None,
+ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "dd40d5d136e1433756735bf9293ee781e5145237a1f82dd491e42185de3a7fc7",
+                       "bytes_per_launch": 741894400 + 577187072, "windows": None,
                        "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
