@@ -170,12 +170,13 @@ def link_bytes(D, real_size, n_cut, lsq_entries):
     return n_cut * per_link + lsq_entries * (4 + (D - 1) * real_size)
 
 
-def jacobi_bytes_per_node(D, real_size):
-    """Algorithmic HBM bytes per active node of one damped-Jacobi sweep: the node's correction
-    vector read and written (D values padded to 2 or 4), its residual vector (4 values: r and the
-    sweep weight) and its flag byte; neighbour reads hit in cache."""
+def jacobi_bytes_per_node(D, real_size, sweeps_per_launch=1):
+    """Algorithmic HBM bytes per active node and sweep of the damped-Jacobi sweeps: per launch the
+    node's correction vector read and written (D values padded to 2 or 4), its residual vector (4
+    values: r and the sweep weight) and its flag byte, shared by the sweeps of the launch (two with
+    the two-sweep kernel, whose first sweep stays in shared memory); neighbour reads hit in cache."""
     dv = 4 if D == 3 else 2
-    return 2 * dv * real_size + 4 * real_size + 1
+    return (2 * dv * real_size + 4 * real_size + 1) / sweeps_per_launch
 
 
 def adjoint_bytes_per_node(D, real_size):
@@ -348,8 +349,10 @@ def run_ours(args, world, rank, local):
     share = {"stream_collide": kt["stream_collide_ms"] / ms, "cutlink": kt["cutlink_ms"] / ms,
              "projection": kt["projection_ms"] / ms, "jacobi (within projection)": kt["jacobi_ms"] / ms}
     avg_jac = kt["jacobi_ms"] / max(kt["jacobi_launches"], 1)
-    jacobi = {"avg_sweep_us": round(avg_jac * 1e3, 2), "sweeps": kt["jacobi_launches"],
-              "GBps": round(nact * jacobi_bytes_per_node(3, 4) / (avg_jac / 1e3) / 1e9, 1) if avg_jac > 0 else None}
+    jsw = tuning.get("jacobi_sweeps", 1) or 1
+    jacobi = {"avg_sweep_us": round(avg_jac * 1e3, 2), "sweeps": kt["jacobi_launches"], "sweeps_per_launch": jsw,
+              "bytes_per_node_sweep": jacobi_bytes_per_node(3, 4, jsw),
+              "GBps": round(nact * jacobi_bytes_per_node(3, 4, jsw) / (avg_jac / 1e3) / 1e9, 1) if avg_jac > 0 else None}
     avg_cut = kt["cutlink_ms"] / max(kt["cutlink_launches"], 1)
     lb = link_bytes(3, 4, info["n_cut"], info["lsq_entries"])
     links = {"kernel": "k_links_f32<3>", "avg_launch_ms": round(avg_cut, 4), "bytes_per_launch": lb,

@@ -293,19 +293,25 @@ typedef struct lbm_tuning {
                              once, 1, 2 or 4 (default 1 for FP32, 2 for BF16S)                  */
     int jacobi_segments;  /* projection sweeps: 32-node segments per warp, 1, 2 or 4 (default 1) */
     int link_block;       /* link kernel: threads per block, 64, 128 or 256 (default 128)        */
+    int jacobi_sweeps;    /* projection: sweeps per launch, 1 or 2.  2 is available for the FP32
+                             forms of boxes with no periodic axis (tiles staged by bulk copies, two
+                             sweeps per pass over memory) and is the default there in 2D; 1 is the
+                             default in 3D and the only choice elsewhere                          */
     int candidates;       /* lbm_autotune: configurations it timed                              */
     double ms_per_step;   /* lbm_autotune: the chosen configuration's time per step             */
     double default_ms_per_step; /* lbm_autotune: the defaults' time per step                     */
 } lbm_tuning;
 
-/* Sets the tile shapes (the last three fields are ignored).  Errors: LBM_ERR_ARG (a value outside
- * its list). */
+/* Sets the tile shapes (the last three fields are ignored; 0 in a field selects its default).
+ * The shapes change no value: two sweeps per launch are bit-identical to two single sweeps.
+ * Errors: LBM_ERR_ARG (a value outside its list). */
 int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t);
 int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t);
 
 /* Autotuner: from the current state, times `steps` steps (CUDA events on the handle's stream, one
  * untimed step first) for each candidate shape, coordinate by coordinate (windows per warp, then
- * Jacobi segments when the body has Neumann links, then the link block when it has cut links),
+ * Jacobi segments and sweeps per launch when the body has Neumann links, then the link block when
+ * it has cut links),
  * restoring the state after each run from `scratch` (lbm_state_bytes bytes of device memory, 256-byte
  * aligned; the library allocates nothing), keeps the fastest shapes and reports them in *out (may
  * be NULL).  The state on return is the state on entry.  Synchronises.  steps should cover a

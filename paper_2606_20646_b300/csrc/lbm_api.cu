@@ -79,6 +79,9 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->dA = c.take<char>((size_t)(D == 3 ? 4 : 2) * np * rs);
         h->dB = c.take<char>((size_t)(D == 3 ? 4 : 2) * np * rs);
         h->resid = c.take<char>((size_t)4 * np * rs);
+        int ntx, nty, ntz;
+        jp_tile_grid(D, h->box.nx, h->box.ny, h->box.nz, ntx, nty, ntz);
+        h->jp_tiles = c.take<int>((size_t)ntx * nty * ntz);
         h->vst = c.take<char>((size_t)D * np * rs);
         h->Gst = c.take<char>((size_t)D * D * np * rs);
         h->partial = c.take<double>((size_t)D * (std::max<size_t>(grid_for(h->nseg, 4), kReduceBlocks) + 1));
@@ -89,6 +92,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
         h->u0 = h->u1 = nullptr;
         h->partial = h->mean = nullptr;
         h->dA = h->dB = h->resid = h->vst = h->Gst = nullptr;
+        h->jp_tiles = nullptr;
     }
     h->staging = h->opt.host_staging ? c.take<double>((size_t)(2 * D + D * D + D * K) * h->box.nbox) : nullptr;
     h->diag = c.take<double>((size_t)kDiagRec * (kReduceBlocks + 1));
@@ -313,7 +317,12 @@ int lbm_create(const lbm_grid *grid, const lbm_levelset *ls, const lbm_material 
     bx.nx = h->grid.n[0];
     bx.ny = h->grid.n[1];
     bx.nz = h->grid.n[2];
-    for (int a = 0; a < 3; ++a) { bx.per[a] = h->grid.periodic[a] != 0; bx.origin[a] = h->grid.origin[a]; }
+    // a 2D body's single z plane is marked periodic in its grid, but no kernel reads a z neighbour in
+    // 2D: the box keeps z non-periodic so that 2D neighbour indices take the plain-offset path
+    for (int a = 0; a < 3; ++a) {
+        bx.per[a] = a < h->D && h->grid.periodic[a] != 0;
+        bx.origin[a] = h->grid.origin[a];
+    }
     bx.dx = h->grid.dx;
     bx.nbox = (long long)bx.nx * bx.ny * bx.nz;
     // plane length: the box rounded up to 32 nodes plus one spare window, so that a 32-node window
@@ -522,11 +531,12 @@ static bool one_of(int v, int a, int b, int c) { return v == 0 || v == a || v ==
 int lbm_set_tuning(lbm_handle *h, const lbm_tuning *t) {
     if (!h || !t) return LBM_ERR_ARG;
     if (!one_of(t->windows_per_warp, 1, 2, 4) || !one_of(t->jacobi_segments, 1, 2, 4) ||
-        !one_of(t->link_block, 64, 128, 256))
+        !one_of(t->link_block, 64, 128, 256) || !one_of(t->jacobi_sweeps, 1, 2, 0))
         return LBM_ERR_ARG;
     h->tune_nw = t->windows_per_warp;
     h->tune_jseg = t->jacobi_segments;
     h->tune_lblock = t->link_block;
+    h->tune_jsweeps = t->jacobi_sweeps;
     return LBM_OK;
 }
 
@@ -536,6 +546,7 @@ int lbm_get_tuning(const lbm_handle *h, lbm_tuning *t) {
     t->windows_per_warp = h->tma_ok ? (h->tune_nw ? h->tune_nw : (h->pop_size == 2 ? 2 : 1)) : 0;
     t->jacobi_segments = h->tune_jseg ? h->tune_jseg : 1;
     t->link_block = h->tune_lblock ? h->tune_lblock : 128;
+    t->jacobi_sweeps = (h->jp_ok && (h->tune_jsweeps ? h->tune_jsweeps == 2 : h->D == 2)) ? 2 : 1;
     return LBM_OK;
 }
 
@@ -573,23 +584,25 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     if (!h->initialized || h->timing || (h->opt.adjoint && h->adj_next >= 0)) return LBM_ERR_STATE;
     int rc = lbm_save_state(h, scratch);
     if (rc) return rc;
-    int *const shape[3] = {&h->tune_nw, &h->tune_jseg, &h->tune_lblock};
-    const int saved[3] = {h->tune_nw, h->tune_jseg, h->tune_lblock};
-    const int cand[3][3] = {{1, 2, 4}, {1, 2, 4}, {64, 128, 256}};
-    const int dflt[3] = {h->pop_size == 2 ? 2 : 1, 1, 128};
-    const bool used[3] = {h->tma_ok, h->n_neu > 0 && h->opt.proj_every > 0, h->n_cut > 0};
-    for (int c = 0; c < 3; ++c) *shape[c] = 0;
+    constexpr int NC = 4;
+    int *const shape[NC] = {&h->tune_nw, &h->tune_jseg, &h->tune_jsweeps, &h->tune_lblock};
+    const int saved[NC] = {h->tune_nw, h->tune_jseg, h->tune_jsweeps, h->tune_lblock};
+    const int cand[NC][3] = {{1, 2, 4}, {1, 2, 4}, {2, 1, 0}, {64, 128, 256}};
+    const int dflt[NC] = {h->pop_size == 2 ? 2 : 1, 1, h->D == 2 ? 2 : 1, 128};
+    const bool proj = h->n_neu > 0 && h->opt.proj_every > 0;
+    const bool used[NC] = {h->tma_ok, proj, proj && h->jp_ok, h->n_cut > 0};
+    for (int c = 0; c < NC; ++c) *shape[c] = 0;
     double best = 0.0;
     int count = 0;
     rc = time_shapes(h, steps, scratch, &best);
     count++;
     const double def_ms = best;
     // coordinate by coordinate; a candidate must beat the best by 1 % to replace it
-    for (int c = 0; c < 3 && rc == LBM_OK; ++c) {
+    for (int c = 0; c < NC && rc == LBM_OK; ++c) {
         if (!used[c]) continue;
         int chosen = 0;
         for (int i = 0; i < 3 && rc == LBM_OK; ++i) {
-            if (cand[c][i] == dflt[c]) continue;
+            if (cand[c][i] == dflt[c] || cand[c][i] == 0) continue;
             *shape[c] = cand[c][i];
             double ms = 0.0;
             rc = time_shapes(h, steps, scratch, &ms);
@@ -603,7 +616,7 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out) {
     }
     const int rl = lbm_load_state(h, scratch);
     if (rc != LBM_OK) {
-        for (int c = 0; c < 3; ++c) *shape[c] = saved[c];
+        for (int c = 0; c < NC; ++c) *shape[c] = saved[c];
         return rc;
     }
     if (rl) return rl;

@@ -20,6 +20,7 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_proj.cuh"
+#include "lbm_jacobi2.cuh"
 #include "lbm_tma.cuh"
 #include "lbm_links.cuh"
 #include "lbm_adjoint.cuh"
@@ -110,6 +111,12 @@ struct lbm_handle {
     double *diag = nullptr;  // diagnostics and audit reductions: kReduceBlocks partial records + the result
     void *dA = nullptr, *dB = nullptr, *resid = nullptr;  // projection correction buffers and residual
     long long n_neu = 0, n_dir = 0, lsq_entries = 0;
+    // two Jacobi sweeps per launch (FP32 forms, no periodic axis): maps of dA, dB and the residual,
+    // the tiles holding an active node
+    bool jp_ok = false;
+    JPairMaps jp_maps;
+    int *jp_tiles = nullptr;
+    int jp_ntiles = 0;
     // state
     bool initialized = false;
     int phase = 0;  // 0: fA holds pre-collision f^0; 1: fA holds post-collision f*^{n-1}
@@ -121,7 +128,7 @@ struct lbm_handle {
     TmaMaps tma_maps[2];
     // tile shapes (0: the form's default): 32-node windows per warp of the fused kernel, segments
     // per warp of a Jacobi sweep, threads per block of the link kernel
-    int tune_nw = 0, tune_jseg = 0, tune_lblock = 0;
+    int tune_nw = 0, tune_jseg = 0, tune_lblock = 0, tune_jsweeps = 0;
     int wait_limit = -1;  // polls of the bulk-copy kernels' first wait (< 0: kTmaSpin)
     // timing
     bool timing = false;
@@ -306,6 +313,43 @@ inline bool encode_population_maps(void *base, long long npad, int planes, int K
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS;
+}
+
+// Maps of the two-sweep Jacobi kernel.  3D: d and the residual as (4 floats, x, y, z) with boxes
+// (4, 32, rows, 1).  2D: d as (x, y) of 8-byte elements (a (d_1, d_2) pair) with box (NP, 1), the
+// residual as (4 floats, x, y) with box (4, NP, 1).
+inline bool encode_jpair_maps(int D, void *dA, void *dB, void *resid, int nx, int ny, int nz, JPairMaps *out) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    bool ok = true;
+    auto enc = [&](CUtensorMap *m, CUtensorMapDataType ty, int rank, void *base, const cuuint64_t *dims,
+                   const cuuint64_t *strides, const cuuint32_t *box) {
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        ok = ok && encode(m, ty, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (D == 3) {
+        const cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+        const cuuint64_t str[3] = {16, 16ull * nx, 16ull * nx * ny};
+        const cuuint32_t bd[4] = {4, 32, (cuuint32_t)JPairLayout<3>::RD, 1};
+        const cuuint32_t br[4] = {4, 32, (cuuint32_t)JPairLayout<3>::RR, 1};
+        enc(&out->d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dA, dims, str, bd);
+        enc(&out->d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dB, dims, str, bd);
+        enc(&out->r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, resid, dims, str, br);
+    } else {
+        if (nx % 2) return false;  // rows of 8-byte pairs must be 16-byte multiples
+        const cuuint64_t dd[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+        const cuuint64_t sd[1] = {8ull * nx};
+        const cuuint32_t bd[2] = {(cuuint32_t)JPairLayout<2>::NP, 1};
+        const cuuint64_t dr[3] = {4, (cuuint64_t)nx, (cuuint64_t)ny};
+        const cuuint64_t sr[2] = {16, 16ull * nx};
+        const cuuint32_t br[3] = {4, (cuuint32_t)JPairLayout<2>::NP, 1};
+        enc(&out->d[0], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, dA, dd, sd, bd);
+        enc(&out->d[1], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, dB, dd, sd, bd);
+        enc(&out->r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, resid, dr, sr, br);
+    }
+    return ok;
 }
 
 inline LevelSetD levelset_view(const lbm_handle *h) {
@@ -501,7 +545,67 @@ template <typename real, int D, typename pop = real> struct Impl {
             h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, levelset_view(h), h->dbcs, h->nbc,
             links(h), h->status);
         CKL();
+        return setup_jpair(h);
+    }
+
+    // two-sweep Jacobi: maps, kernel attributes and the list of tiles holding an active node (the
+    // geometry pass's window scratch holds the tile flags and their scan)
+    static int setup_jpair(lbm_handle *h) {
+        h->jp_ok = false;
+        h->jp_ntiles = 0;
+        if constexpr (sizeof(real) == 4) {
+            const Box &b = h->box;
+            if (!h->jp_tiles || b.per[0] || b.per[1] || b.per[2] || h->nseg == 0) return LBM_OK;
+            int ntx, nty, ntz;
+            jp_tile_grid(D, b.nx, b.ny, b.nz, ntx, nty, ntz);
+            const long long nt = (long long)ntx * nty * ntz;
+            if (nt > h->nsegmax) return LBM_OK;
+            bool ok = encode_jpair_maps(D, h->dA, h->dB, h->resid, b.nx, b.ny, b.nz, &h->jp_maps);
+            if constexpr (D == 3)
+                ok = ok && cudaFuncSetAttribute(k_jacobi_pair3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                JPairLayout<3>::smem_bytes) == cudaSuccess &&
+                     cudaFuncSetAttribute(k_jacobi_pair3, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                         cudaSuccess;
+            else
+                ok = ok && cudaFuncSetAttribute(k_jacobi_pair2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                JPairLayout<2>::smem_bytes) == cudaSuccess &&
+                     cudaFuncSetAttribute(k_jacobi_pair2, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                         cudaSuccess;
+            cudaGetLastError();
+            if (!ok) return LBM_OK;
+            CK(cudaMemsetAsync(h->segflag, 0, (size_t)nt * sizeof(int), h->stream));
+            k_jp_mark<<<grid_for(b.nbox, 256), 256, 0, h->stream>>>(b, h->flags, h->segflag);
+            CKL();
+            if (scan(h->segflag, h->segidx, nt, h->scan_scratch, h->stream)) return LBM_ERR_CUDA;
+            k_jp_compact<<<grid_for(nt, 256), 256, 0, h->stream>>>(h->segflag, h->segidx, (int)nt, h->jp_tiles);
+            CKL();
+            int last[2] = {0, 0};
+            CK(cudaMemcpyAsync(&last[0], h->segidx + (nt - 1), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaMemcpyAsync(&last[1], h->segflag + (nt - 1), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            h->jp_ntiles = last[0] + last[1];
+            h->jp_ok = h->jp_ntiles > 0;
+        }
         return LBM_OK;
+    }
+
+    // two sweeps from src (nullptr: d = 0) into dst with the two-sweep kernel
+    static void launch_jpair(lbm_handle *h, const ProjArgs<real> &p, const real *src, real *dst) {
+        if constexpr (sizeof(real) == 4) {
+            const CUtensorMap &dm = h->jp_maps.d[src == static_cast<const real *>(h->dB) ? 1 : 0];
+            const int spin = h->wait_limit >= 0 ? h->wait_limit : kTmaSpin;
+            if constexpr (D == 3)
+                k_jacobi_pair3<<<h->jp_ntiles, JPairLayout<3>::threads, JPairLayout<3>::smem_bytes, h->stream>>>(
+                    p, dm, h->jp_maps.r, src == nullptr, dst, h->jp_tiles, spin);
+            else
+                k_jacobi_pair2<<<h->jp_ntiles, JPairLayout<2>::threads, JPairLayout<2>::smem_bytes, h->stream>>>(
+                    p, dm, h->jp_maps.r, src == nullptr, dst, h->jp_tiles, spin);
+        }
+    }
+    // two sweeps per launch: chosen by the tuning, else the default of the dimension (2D: on; 3D:
+    // off, the 3D tiles' halos and per-plane barriers cost more than the second pass over memory)
+    static bool jpair_on(const lbm_handle *h) {
+        return h->jp_ok && (h->tune_jsweeps ? h->tune_jsweeps == 2 : D == 2);
     }
 
     static int init(lbm_handle *h, int mode, const double *v0, const double *F0, const double *u0, const double *dU0) {
@@ -615,8 +719,14 @@ template <typename real, int D, typename pop = real> struct Impl {
         real *dst = A;
         EventPair ep;
         if (h->timing && h->opt.proj_iters > 0) timing_begin(h, ep, 3, h->opt.proj_iters);
-        for (int it = 0; it < h->opt.proj_iters; ++it) {
-            launch_jacobi(h, p, src, dst);
+        for (int it = 0; it < h->opt.proj_iters;) {
+            if (jpair_on(h) && it + 1 < h->opt.proj_iters) {
+                launch_jpair(h, p, src, dst);
+                it += 2;
+            } else {
+                launch_jacobi(h, p, src, dst);
+                it += 1;
+            }
             h->launches++;
             src = dst;
             dst = (dst == A) ? B : A;

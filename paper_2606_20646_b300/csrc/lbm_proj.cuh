@@ -243,7 +243,10 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
             real acc = r[j][i];
             #pragma unroll
             for (int q = 0; q < Q; ++q) acc += ((cut[j] >> q) & 1) ? real(0) : nb[j][q][i];
-            out[i] = (real(1) - beta) * dold[j][i] + w * acc;
+            // FP32: the rounding of fma(w, acc, (1 - beta) d) spelled out, which the two-sweep kernel
+            // repeats; FP64: separate products, as the oracle
+            if constexpr (sizeof(real) == 4) out[i] = __fmaf_rn(w, acc, __fmul_rn(real(1) - beta, dold[j][i]));
+            else out[i] = (real(1) - beta) * dold[j][i] + w * acc;
         }
         st_vec<V, real>(dout + (long long)V * node[j], out);
     }

@@ -90,7 +90,8 @@ LAYOUT = {"planes": 0, "nodes": 1}
 
 class lbm_tuning(C.Structure):
     _fields_ = [("windows_per_warp", C.c_int), ("jacobi_segments", C.c_int), ("link_block", C.c_int),
-                ("candidates", C.c_int), ("ms_per_step", C.c_double), ("default_ms_per_step", C.c_double)]
+                ("jacobi_sweeps", C.c_int), ("candidates", C.c_int), ("ms_per_step", C.c_double),
+                ("default_ms_per_step", C.c_double)]
 
 
 # symbol -> (restype, argtypes); every entry point declared in include/lbm.h
@@ -350,16 +351,18 @@ class Simulation:
         return self
 
     # -- tile shapes -----------------------------------------------------------------------------
-    _TUNE_KEYS = ("windows_per_warp", "jacobi_segments", "link_block", "candidates", "ms_per_step",
-                  "default_ms_per_step")
+    _TUNE_KEYS = ("windows_per_warp", "jacobi_segments", "link_block", "jacobi_sweeps", "candidates",
+                  "ms_per_step", "default_ms_per_step")
 
     def get_tuning(self) -> dict:
         t = lbm_tuning()
         _check(load_library().lbm_get_tuning(self.h, C.byref(t)), "lbm_get_tuning")
-        return {k: getattr(t, k) for k in self._TUNE_KEYS[:3]}
+        return {k: getattr(t, k) for k in self._TUNE_KEYS[:4]}
 
-    def set_tuning(self, windows_per_warp: int = 0, jacobi_segments: int = 0, link_block: int = 0):
-        t = lbm_tuning(windows_per_warp, jacobi_segments, link_block, 0, 0.0, 0.0)
+    def set_tuning(self, windows_per_warp: int = 0, jacobi_segments: int = 0, link_block: int = 0,
+                   jacobi_sweeps: int = 0):
+        """Tile shapes (0: the default); jacobi_sweeps: sweeps per Jacobi launch, 2 or 1."""
+        t = lbm_tuning(windows_per_warp, jacobi_segments, link_block, jacobi_sweeps, 0, 0.0, 0.0)
         _check(load_library().lbm_set_tuning(self.h, C.byref(t)), "lbm_set_tuning")
         return self
 

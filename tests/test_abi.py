@@ -110,7 +110,7 @@ def test_new_entry_points_refuse_bad_arguments_without_gpu(lib):
     """Tuning, autotuner, saved states and reverse mode check their arguments before any device
     work: a null handle or buffer is LBM_ERR_ARG."""
     from paper_2606_20646_b300 import lbm
-    t = lbm.lbm_tuning(0, 0, 0, 0, 0.0, 0.0)
+    t = lbm.lbm_tuning(0, 0, 0, 0, 0, 0.0, 0.0)
     assert lib.lbm_set_tuning(None, C.byref(t)) == -1
     assert lib.lbm_get_tuning(None, C.byref(t)) == -1
     assert lib.lbm_autotune(None, 20, None, None) == -1

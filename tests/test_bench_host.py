@@ -26,6 +26,7 @@ def test_algorithmic_bytes_per_node():
     assert b.recompute_bytes_per_node(3, 4) == 625 + 36
     # Jacobi sweep: correction vector (padded to 4) read and written, residual vector, flags
     assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 + 1 == 49
+    assert b.jacobi_bytes_per_node(3, 4, 2) == 24.5
     # the method's figure: u* in the population precision (the coverage contract's 601 B in 3D FP32)
     assert b.method_bytes_per_node(3, 4) == 601
     assert b.method_bytes_per_node(3, 2) == 2 * 72 * 2 + 2 * 3 * 2 + 1
