@@ -224,7 +224,7 @@ typedef struct lbm_kernel_time {
     double projection_ms;     /* projection, repair and reset kernels             */
     long long stream_collide_launches, cutlink_launches, projection_launches;
     double jacobi_ms;         /* damped-Jacobi sweeps alone (part of projection_ms) */
-    long long jacobi_launches;
+    long long jacobi_launches; /* the sweeps jacobi_ms covers (two per launch with two-sweep launches) */
 } lbm_kernel_time;
 
 typedef struct lbm_handle lbm_handle;

@@ -82,7 +82,7 @@ __device__ __forceinline__ int proj_degree(int D, unsigned cut, uint8_t dm) {
 // Damped Jacobi on u from u0 equals damped Jacobi on the correction d = u - u0 from 0 with this
 // right-hand side, so the sweeps can run on d in the population precision.
 template <typename real, int D>
-__global__ void __launch_bounds__(128) k_proj_residual(const ProjArgs<real> a) {
+__global__ void __launch_bounds__(128, 6) k_proj_residual(const ProjArgs<real> a) {
     TLV_NODE_PROLOGUE(a)
     const long long P = a.b.npad;
     const unsigned cut = fl & kCutMask;

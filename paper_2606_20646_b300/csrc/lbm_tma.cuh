@@ -490,7 +490,7 @@ __device__ __forceinline__ void collide_window(const StepArgs<float> &a, const R
 // barrier (bounded) before computing it, so no warp can leave while one of its copies is in flight.
 // REPAIR: the repair step of a projection step (repair_staged) instead of the plain collision.
 template <int D, typename pop = float, int NW = kTmaWindows<pop>, bool REPAIR = false>
-__global__ void __launch_bounds__(32, REPAIR ? 12 : 16) k_stream_collide_tma(const StepArgs<float> a,
+__global__ void __launch_bounds__(32, 16) k_stream_collide_tma(const StepArgs<float> a,
                                                               const __grid_constant__ TmaMaps maps,
                                                               const RepairArgs rp) {
     using L = TmaLayout<D, sizeof(pop)>;
