@@ -69,6 +69,7 @@ static void carve_solver(lbm_handle *h, char *base, size_t *bytes) {
     h->l_rec = c.take<char>((size_t)K * nc * rs);
     h->l_fo = c.take<char>((size_t)2 * K * nc * rs);
     h->l_bvec = rs == 4 ? c.take<float4>(nc) : nullptr;
+    h->l_cu = rs == 4 ? c.take<float>(nc) : nullptr;
     h->l_gsum = (rs == 4 && h->has_neumann_bc) ? c.take<float>((size_t)8 * nc) : nullptr;
     if (h->has_neumann_bc) {
         h->l_sidx = c.take<int>((size_t)kLsqCap * nc);

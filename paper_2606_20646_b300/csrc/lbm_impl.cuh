@@ -105,6 +105,7 @@ struct lbm_handle {
     double *l_eta = nullptr, *l_Xb = nullptr, *l_Nb = nullptr, *l_tan = nullptr;
     void *l_h = nullptr, *l_w = nullptr, *l_rec = nullptr, *l_fo = nullptr;
     float4 *l_bvec = nullptr;  // FP32 forms: per-link geometric vector of the boundary profile
+    float *l_cu = nullptr;     // FP32 forms: per-link coefficient of the upstream term added by the gather
     float *l_gsum = nullptr;   // FP32 forms with Neumann links: per-link tangent-image sums (8 floats)
     void *u0 = nullptr, *u1 = nullptr;  // projection warm starts (displacement-accumulator layout)
     double *partial = nullptr, *mean = nullptr, *staging = nullptr;
@@ -389,6 +390,7 @@ template <typename real, int D, typename pop = real> struct Impl {
         L.w = static_cast<real *>(h->l_w);
         L.rec = static_cast<real *>(h->l_rec);
         L.fo = static_cast<real *>(h->l_fo);
+        L.cu = h->l_cu;
         L.bvec = h->l_bvec;
         L.ncut = h->n_cut;
         return L;
@@ -406,6 +408,7 @@ template <typename real, int D, typename pop = real> struct Impl {
         a.ustar = static_cast<real *>(h->ustar);
         a.un = static_cast<real *>(h->un);
         a.lrec = static_cast<const real *>(h->l_rec);
+        a.lcu = h->l_cu;
         a.lfo = static_cast<real *>(h->l_fo);
         a.vst = static_cast<real *>(h->vst);
         a.Gst = static_cast<real *>(h->Gst);
@@ -545,6 +548,12 @@ template <typename real, int D, typename pop = real> struct Impl {
             h->box, h->seg, (int)h->nseg, h->flags, h->dmask, h->lstart, levelset_view(h), h->dbcs, h->nbc,
             links(h), h->status);
         CKL();
+        if constexpr (sizeof(real) == 4) {
+            if (h->n_cut > 0) {
+                k_link_cu<D><<<grid_for(h->n_cut, 256), 256, 0, h->stream>>>(links(h), h->flags, h->dbcs);
+                CKL();
+            }
+        }
         return setup_jpair(h);
     }
 

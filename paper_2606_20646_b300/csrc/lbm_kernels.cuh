@@ -348,6 +348,8 @@ template <typename real> struct LinkGeom {
     real *rec;          // [ncut*K] reconstructed incoming populations for the next gather (link-major)
     real *fo;           // [ncut*2K] f*_c(m) then f*_{c^1}(m) of the link's node after the last collision
     float4 *bvec;       // [ncut] FP32 forms: the link's geometric vector for its boundary profile
+    float *cu;          // [ncut] FP32 forms: D_b,v (1 - 2 eta) of an eta < 1/2 link with an active upstream
+                        // node, else 0; the next gather adds its term D_b (1 - 2 eta) f*_c(m - e_c)
     long long ncut;
 };
 
@@ -686,6 +688,8 @@ template <typename real> struct StepArgs {
     real *ustar;
     real *un;
     const real *lrec;  // per cut link: reconstructed incoming populations (K), read by the gather
+    const float *lcu;  // per cut link, FP32 forms: coefficient of the upstream term the gather adds
+                       // (LinkGeom::cu), null in the FP64 form
     real *lfo;         // per cut link: f*_c(m), f*_{c^1}(m) (2K), written by the collision kernels
     real *vst, *Gst;   // projection steps: v^n and G^n = F^n - I (D and D*D planes)
     real *u0;          // projection steps: u^n (displacement-accumulator layout)
@@ -805,14 +809,25 @@ __device__ __forceinline__ void gather(const StepArgs<real> &a, int node, int x,
         }
     }
     if (cut) {
-        // the populations a cut link leaves unknown arrive reconstructed by the link kernel
+        // the populations a cut link leaves unknown arrive reconstructed by the link kernel; an eta < 1/2
+        // link with an active upstream node m - e_c gets its upstream term here, from the value that
+        // direction c pulls from that node (slot c = q^1, pulled: link (m, q) is not cut)
         const long long l0 = __ldg(a.lstart + node);
         #pragma unroll
         for (int q = 0; q < Q; ++q)
             if ((cut >> (q ^ 1)) & 1) {
                 long long l = link_of(l0, cut, q ^ 1);
                 TLV_BOUND(l, a.ncut, a.status);
-                vload<K>(a.lrec + l * K, &f[q * K]);
+                real r[K];
+                vload<K>(a.lrec + l * K, r);
+                if constexpr (sizeof(real) == 4) {
+                    const float cv = a.lcu ? __ldg(a.lcu + l) : 0.0f;
+                    if (cv != 0.0f)
+                        #pragma unroll
+                        for (int k = 0; k < K; ++k) r[k] += (k < D ? cv : -cv) * f[(q ^ 1) * K + k];
+                }
+                #pragma unroll
+                for (int k = 0; k < K; ++k) f[q * K + k] = r[k];
             }
     }
     }

@@ -195,6 +195,19 @@ __global__ void __launch_bounds__(256) k_link_sums(const CutArgs<float> a, float
     }
 }
 
+// Coefficient of the upstream term of each FP32 link (LinkGeom::cu): D_b,v (1 - 2 eta) for eta < 1/2
+// with an active upstream node m - e_c, else 0; D_b,v = +1 for Neumann, -1 for Dirichlet links.
+template <int D>
+__global__ void k_link_cu(LinkGeom<float> L, const uint8_t *__restrict__ flags, const BCD *__restrict__ bcs) {
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= L.ncut) return;
+    const int q = L.q[l];
+    const float eta = (float)L.eta[l];
+    const bool up = !((flags[L.node[l]] >> (q ^ 1)) & 1);
+    const float dv = bcs[L.bc[l]].kind != 0 ? 1.0f : -1.0f;  // kind 1: Neumann
+    L.cu[l] = (up && !(eta >= 0.5f)) ? dv * (1.0f - 2.0f * eta) : 0.0f;
+}
+
 // One thread per cut link: boundary values, the traction inversion of a Neumann link (its tangent
 // images from k_link_sums), and the reconstruction of the K incoming components.
 template <int D, typename pop>
@@ -208,23 +221,13 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
     const BCTimeF &tb = bt.bc[__ldg(a.L.bc + l)];
     const int mnode = __ldg(a.L.node + l);
     const float eta = (float)__ldg(a.L.eta + l);
-    // operands of the reconstruction, loaded first: the node's kept pair f*_c(m), f*_{c^1}(m) and, for
-    // eta < 1/2 with an active upstream node m + e_{c^1}, that node's f*_c
-    const bool upn = !((__ldg(a.flags + mnode) >> (q ^ 1)) & 1) && !(eta >= 0.5f);
-    float fo[K], fi[K], fu[K];
+    // operands of the reconstruction, loaded first: the node's kept pair f*_c(m), f*_{c^1}(m).  The
+    // upstream node's f*_c, which an eta < 1/2 link with an active upstream node m - e_c needs, is the
+    // value the next gather pulls for direction c at m: that gather adds its term (cu != 0)
+    const float cu = __ldg(a.L.cu + l);
+    float fo[K], fi[K];
     vload<K>(a.L.fo + l * (2 * K), fo);
     vload<K>(a.L.fo + l * (2 * K) + K, fi);
-    if (upn) {
-        int x, y, z;
-        node_xyz(a.b, mnode, x, y, z);
-        int mup = nbr(a.b, mnode, x, y, z, q ^ 1);
-        TLV_BOUND(mup, a.b.npad, a.status);
-        #pragma unroll
-        for (int k = 0; k < K; ++k) fu[k] = pop_ld<float, pop>(a.fstar, (long long)(q * K + k) * a.b.npad + mup);
-    } else {
-        #pragma unroll
-        for (int k = 0; k < K; ++k) fu[k] = fo[k];
-    }
     const float4 gv = __ldg(a.L.bvec + l);
     const float gl[3] = {gv.x, gv.y, gv.z};
     float val[D];  // Dirichlet velocity or Neumann traction at X_b, t^n + dt/2
@@ -341,8 +344,10 @@ __global__ void __launch_bounds__(256) k_links_f32(const CutArgs<float> a, const
         const float Dk = ((k < D) == neu) ? 1.0f : -1.0f;
         if (eta >= 0.5f)
             Rk[k] = (Dk * fo[k] + S[k]) / (2.0f * eta) + (1.0f - 1.0f / (2.0f * eta)) * fi[k];
-        else
-            Rk[k] = Dk * (2.0f * eta * fo[k] + (1.0f - 2.0f * eta) * fu[k]) + S[k];
+        else if (cu != 0.0f)
+            Rk[k] = Dk * (2.0f * eta * fo[k]) + S[k];  // + D_k (1 - 2 eta) f*_c(m - e_c) in the gather
+        else  // no upstream node: f*_c(m) stands in for it
+            Rk[k] = Dk * (2.0f * eta * fo[k] + (1.0f - 2.0f * eta) * fo[k]) + S[k];
     }
     vstore<K>(a.L.rec + l * K, Rk);
 }

@@ -160,13 +160,20 @@ __device__ __forceinline__ void tma_closure(const StepArgs<float> &a, char *wsm,
                 stage_put<D, pop>(wsm, 1, k, lane, pop_ld<float, pop>(fs, (long long)(1 * K + k) * P + node - (a.b.nx - 1)));
     }
     if (!cut) return;
-    #pragma unroll
+    // boundary nodes only: a rolled loop over the directions keeps the kernel's code small
+    #pragma unroll 1
     for (int q = 0; q < Q; ++q) {
         if ((cut >> (q ^ 1)) & 1) {
             float r[K];
             long long l = link_of(l0, cut, q ^ 1);
             TLV_BOUND(l, a.ncut, a.status);
             vload<K>(a.lrec + l * K, r);
+            // an eta < 1/2 link with an active upstream node: its term D_b (1 - 2 eta) f*_c(m - e_c), with
+            // f*_c(m - e_c) the value staged for direction c = q^1 (pulled: link (m, q) is not cut)
+            const float cv = __ldg(a.lcu + l);
+            if (cv != 0.0f)
+                #pragma unroll
+                for (int k = 0; k < K; ++k) r[k] += (k < D ? cv : -cv) * staged<D, pop>(wsm, q ^ 1, k, lane);
             #pragma unroll
             for (int k = 0; k < K; ++k) stage_put<D, pop>(wsm, q, k, lane, r[k]);
         }
