@@ -19,6 +19,8 @@
 
 namespace tlv {
 
+// Tile constants (compile-time; the values below are the measured best: ring depth 4 in 3D and 5 in
+// 2D, 3D tiles of 8 rows and 32 planes, 2D tiles of 32 rows).
 #ifndef TLV_JP_STAGES3
 #define TLV_JP_STAGES3 4
 #endif
@@ -35,7 +37,10 @@ namespace tlv {
 template <int D> constexpr int kJPStages = D == 3 ? TLV_JP_STAGES3 : TLV_JP_STAGES2;
 static_assert(kJPStages<3> >= 4 && kJPStages<2> >= 4, "a stage is refilled two planes behind the plane in use");
 constexpr int kJPDp = 4;      // d' planes kept: p-2 .. p and the next
-constexpr int kJPTy = 8;      // 3D: output rows (y) of a tile; 28 output columns (x); kJPChunk3 planes (z)
+#ifndef TLV_JP_TY
+#define TLV_JP_TY 8
+#endif
+constexpr int kJPTy = TLV_JP_TY;  // 3D: output rows (y) of a tile; 28 output columns (x); kJPChunk3 planes (z)
 constexpr int kJPChunk3 = TLV_JP_CHUNK3;
 constexpr int kJPW2 = 8;      // 2D: warps of a tile, 28 output columns each; kJPChunk2 rows (y)
 constexpr int kJPChunk2 = TLV_JP_CHUNK2;
