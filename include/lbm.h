@@ -323,8 +323,9 @@ int lbm_autotune(lbm_handle *h, int steps, void *scratch, lbm_tuning *out);
 /* Bounded waits (no counterpart in the paper).  The bulk-copy kernels poll the barrier of their
  * copies at most 2^20 times before they latch LBM_DEV_TIMEOUT, wait once more with that limit for
  * every copy they issued, and return without writing (the step is then invalid).  This sets the
- * first wait's limit: 0 makes every first wait run out at once, which tests that path without a
- * fault; a negative value restores 2^20.  Takes effect at the next launch. */
+ * first wait's limit (in the two-sweep Jacobi kernel, every wait's, after which the whole block
+ * stops): 0 makes those waits run out at once, which tests that path without a fault; a negative
+ * value restores 2^20.  Takes effect at the next launch. */
 int lbm_set_wait_limit(lbm_handle *h, int polls);
 
 /* ---- parameters, saved states and reverse mode --------------------------------------------

@@ -93,3 +93,25 @@ def test_bulk_copy_wait_that_runs_out_is_reported():
     sim.set_initial().step(3)
     assert sim.sync(raise_on_status=False) == 0
     sim.close()
+
+
+def test_two_sweep_jacobi_wait_that_runs_out_is_reported():
+    """The two-sweep Jacobi kernel's bounded waits: on a 2D body whose rows (230 nodes) are not a
+    multiple of 16 the fused kernel uses plain loads, so the projection's two-sweep launches are the
+    only kernels that wait for bulk copies.  With the first limit at 0 polls every block gives up at
+    once, votes to stop, waits (with the full limit) for the planes it issued and stores nothing;
+    LBM_DEV_TIMEOUT is reported and the context stays usable."""
+    from paper_2606_20646_b300 import lbm
+    p = I.superellipse_shell_2d(230)
+    sim = lbm.Simulation(p, precision="fp32")
+    assert sim.get_tuning()["jacobi_sweeps"] == 2
+    sim.set_initial()
+    sim.set_wait_limit(0)
+    sim.step(1)                                 # step 0 is a projection step
+    st = sim.sync(raise_on_status=False)
+    assert st & 128
+    sim.close()
+    sim = lbm.Simulation(p, precision="fp32")
+    sim.set_initial().step(3)
+    assert sim.sync(raise_on_status=False) == 0
+    sim.close()
