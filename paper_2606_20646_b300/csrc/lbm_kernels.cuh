@@ -117,14 +117,18 @@ template <typename real, int D>
 __device__ __forceinline__ void un_load(const real *un, long long node, real *hi, real *lo) {
     const real *p = un + (long long)kUnStride<real, D> * node;
     if constexpr (kDispPair<real>) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
         if constexpr (D == 3) {
-            const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-            hi[0] = a.x; hi[1] = a.y; hi[2] = a.z;
-            lo[0] = b.x; lo[1] = b.y; lo[2] = b.z;
-        } else {
-            hi[0] = a.x; hi[1] = a.y; lo[0] = a.z; lo[1] = a.w;
+            // the whole 32-byte record in one 256-bit load (records are 32-byte aligned; read-only here)
+            float w[8];
+            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=f"(w[0]), "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]), "=f"(w[5]), "=f"(w[6]), "=f"(w[7])
+                : "l"(p));
+            hi[0] = w[0]; hi[1] = w[1]; hi[2] = w[2];
+            lo[0] = w[4]; lo[1] = w[5]; lo[2] = w[6];
+            return;
         }
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        hi[0] = a.x; hi[1] = a.y; lo[0] = a.z; lo[1] = a.w;
     } else {
         const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
         hi[0] = a.x; hi[1] = a.y;
