@@ -110,18 +110,18 @@ class Clocks:
 # timed box by its number of windows (segments).
 KERNEL_SOURCES = ["paper_2606_20646_b300/csrc/lbm_tma.cuh", "paper_2606_20646_b300/csrc/lbm_kernels.cuh",
                   "paper_2606_20646_b300/csrc/lbm_device.cuh"]
-TRAFFIC_CAPTURE = {"sources_sha256": "7a5a538ce957ac9a14115e5280b705f6a41074dec975d58ff57d73e857ca2999",
-                   "bytes_per_launch": 375120640 + 265225216, "windows": 30112,
+TRAFFIC_CAPTURE = {"sources_sha256": "2e5642890a287691ab0a67aeee019f2e73c0b5c4ee76206a35ff6ce29f67fa20",
+                   "bytes_per_launch": 375150336 + 265185152, "windows": 30112,
                    "summary": "profiles/k_stream_collide_tma_shell_3d.md"}
 # the same for the BF16-storage fused kernel (two windows per warp)
-BF16_TRAFFIC_CAPTURE = {"sources_sha256": "7a5a538ce957ac9a14115e5280b705f6a41074dec975d58ff57d73e857ca2999",
-                        "bytes_per_launch": 218186240 + 134077440, "windows": 30112,
+BF16_TRAFFIC_CAPTURE = {"sources_sha256": "2e5642890a287691ab0a67aeee019f2e73c0b5c4ee76206a35ff6ce29f67fa20",
+                        "bytes_per_launch": 218193408 + 133783296, "windows": 30112,
                         "summary": "profiles/k_stream_collide_tma_bf16_shell_3d.md"}
 # the same for the reverse step on the clamped cube (128^3, the timed size itself)
 ADJ_SOURCES = ["paper_2606_20646_b300/csrc/lbm_adjoint.cuh", "paper_2606_20646_b300/csrc/lbm_tma.cuh",
                "paper_2606_20646_b300/csrc/lbm_kernels.cuh"]
-ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "46375e086e28c207134357eaea1edc882ef7803140b0e7422cf9df1b95d45347",
-                       "bytes_per_launch": 741909589 + 576067157, "windows": None,
+ADJ_TRAFFIC_CAPTURE = {"sources_sha256": "1f155594c04ba11848b4cd93e824e9713aa5740703e15a8ba72426b1ee6c3a97",
+                       "bytes_per_launch": 741957632 + 576005973, "windows": None,
                        "summary": "profiles/k_adj_step_tma_inclusion_cube.md"}
 
 
