@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-errors", action="store_true", help="skip the FP32/FP64 errors against the oracle")
     ap.add_argument("--no-batch", action="store_true", help="skip the packed 2D multi-specimen measurement")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--batch-specimens", type=int, default=96, help="specimens of the packed 2D batch")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode measurement")
     ap.add_argument("--adj-n", type=int, default=128)
     ap.add_argument("--adj-steps", type=int, default=3000)
@@ -455,7 +456,7 @@ def run_ours(args, world, rank, local):
     # ---- many 2D specimens packed into one body, 1000 steps as one CUDA graph -------------------
     batch = None
     if not args.no_batch:
-        packed, specs = I.batch_2d(steps=args.batch_steps)
+        packed, specs = I.batch_2d(n_spec=args.batch_specimens, steps=args.batch_steps)
         sim = lbm.Simulation(packed, precision="fp32", device=dev)
         inf_b = sim.info()
         sim.set_initial()
