@@ -57,31 +57,23 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
-                                            int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // the sweep's blend (1 - beta) d + w acc, rounded as in k_jacobi
 __device__ __forceinline__ float jp_blend(float beta1, float dold, float w, float acc) {
     return __fmaf_rn(w, acc, __fmul_rn(beta1, dold));
 }
 
-// tensor maps of the sweep: the two correction buffers and the residual
+// tensor maps of the sweep: the two correction buffers and the residual (2D: r for the first 768
+// floats of a staged row, rt for its tail)
 struct JPairMaps {
     CUtensorMap d[2];
-    CUtensorMap r;
+    CUtensorMap r, rt;
 };
 
 template <int D> struct JPairLayout;
 template <> struct JPairLayout<3> {
     static constexpr int RD = kJPTy + 4, RR = kJPTy + 2;  // staged rows of d and of r / d'
-    static constexpr int d_bytes = RD * 32 * 16;           // box (4, 32, RD, 1) floats
-    static constexpr int r_bytes = RR * 32 * 16;           // box (4, 32, RR, 1)
+    static constexpr int d_bytes = RD * 32 * 16;           // box (128, RD, 1) floats
+    static constexpr int r_bytes = RR * 32 * 16;           // box (128, RR, 1)
     static constexpr int stage_bytes = d_bytes + r_bytes;
     static constexpr int dp_bytes = RR * 32 * 16;
     static constexpr int threads = RR * 32;
@@ -89,13 +81,17 @@ template <> struct JPairLayout<3> {
 };
 template <> struct JPairLayout<2> {
     static constexpr int NP = 28 * kJPW2 + 4;                        // staged positions of a row
-    static constexpr int d_bytes = ((NP * 8 + 127) / 128) * 128;     // box (2, NP, 1) floats
-    static constexpr int r_bytes = ((NP * 16 + 127) / 128) * 128;    // box (4, NP, 1)
+    static constexpr int d_bytes = ((NP * 8 + 127) / 128) * 128;     // box (NP, 1) of 8-byte pairs
+    static constexpr int r_bytes = ((NP * 16 + 127) / 128) * 128;    // boxes (256, 1) x 3 and (r_tail, 1) floats
+    static constexpr int r_tail = 4 * NP - 768;
     static constexpr int stage_bytes = d_bytes + r_bytes;
     static constexpr int dp_bytes = ((NP * 8 + 127) / 128) * 128;
     static constexpr int threads = kJPW2 * 32;
     static constexpr int smem_bytes = kJPStages<2> * stage_bytes + kJPDp * dp_bytes + kJPStages<2> * 8;
 };
+static_assert(JPairLayout<2>::r_tail > 0 && JPairLayout<2>::r_tail <= 256 && JPairLayout<2>::r_tail % 4 == 0 &&
+                  3072 + 4 * JPairLayout<2>::r_tail <= JPairLayout<2>::r_bytes,
+              "a staged residual row is three 256-float boxes and a tail box");
 
 // tiles of the box: (ntx, nty, ntz) in 3D, (ntx, nty) in 2D; t = tx + ntx (ty + nty tz)
 __host__ __device__ inline void jp_tile_grid(int D, int nx, int ny, int nz, int &ntx, int &nty, int &ntz) {
@@ -173,8 +169,9 @@ static __global__ void __launch_bounds__(JPairLayout<3>::threads, 2)
         char *st = smem + s * L::stage_bytes;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bars + s, tx);
-        if (!dzero) tma_load_4d(st, &dmap, bars + s, 0, x0 - 2, y0 - 2, p);
-        tma_load_4d(st + L::d_bytes, &rmap, bars + s, 0, x0 - 2, y0 - 1, p);
+        // float coordinate 4 (x0 - 2): a multiple of 4 floats, as the copies need
+        if (!dzero) tma_load_3d(st, &dmap, bars + s, 4 * (x0 - 2), y0 - 2, p);
+        tma_load_3d(st + L::d_bytes, &rmap, bars + s, 4 * (x0 - 2), y0 - 1, p);
     };
     auto wait = [&](int p, int lim) {
         const int j = p - p0;
@@ -267,7 +264,8 @@ static __global__ void __launch_bounds__(JPairLayout<3>::threads, 2)
 // whole number of 16-byte units; x0 - 2 is even, as the 8-byte elements need.
 static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
     k_jacobi_pair2(const ProjArgs<float> a, const __grid_constant__ CUtensorMap dmap,
-                   const __grid_constant__ CUtensorMap rmap, int dzero, float *__restrict__ dout,
+                   const __grid_constant__ CUtensorMap rmap, const __grid_constant__ CUtensorMap rtmap, int dzero,
+                   float *__restrict__ dout,
                    const int *__restrict__ tiles, int spin) {
     using L = JPairLayout<2>;
     extern __shared__ __align__(128) char smem[];
@@ -299,7 +297,10 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bars + s, tx);
         if (!dzero) tma_load_2d(st, &dmap, bars + s, x0 - 2, p);
-        tma_load_3d(st + L::d_bytes, &rmap, bars + s, 0, x0 - 2, p);
+        // the residual row in four pieces at 1 KB-aligned offsets (a box holds at most 256 floats)
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_2d(st + L::d_bytes + 1024 * k, &rmap, bars + s, 4 * (x0 - 2) + 256 * k, p);
+        tma_load_2d(st + L::d_bytes + 3072, &rtmap, bars + s, 4 * (x0 - 2) + 768, p);
     };
     auto wait = [&](int p, int lim) {
         const int j = p - p0;
