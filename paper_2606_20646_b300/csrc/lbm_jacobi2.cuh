@@ -279,7 +279,6 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
     const int y1 = min(y0 + kJPChunk2, ny);
     const int i = 28 * warp + lane;  // staged position
     const int x = x0 - 2 + i;
-    const bool col_in = x >= 0 && x < nx;
     // d' positions 1 .. NP-2 split between the warps without overlap; d'' positions 2 .. NP-3
     const bool dp_mine = (lane >= 2 && lane <= 29) || (warp == 0 && lane == 1) || (warp == kJPW2 - 1 && lane == 30);
     const bool out_mine = lane >= 2 && lane <= 29;
@@ -313,9 +312,6 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
     auto dps = [&](int p) {
         return reinterpret_cast<float2 *>(smem + kJPStages<2> * L::stage_bytes + ((p - p0) & (kJPDp - 1)) * L::dp_bytes);
     };
-    auto flag_at = [&](int p) -> uint8_t {
-        return (col_in && p >= 0 && p < ny) ? __ldg(a.flags + (x + nx * p)) : uint8_t(0);
-    };
     auto f4 = [](float2 v) { return make_float4(v.x, v.y, 0.0f, 0.0f); };
     if (threadIdx.x == 0)
         for (int p = p0; p <= min(p0 + kJPStages<2> - 2, plast); ++p) issue(p);
@@ -323,7 +319,6 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
     bool ok = true;
     for (int p = p0; p <= p0 + 1 && ok; ++p)
         if ((ok = wait(p, spin))) done = p;
-    uint8_t f_prev = 0, f_cur = flag_at(y0 - 1), f_next = flag_at(y0);
     const float2 zero2 = make_float2(0.f, 0.f);
     for (int y = y0 - 1; y <= y1; ++y) {
         if (ok && (ok = wait(y + 1, spin))) done = y + 1;
@@ -331,9 +326,10 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
             const float2 *D0 = dst(y), *Dm = dst(y - 1), *Dp = dst(y + 1);
             const float2 own = dzero ? zero2 : D0[i];
             float2 out = own;
-            if (f_cur & kActive) {
+            {
+                // 2D residual record (r_1, r_2, w, cut bits); w = 0 at inactive and out-of-box positions
                 const float4 r2 = rst(y)[i];
-                const float4 r = make_float4(r2.x, r2.y, 0.0f, r2.z);  // 2D residual: (r_1, r_2, w, 0)
+                const float4 r = make_float4(r2.x, r2.y, 0.0f, r2.z);
                 if (r.w > 0.0f) {
                     float4 nb[4];
                     if (dzero) {
@@ -345,7 +341,7 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
                         nb[2] = f4(Dp[i]);
                         nb[3] = f4(Dm[i]);
                     }
-                    const float3 o = jp_update<4>(beta1, f4(own), r, f_cur & kCutMask, nb);
+                    const float3 o = jp_update<4>(beta1, f4(own), r, __float_as_uint(r2.w) & kCutMask, nb);
                     out = make_float2(o.x, o.y);
                 }
             }
@@ -355,13 +351,13 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
             ok = false;
             break;
         }
-        if (y - 1 >= y0 && out_mine && (f_prev & kActive)) {
+        if (y - 1 >= y0 && out_mine) {
             const float4 r2 = rst(y - 1)[i];
             const float4 r = make_float4(r2.x, r2.y, 0.0f, r2.z);
             if (r.w > 0.0f) {
                 const float2 *P0 = dps(y - 1), *Pm = dps(y - 2), *Pp = dps(y);
                 const float4 nb[4] = {f4(P0[i + 1]), f4(P0[i - 1]), f4(Pp[i]), f4(Pm[i])};
-                const float3 v = jp_update<4>(beta1, f4(P0[i]), r, f_prev & kCutMask, nb);
+                const float3 v = jp_update<4>(beta1, f4(P0[i]), r, __float_as_uint(r2.w) & kCutMask, nb);
                 *reinterpret_cast<float2 *>(dout + 2LL * (x + nx * (y - 1))) = make_float2(v.x, v.y);
             }
         }
@@ -369,9 +365,6 @@ static __global__ void __launch_bounds__(JPairLayout<2>::threads, 4)
             issue(y + kJPStages<2> - 2);
             issued = y + kJPStages<2> - 2;
         }
-        f_prev = f_cur;
-        f_cur = f_next;
-        f_next = flag_at(y + 2);
     }
     if (!ok && threadIdx.x == 0) {
         set_status(a.status, kStTimeout);

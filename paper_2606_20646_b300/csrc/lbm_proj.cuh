@@ -22,7 +22,7 @@ template <typename real> struct ProjArgs {
     const BCD *bcs;
     const real *Gst;
     const real *u0;    // warm start (displacement-accumulator layout: FP64 planes or FP32 pairs)
-    real *resid;       // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start
+    real *resid;       // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start (FP32 2D: the 4th the cut bits)
     double t, beta;
     int *status;
 };
@@ -157,6 +157,9 @@ __global__ void __launch_bounds__(128, 6) k_proj_residual(const ProjArgs<real> a
     #pragma unroll
     for (int i = 0; i < D; ++i) out[i] = (real)r[i] + rf[i];
     out[D] = deg > 0 ? (real)a.beta / (real)deg : real(0);
+    // FP32 2D: the record's spare fourth value carries the node's cut-direction bits, so the
+    // two-sweep kernel has them with the staged residual row and loads no flag bytes
+    if constexpr (D == 2 && sizeof(real) == 4) out[3] = __uint_as_float(cut);
     st_vec<4, real>(a.resid + 4 * (long long)node, out);
 }
 
