@@ -237,7 +237,9 @@ static __global__ void __launch_bounds__(JPairLayout<3>::threads, 2)
                 const int o = warp * 32 + lane;
                 const float4 nb[6] = {P0[o + 1], P0[o - 1], P0[o + 32], P0[o - 32], Pp[o], Pm[o]};
                 const float3 v = jp_update<6>(beta1, P0[o], r, f_prev & kCutMask, nb);
-                *reinterpret_cast<float4 *>(dout + 4LL * (x + nx * (y + ny * (z - 1)))) = make_float4(v.x, v.y, v.z, 0.0f);
+                // the fourth value: the node's cut bits, which a one-sweep launch after this one reads
+                *reinterpret_cast<float4 *>(dout + 4LL * (x + nx * (y + ny * (z - 1)))) =
+                    make_float4(v.x, v.y, v.z, __uint_as_float(f_prev & kCutMask));
             }
         }
         // the stage of plane z-2 is free (its d fed d'(z-1), its r d''(z-2)): refill it with the plane

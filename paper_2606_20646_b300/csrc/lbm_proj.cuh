@@ -200,11 +200,15 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
             ln[j][q] = l < 0 ? 0 : (l >= P ? (int)(P - 1) : l);  // only inactive nodes can point outside
         }
     }
+    // FP32 3D: the node's cut-direction bits travel in d's spare fourth value, written by the first
+    // sweep of a solve (from the flag byte) and copied by every later one, so only the first sweep
+    // loads flag bytes
+    constexpr bool kCutInD = sizeof(real) == 4 && D == 3;
     real r[S][4], dold[S][V], nb[S][Q][V];
     unsigned cut[S];
     #pragma unroll
     for (int j = 0; j < S; ++j) {
-        cut[j] = __ldg(a.flags + node[j]) & kCutMask;
+        if (!kCutInD || !din) cut[j] = __ldg(a.flags + node[j]) & kCutMask;
         ld_vec<4, real>(a.resid + 4LL * node[j], r[j]);
         if (din) {
             ld_vec<V, real>(din + (long long)V * node[j], dold[j]);
@@ -213,10 +217,12 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
                 if (q >= 2 || !shx) ld_vec<V, real>(din + (long long)V * ln[j][q], nb[j][q]);
             if constexpr (shx) {
                 // the x neighbours are the neighbouring lanes' own vectors; lane 31 loads node + 1 and
-                // lane 0 node - 1 (the other lanes load their own node again, an L1 hit)
+                // lane 0 node - 1
                 real e[V];
-                const int ie = lane == 31 ? node[j] + 1 : (lane == 0 ? (node[j] > 0 ? node[j] - 1 : 0) : node[j]);
-                ld_vec<V, real>(din + (long long)V * ie, e);
+                #pragma unroll
+                for (int i = 0; i < V; ++i) e[i] = real(0);
+                const int ie = lane == 31 ? node[j] + 1 : (node[j] > 0 ? node[j] - 1 : 0);
+                if (lane == 0 || lane == 31) ld_vec<V, real>(din + (long long)V * ie, e);
                 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const real dn = __shfl_down_sync(0xffffffffu, dold[j][i], 1);
@@ -232,6 +238,12 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
                 #pragma unroll
                 for (int q = 0; q < Q; ++q) nb[j][q][i] = real(0);
             }
+        }
+    }
+    if constexpr (kCutInD) {
+        if (din) {
+            #pragma unroll
+            for (int j = 0; j < S; ++j) cut[j] = __float_as_uint(dold[j][3]) & kCutMask;
         }
     }
     #pragma unroll
@@ -251,6 +263,7 @@ __device__ __forceinline__ void jacobi_segments(const ProjArgs<real> &a, const r
             if constexpr (sizeof(real) == 4) out[i] = __fmaf_rn(w, acc, __fmul_rn(real(1) - beta, dold[j][i]));
             else out[i] = (real(1) - beta) * dold[j][i] + w * acc;
         }
+        if constexpr (kCutInD) out[3] = __uint_as_float(cut[j]);
         st_vec<V, real>(dout + (long long)V * node[j], out);
     }
 }
