@@ -24,9 +24,11 @@ def test_algorithmic_bytes_per_node():
     # reverse step: gbar read and written, F and dL/du* read, dL/dmu (FP64) read and written, flags
     assert b.adjoint_bytes_per_node(3, 4) == 576 + 36 + 12 + 16 + 1 == 641
     assert b.recompute_bytes_per_node(3, 4) == 625 + 36
-    # Jacobi sweep: correction vector (padded to 4) read and written, residual vector, flags
-    assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 + 1 == 49
-    assert b.jacobi_bytes_per_node(3, 4, 2) == 24.5
+    # Jacobi sweep: correction vector (padded to 4) read and written, residual vector (FP64: flags)
+    assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 == 48
+    assert b.jacobi_bytes_per_node(3, 4, 2) == 24
+    assert b.jacobi_bytes_per_node(2, 4, 2) == (2 * 2 * 4 + 4 * 4) / 2
+    assert b.jacobi_bytes_per_node(3, 8) == 2 * 4 * 8 + 4 * 8 + 1
     # the method's figure: u* in the population precision (the coverage contract's 601 B in 3D FP32)
     assert b.method_bytes_per_node(3, 4) == 601
     assert b.method_bytes_per_node(3, 2) == 2 * 72 * 2 + 2 * 3 * 2 + 1
