@@ -1511,8 +1511,7 @@ __global__ void __launch_bounds__(256) k_cutlinks(const CutArgs<real> a) {
 // d holds kDV values per node (D components, padded to 2 or 4), the residual 4 values per node,
 // (r_1..r_D, w) padded, with the sweep weight w = beta/deg (0 where a node is inactive or has no
 // edge).  Inactive nodes keep d = 0 in both buffers (the storage is zeroed and sweeps write active
-// nodes only).  The FP32 forms use the spare slots for the node's cut-direction bits (bit pattern
-// of an unsigned): in 3D the fourth value of d, in 2D the fourth value of the residual.
+// nodes only).
 template <int D> constexpr int kDV = D == 3 ? 4 : 2;
 
 }  // namespace tlv

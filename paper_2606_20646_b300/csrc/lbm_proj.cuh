@@ -22,7 +22,10 @@ template <typename real> struct ProjArgs {
     const BCD *bcs;
     const real *Gst;
     const real *u0;    // warm start (displacement-accumulator layout: FP64 planes or FP32 pairs)
-    real *resid;       // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start (FP32 2D: the 4th the cut bits)
+    // per node (r_1..r_D, w) with w = beta/deg, 4 values: residual at the warm start.  The FP32
+    // forms use spare slots for the node's cut-direction bits (bit pattern of an unsigned): in 2D
+    // the residual's fourth value, in 3D the fourth value of the correction d
+    real *resid;
     double t, beta;
     int *status;
 };
