@@ -153,6 +153,51 @@ def test_single_node_collision_brute_force(D):
     assert np.allclose(out.sum(0)[D:], S[D:], atol=1e-14)
 
 
+def _uniform_damped(D, c, b, gamma=10.0, n=6, t_end=0.5):
+    """Periodic box at rest-frame F = I with a uniform velocity: v(0) and v(t_end) from the oracle."""
+    dx = 1.0 / n
+    p = I.Problem(name=f"uniform_damped_{D}d", dim=D, n=(n, n, n if D == 3 else 1), dx=dx, origin=(0, 0, 0),
+                  periodic=(True, True, True), mu=1.0, lam=2.0,
+                  options=I.Options(c=c, omega=1.8, gamma=gamma, proj_every=0, body_force=tuple(b) + (0.0,) * (3 - len(b))))
+    I._rest_fields(p)
+    v0 = np.array([0.01, -0.02, 0.015])[:D]
+    for i in range(D):
+        p.v0[i] = v0[i]
+    o = oracle.Oracle(p)
+    o.set_initial()
+    va = o.fields()[0].reshape(D, -1).copy()
+    steps = int(round(t_end / p.dt))
+    o.step(steps)
+    v, F, _u = o.fields()
+    return p.dt, steps, va, v.reshape(D, -1), F.reshape(D * D, -1)
+
+
+@pytest.mark.parametrize("D,b", [(2, (0.0, 0.0)), (3, (0.3, 0.0, -0.2))])
+def test_uniform_damped_state_decays_by_the_trapezoidal_factor(D, b):
+    """Damped momentum balance dv/dt = b - gamma v (Sec. 2, B = (b - gamma v, 0)) for a uniform state
+    at F = I, where P(I) = 0 and streaming changes nothing: the recovery with the half-step source
+    (Eq. state-recovery-general) and the collision's momentum shift dt*B make one full step the
+    trapezoidal map v' (1 + gamma dt/2) = v (1 - gamma dt/2) + dt b.  Its closed form
+    v_n = b/gamma + (v_0 - b/gamma) r^n, r = (1 - gamma dt/2)/(1 + gamma dt/2), holds to round-off,
+    and v(t) converges to the ODE's exp(-gamma t) solution at second order in dt (a full-step
+    factor 1 + gamma dt in the recovery, or a dropped half-step source, is first order)."""
+    gamma, t_end = 10.0, 0.5
+    b = np.asarray(b, dtype=float)
+    vinf = b / gamma
+    errs = []
+    for c in (10.0, 20.0, 40.0):
+        dt, steps, va, v, F = _uniform_damped(D, c, tuple(b), gamma=gamma, t_end=t_end)
+        assert np.ptp(v, axis=1).max() < 1e-15  # stays uniform
+        assert np.abs(F - np.eye(D).reshape(-1, 1)).max() < 1e-14  # F stays I
+        r = (1.0 - 0.5 * gamma * dt) / (1.0 + 0.5 * gamma * dt)
+        expect = vinf[:, None] + (va - vinf[:, None]) * r ** steps
+        assert np.allclose(v, expect, rtol=1e-12, atol=1e-15)
+        exact = vinf[:, None] + (va - vinf[:, None]) * math.exp(-gamma * steps * dt)
+        errs.append(np.abs(v - exact).max())
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(orders) > 1.9, (errs, orders)
+
+
 # --------------------------------------------------------------------------- bulk dynamics
 
 def test_shear_wave_second_order_convergence():
