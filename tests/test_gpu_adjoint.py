@@ -79,7 +79,7 @@ def _adjoint(p, ut, act, mu0, precision):
     L.backward()
     assert sim.sync(raise_on_status=False) == 0
     sim.close()
-    return float(L), mu.grad.cpu().numpy(), b.grad.numpy()
+    return float(L.detach()), mu.grad.cpu().numpy(), b.grad.numpy()
 
 
 def _fd_mu(forward, p, ut, mu0, node, act, rel=1e-4):
