@@ -435,6 +435,33 @@ def tube_3d(nxy: int = 76, nz: int = 300, dx: float = 0.01) -> Problem:
     return p
 
 
+def rigid_translation(dim: int, anchored: bool, n: Optional[int] = None, proj_every: int = 5,
+                      steps: int = 23) -> Problem:
+    """A disc (2D) or ball (3D) of radius 0.37 in the unit box moving at the uniform velocity
+    vt = (0.01, -0.02, 0.015) with F = I, its surface traction-free; with `anchored`, a hole of
+    radius 0.15 whose surface carries the Dirichlet translation u_D = t vt.  u = vt t, v = vt, F = I
+    is the exact solution (P(I) = 0, zero tractions), kept through projection steps every
+    `proj_every` steps."""
+    n = n if n is not None else (40 if dim == 2 else 20)
+    p = Problem(name=f"rigid_translation_{dim}d{'_anchored' if anchored else ''}", dim=dim,
+                n=(n, n, n if dim == 3 else 1), dx=1.0 / n, origin=(0.0, 0.0, 0.0),
+                periodic=(False, False, False), mu=1.0, lam=2.0,
+                options=Options(c=10.0, omega=1.8, gamma=0.0, proj_every=proj_every))
+    c = (0.5, 0.5, 0.5)
+    vt = np.array([0.01, -0.02, 0.015])[:dim]
+    p.shapes = [Shape("sphere", c, (0.37,), boundary_id=1)]
+    p.bcs = [BC(1, "neumann", "const", vec=(0.0, 0.0, 0.0))]
+    if anchored:
+        p.shapes.append(Shape("sphere", c, (0.15,), complement=True, boundary_id=0))
+        p.bcs.append(BC(0, "dirichlet", "const", ramp="time", vec=tuple(vt)))
+    _rest_fields(p)
+    for i in range(dim):
+        p.v0[i] = vt[i]
+    p.steps = steps
+    p.meta = dict(vt=vt)
+    return p
+
+
 def random_periodic(dim: int, n: int, seed: int, amp: float = 0.02, mu: float = 1.0,
                     lam: float = 3.0, omega: float = 1.7, gamma: float = 0.0,
                     body_force=(0.0, 0.0, 0.0), init_mode: str = "equilibrium") -> Problem:

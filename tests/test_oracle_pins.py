@@ -172,29 +172,15 @@ def _uniform_damped(D, c, b, gamma=10.0, n=6, t_end=0.5):
     return p.dt, steps, va, v.reshape(D, -1), F.reshape(D * D, -1)
 
 
-def _rigid_translation(D, anchored, proj_every=5, steps=23):
-    """A disc (ball) or annulus (shell) moving at a uniform velocity with F = I: traction-free outer
-    surface; with `anchored`, an inner surface carrying the Dirichlet translation u_D = t vt."""
-    n = 40 if D == 2 else 20
-    p = I.Problem(name=f"rigid_{D}d", dim=D, n=(n, n, n if D == 3 else 1), dx=1.0 / n, origin=(0, 0, 0),
-                  periodic=(False, False, False), mu=1.0, lam=2.0,
-                  options=I.Options(c=10.0, omega=1.8, gamma=0.0, proj_every=proj_every))
-    c = (0.5, 0.5, 0.5)
-    vt = np.array([0.01, -0.02, 0.015])[:D]
-    p.shapes = [I.Shape("sphere", c, (0.37,), boundary_id=1)]
-    p.bcs = [I.BC(1, "neumann", "const", vec=(0, 0, 0))]
-    if anchored:
-        p.shapes.append(I.Shape("sphere", c, (0.15,), complement=True, boundary_id=0))
-        p.bcs.append(I.BC(0, "dirichlet", "const", ramp="time", vec=tuple(vt)))
-    I._rest_fields(p)
-    for i in range(D):
-        p.v0[i] = vt[i]
+def _rigid_translation(D, anchored):
+    p = I.rigid_translation(D, anchored)
     o = oracle.Oracle(p)
     o.set_initial()
-    o.step(steps)
+    o.step(p.steps)
     v, F, u = o.fields()
     act = o.active_mask().reshape(-1).astype(bool)
-    return vt, steps * p.dt, v.reshape(D, -1)[:, act], F.reshape(D * D, -1)[:, act], u.reshape(D, -1)[:, act]
+    return (p.meta["vt"], p.steps * p.dt, v.reshape(D, -1)[:, act], F.reshape(D * D, -1)[:, act],
+            u.reshape(D, -1)[:, act])
 
 
 @pytest.mark.parametrize("D", [2, 3])
