@@ -174,12 +174,12 @@ def link_bytes(D, real_size, n_cut, lsq_entries):
 def jacobi_bytes_per_node(D, real_size, sweeps_per_launch=1):
     """Algorithmic HBM bytes per active node and sweep of the damped-Jacobi sweeps: per launch the
     node's correction vector read and written (D values padded to 2 or 4), its residual vector (4
-    values: r and the sweep weight) and, in the FP64 form, its flag byte (the FP32 forms carry the
-    node's cut bits in a spare slot of d (3D) or of the residual (2D)), shared by the sweeps of the
-    launch (two with the two-sweep kernel, whose first sweep stays in shared memory); neighbour
-    reads hit in cache."""
+    values: r and the sweep weight) and its flag byte, shared by the sweeps of the launch (two with
+    the two-sweep kernel, whose first sweep stays in shared memory); neighbour reads hit in cache.
+    The FP32 forms' 3D sweeps and 2D two-sweep launches load no flag byte: the node's cut bits ride
+    in a spare slot of d (3D) or of the residual (2D)."""
     dv = 4 if D == 3 else 2
-    flag = 1 if real_size == 8 else 0
+    flag = 1 if real_size == 8 or (D == 2 and sweeps_per_launch == 1) else 0
     return (2 * dv * real_size + 4 * real_size + flag) / sweeps_per_launch
 
 

@@ -28,6 +28,7 @@ def test_algorithmic_bytes_per_node():
     assert b.jacobi_bytes_per_node(3, 4) == 2 * 4 * 4 + 4 * 4 == 48
     assert b.jacobi_bytes_per_node(3, 4, 2) == 24
     assert b.jacobi_bytes_per_node(2, 4, 2) == (2 * 2 * 4 + 4 * 4) / 2
+    assert b.jacobi_bytes_per_node(2, 4) == 2 * 2 * 4 + 4 * 4 + 1 == 33
     assert b.jacobi_bytes_per_node(3, 8) == 2 * 4 * 8 + 4 * 8 + 1
     # the method's figure: u* in the population precision (the coverage contract's 601 B in 3D FP32)
     assert b.method_bytes_per_node(3, 4) == 601
