@@ -3,6 +3,7 @@ twin ``liblbm_b300_check.so`` (-DLBM_CHECK: data-dependent indices checked in th
 violation latched as LBM_DEV_BOUNDS)."""
 from __future__ import annotations
 
+import fcntl
 import glob
 import os
 import subprocess
@@ -49,7 +50,18 @@ def _link(lib: str, objdir: str, extra: list, verbose: bool) -> list:
 
 def build(force: bool = False, verbose: bool = False, check: bool = True) -> str:
     """Compile both libraries (the checked one unless check=False) when a source is newer; the
-    translation units compile in parallel."""
+    translation units compile in parallel.  Callers in several processes (one per rank) take turns
+    on a lock file, so one compiles and the others then find the libraries current."""
+    os.makedirs(os.path.join(HERE, "_build"), exist_ok=True)
+    with open(os.path.join(HERE, "_build", ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, check)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, check: bool) -> str:
     targets = [(LIB, os.path.join(HERE, "_build"), [])]
     if check:
         targets.append((LIB_CHECK, os.path.join(HERE, "_build_check"), ["-DLBM_CHECK"]))
